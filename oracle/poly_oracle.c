@@ -1,0 +1,515 @@
+/*
+ * poly_oracle.c -- plain, slow, obviously-correct CPU oracle for polynomial
+ * lossless compression (Aubert et al., "Polynomial data compression for
+ * large-scale physics experiments", arXiv:1805.01844).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may link or call
+ * this file: only the test suite, the smoke check and the benchmark's CPU
+ * baseline / reference legs use it.  It shares no code, header, table or
+ * constant with the CUDA implementation.
+ *
+ * Every arithmetic step is written in the order the paper gives it, with
+ * unsigned __int128 intermediates so that no product can overflow.  There is
+ * no blocking, fusion or reordering beyond what the method itself states.
+ *
+ * What it computes, with the passage each function follows:
+ *   po_eq1_p        -- Sec. 3.1, Eq. 1: number of base-B digits per word,
+ *                      integer form p = max{p : B^p <= 2^w - 1}.
+ *   po_basic_*      -- Sec. 3.1, Eq. 2: s_j = sum_i v_{i+p(j-1)} B^{i-1}
+ *                      (first value in the lowest power), decoded by
+ *                      polynomial division.
+ *   po_adv_*        -- Sec. 3.2, Eqs. 3-11 and the series for the whole
+ *                      vector: split base R_i * R'_i >= B, word
+ *                      s_i = r_i + R_i (sum_k v_{q_i+k} B^{p_i-k} + r'_{i-1} B^{p_i}).
+ *   po_compress /
+ *   po_decompress   -- Sec. 3.3 (blocked compression) and Fig. 2 (minimum
+ *                      then base stored once per block, then the packed data).
+ *
+ * Readings where the paper is silent or garbled (each is listed in the design
+ * notes of the repository):
+ *   - capacity constant: 2^w - 1 with w in {32, 64} replaces 2^32 - 1;
+ *     p is computed with integers, never with a floating-point logarithm.
+ *   - basic variant: p is clamped to >= 1 (only B = 2^32 with w = 32 hits it;
+ *     an offset < 2^32 then occupies one word by itself).
+ *   - B == 1: a block is stored with zero payload words.
+ *   - the range 1 <= j < n/p of Eq. 2 is read as j = 1..ceil(n_b/p); missing
+ *     digits of the last word are 0 (both variants).
+ *   - advanced series, index reading: word i holds, from the most significant
+ *     end, the high part r'_{i-1} of the element split off word i-1, then p_i
+ *     whole elements (first element at the highest power), then the low part
+ *     r_i of the next element.  q_i counts the elements before word i's whole
+ *     digits: q_1 = 0, q_{i+1} = q_i + p_i + 1.  The vector ends with the
+ *     first word whose split slot lies past the end (that slot is 0).
+ *   - base stored as B - 1 (B = 2^d does not fit in d bits).
+ */
+#include <stdint.h>
+#include <stddef.h>
+#include <string.h>
+#include <stdlib.h>
+
+typedef unsigned __int128 u128;
+
+enum {
+    PO_OK = 0,
+    PO_ERR_INVALID_ARG = 1,
+    PO_ERR_CAPACITY = 2,
+    PO_ERR_CORRUPT = 3,
+    PO_ERR_UNSUPPORTED = 6
+};
+
+#define PO_HEADER_BYTES 64u
+
+/* ---------------------------------------------------------------- Eq. 1 -- */
+
+/* C = 2^w - 1, the largest value one packed word can hold. */
+static u128 po_capacity(unsigned w) { return (((u128)1) << w) - 1; }
+
+/* Eq. 1 in integer form: the largest p >= 0 with B^p <= 2^w - 1.
+ * B >= 2, 1 <= w <= 64, B <= 2^33 (so that B^p * B never leaves 128 bits). */
+unsigned po_eq1_p(uint64_t B, unsigned w)
+{
+    u128 C = po_capacity(w);
+    u128 power = 1; /* B^p */
+    unsigned p = 0;
+    while (power * (u128)B <= C) {
+        power *= (u128)B;
+        p += 1;
+    }
+    return p;
+}
+
+/* ------------------------------------------------------ basic, Eq. 2 ----- */
+
+/* digits per word of the basic variant (Eq. 1, clamped to >= 1) */
+static unsigned po_basic_p(uint64_t B, unsigned w)
+{
+    unsigned p = po_eq1_p(B, w);
+    return p == 0 ? 1u : p;
+}
+
+/* number of packed words for a block of n_b offsets in base B */
+uint64_t po_basic_count(uint64_t B, unsigned w, uint64_t n_b)
+{
+    if (B <= 1 || n_b == 0) return 0;
+    uint64_t p = po_basic_p(B, w);
+    return (n_b + p - 1) / p;
+}
+
+/* Eq. 2: word j (0-based) = sum_{i=0}^{p-1} u[j p + i] * B^i. */
+uint64_t po_basic_pack(uint64_t B, unsigned w, const uint64_t *u, uint64_t n_b,
+                       uint64_t *words)
+{
+    uint64_t W = po_basic_count(B, w, n_b);
+    if (W == 0) return 0;
+    uint64_t p = po_basic_p(B, w);
+    for (uint64_t j = 0; j < W; ++j) {
+        u128 s = 0;
+        u128 power = 1; /* B^i */
+        for (uint64_t i = 0; i < p; ++i) {
+            uint64_t idx = j * p + i;
+            uint64_t digit = idx < n_b ? u[idx] : 0;
+            s += (u128)digit * power;
+            power *= (u128)B;
+        }
+        words[j] = (uint64_t)s;
+    }
+    return W;
+}
+
+/* Polynomial division: digit i of word j is (s div B^i) mod B.  A word is
+ * rejected if it is not the image of valid digits: s >= B^k where k is the
+ * number of real (non-padding) digits it holds. */
+int po_basic_unpack(uint64_t B, unsigned w, const uint64_t *words, uint64_t n_words,
+                    uint64_t n_b, uint64_t *u)
+{
+    if (B <= 1) {
+        if (n_words != 0) return PO_ERR_CORRUPT;
+        for (uint64_t i = 0; i < n_b; ++i) u[i] = 0;
+        return PO_OK;
+    }
+    uint64_t W = po_basic_count(B, w, n_b);
+    if (n_words != W) return PO_ERR_CORRUPT;
+    uint64_t p = po_basic_p(B, w);
+    for (uint64_t j = 0; j < W; ++j) {
+        u128 s = words[j];
+        uint64_t k = n_b - j * p < p ? n_b - j * p : p; /* real digits */
+        u128 limit = 1;
+        for (uint64_t i = 0; i < k; ++i) limit *= (u128)B;
+        if (s >= limit) return PO_ERR_CORRUPT;
+        for (uint64_t i = 0; i < k; ++i) {
+            u[j * p + i] = (uint64_t)(s % B);
+            s /= B;
+        }
+    }
+    return PO_OK;
+}
+
+/* -------------------------------------------- advanced, Sec. 3.2 --------- */
+
+/* One step of the split-base series (the unnumbered system after Eq. 11):
+ *   p_i  = max{p : R'_{i-1} B^p <= C}          (floor((ln C - ln R'_{i-1}) / ln B))
+ *   R_i  = floor(C / (R'_{i-1} B^{p_i}))
+ *   R'_i = ceil(B / R_i)
+ * Rprev is R'_{i-1} (R'_0 = 1). */
+static void po_adv_step(uint64_t B, unsigned w, uint64_t Rprev,
+                        unsigned *p_i, uint64_t *R_i, uint64_t *Rp_i)
+{
+    u128 C = po_capacity(w);
+    u128 denom = Rprev; /* R'_{i-1} B^p */
+    unsigned p = 0;
+    while (denom * (u128)B <= C) {
+        denom *= (u128)B;
+        p += 1;
+    }
+    u128 R = C / denom;
+    *p_i = p;
+    *R_i = (uint64_t)R;
+    *Rp_i = (uint64_t)(((u128)B + R - 1) / R);
+}
+
+/* Schedule of a block: per word i (0-based here) its p_i, R_i, R'_i and q_i.
+ * Returns the number of words; fills at most `cap` entries (pointers may be
+ * NULL to only count). */
+uint64_t po_adv_schedule(uint64_t B, unsigned w, uint64_t n_b,
+                         uint32_t *p_out, uint64_t *R_out, uint64_t *Rp_out,
+                         uint64_t *q_out, uint64_t cap)
+{
+    if (B <= 1 || n_b == 0) return 0;
+    uint64_t Rprev = 1; /* R'_0 */
+    uint64_t q = 0;     /* elements before this word's whole digits */
+    uint64_t i = 0;
+    for (;;) {
+        unsigned p;
+        uint64_t R, Rp;
+        po_adv_step(B, w, Rprev, &p, &R, &Rp);
+        if (i < cap) {
+            if (p_out) p_out[i] = p;
+            if (R_out) R_out[i] = R;
+            if (Rp_out) Rp_out[i] = Rp;
+            if (q_out) q_out[i] = q;
+        }
+        i += 1;
+        uint64_t split = q + p; /* index of the element split by this word */
+        if (split >= n_b) break; /* the split slot is padding: last word */
+        q = split + 1;
+        Rprev = Rp;
+    }
+    return i;
+}
+
+uint64_t po_adv_count(uint64_t B, unsigned w, uint64_t n_b)
+{
+    return po_adv_schedule(B, w, n_b, NULL, NULL, NULL, NULL, 0);
+}
+
+/* s_i = r_i + R_i * ( sum_{k=1}^{p_i} v_{q_i+k} B^{p_i-k} + r'_{i-1} B^{p_i} )
+ * with the split element e = v_{q_i+p_i+1} (1-based), r'_i = e div R_i,
+ * r_i = e - r'_i R_i.  Elements past n_b are 0. */
+uint64_t po_adv_pack(uint64_t B, unsigned w, const uint64_t *u, uint64_t n_b,
+                     uint64_t *words)
+{
+    if (B <= 1 || n_b == 0) return 0;
+    uint64_t Rprev = 1;  /* R'_{i-1} */
+    uint64_t rpprev = 0; /* r'_{i-1} */
+    uint64_t q = 0;
+    uint64_t i = 0;
+    for (;;) {
+        unsigned p;
+        uint64_t R, Rp;
+        po_adv_step(B, w, Rprev, &p, &R, &Rp);
+        /* sum_{k=1}^{p} v_{q+k} B^{p-k}, 0-based element q+k-1 */
+        u128 body = 0;
+        for (unsigned k = 1; k <= p; ++k) {
+            uint64_t idx = q + k - 1;
+            uint64_t digit = idx < n_b ? u[idx] : 0;
+            u128 power = 1;
+            for (unsigned e = 0; e < p - k; ++e) power *= (u128)B;
+            body += (u128)digit * power;
+        }
+        u128 top = 1;
+        for (unsigned e = 0; e < p; ++e) top *= (u128)B;
+        body += (u128)rpprev * top;
+        uint64_t split = q + p;
+        uint64_t e_split = split < n_b ? u[split] : 0;
+        uint64_t rp = e_split / R;
+        uint64_t r = e_split - rp * R;
+        u128 s = (u128)r + (u128)R * body;
+        words[i] = (uint64_t)s;
+        i += 1;
+        if (split >= n_b) break;
+        q = split + 1;
+        Rprev = Rp;
+        rpprev = rp;
+    }
+    return i;
+}
+
+/* Inverse of po_adv_pack.  Rejects any word that is not the image of valid
+ * digits: a top part r'_{i-1} >= R'_{i-1}, a re-joined split element >= B, a
+ * non-zero padding digit, or a non-zero low part in a padding split slot. */
+int po_adv_unpack(uint64_t B, unsigned w, const uint64_t *words, uint64_t n_words,
+                  uint64_t n_b, uint64_t *u)
+{
+    if (B <= 1) {
+        if (n_words != 0) return PO_ERR_CORRUPT;
+        for (uint64_t i = 0; i < n_b; ++i) u[i] = 0;
+        return PO_OK;
+    }
+    if (n_words != po_adv_count(B, w, n_b)) return PO_ERR_CORRUPT;
+    uint64_t Rprev = 1;
+    uint64_t Rlast = 1;  /* R_{i-1} */
+    uint64_t rlast = 0;  /* r_{i-1} */
+    uint64_t q = 0;
+    for (uint64_t i = 0; i < n_words; ++i) {
+        unsigned p;
+        uint64_t R, Rp;
+        po_adv_step(B, w, Rprev, &p, &R, &Rp);
+        u128 s = words[i];
+        uint64_t r = (uint64_t)(s % R);
+        u128 body = s / R;
+        /* whole digits, least significant first = last element first */
+        for (unsigned k = p; k >= 1; --k) {
+            uint64_t digit = (uint64_t)(body % B);
+            body /= B;
+            uint64_t idx = q + k - 1;
+            if (idx < n_b) u[idx] = digit;
+            else if (digit != 0) return PO_ERR_CORRUPT;
+        }
+        /* what is left is r'_{i-1}, the high part of the element split off
+         * the previous word */
+        if (body >= (u128)Rprev) return PO_ERR_CORRUPT;
+        if (i > 0) {
+            u128 e = body * (u128)Rlast + rlast;
+            if (e >= (u128)B) return PO_ERR_CORRUPT;
+            u[q - 1] = (uint64_t)e;
+        }
+        uint64_t split = q + p;
+        if (split >= n_b) {
+            if (r != 0) return PO_ERR_CORRUPT;
+            if (i + 1 != n_words) return PO_ERR_CORRUPT;
+            break;
+        }
+        q = split + 1;
+        Rprev = Rp;
+        Rlast = R;
+        rlast = r;
+    }
+    return PO_OK;
+}
+
+/* ------------------------------------------ blocked stream, Sec. 3.3 ----- */
+
+/* Stream layout (all little-endian):
+ *   header, 64 bytes:  "PCMP", u16 version = 1, u8 variant, u8 dtype_bits,
+ *                      u8 word_bits, 3 zero bytes, u32 block_len,
+ *                      u64 n_samples, u64 n_blocks, u64 payload_words,
+ *                      24 zero bytes
+ *   block table:       per block (vmin, B - 1), each a dtype_bits field,
+ *                      zero-padded to a multiple of 16 bytes
+ *   payload:           per block, its packed words (word_bits each)       */
+
+static void put_le(uint8_t *dst, uint64_t v, unsigned nbytes)
+{
+    for (unsigned i = 0; i < nbytes; ++i) dst[i] = (uint8_t)(v >> (8 * i));
+}
+
+static uint64_t get_le(const uint8_t *src, unsigned nbytes)
+{
+    uint64_t v = 0;
+    for (unsigned i = 0; i < nbytes; ++i) v |= (uint64_t)src[i] << (8 * i);
+    return v;
+}
+
+static uint64_t po_count(unsigned variant, uint64_t B, unsigned w, uint64_t n_b)
+{
+    return variant == 0 ? po_basic_count(B, w, n_b) : po_adv_count(B, w, n_b);
+}
+
+static int po_params_ok(unsigned variant, unsigned d, unsigned w, uint64_t L)
+{
+    return (variant == 0 || variant == 1) && (d == 16 || d == 32) &&
+           (w == 32 || w == 64) && L >= 1 && L <= 0xFFFFFFFFull;
+}
+
+static uint64_t po_table_bytes(uint64_t n_blocks, unsigned d)
+{
+    uint64_t t = n_blocks * 2 * (d / 8);
+    return (t + 15) / 16 * 16;
+}
+
+/* Worst-case stream size for n samples: every block at its largest word count
+ * over all B in [1, 2^d]. */
+int po_bound(unsigned variant, unsigned d, unsigned w, uint64_t L, uint64_t n,
+             uint64_t *max_bytes)
+{
+    if (!po_params_ok(variant, d, w, L)) return PO_ERR_INVALID_ARG;
+    uint64_t n_blocks = (n + L - 1) / L;
+    uint64_t total = PO_HEADER_BYTES + po_table_bytes(n_blocks, d);
+    /* per block length class: full blocks and the last one */
+    uint64_t Bmax = (uint64_t)1 << d;
+    uint64_t pmin = variant == 0 ? po_basic_p(Bmax, w) : po_eq1_p(Bmax, w);
+    for (int last = 0; last < 2; ++last) {
+        uint64_t nb, count;
+        if (n_blocks == 0) break;
+        if (!last) { nb = L; count = n_blocks - 1; }
+        else { nb = n - (n_blocks - 1) * L; count = 1; }
+        if (count == 0) continue;
+        /* basic: ceil(n_b/p) is largest at the largest B.  advanced: every word
+         * consumes at least p_1(B) >= p_1(2^d) elements (p_i >= p_1 - 1 plus
+         * the split slot), hence at most ceil((n_b + 1) / p_1) words, or
+         * n_b + 1 words when p_1 = 0. */
+        uint64_t Wb;
+        if (variant == 0) Wb = (nb + pmin - 1) / pmin;
+        else Wb = pmin == 0 ? nb + 1 : (nb + 1 + pmin - 1) / pmin;
+        total += count * Wb * (w / 8);
+    }
+    *max_bytes = total;
+    return PO_OK;
+}
+
+uint64_t po_stream_bytes(unsigned d, unsigned w, uint64_t n_blocks, uint64_t payload_words)
+{
+    return PO_HEADER_BYTES + po_table_bytes(n_blocks, d) + payload_words * (w / 8);
+}
+
+int po_compress(const void *in, uint64_t n, unsigned variant, unsigned d, unsigned w,
+                uint64_t L, uint8_t *out, uint64_t cap, uint64_t *out_bytes)
+{
+    if (!po_params_ok(variant, d, w, L)) return PO_ERR_INVALID_ARG;
+    uint64_t bound;
+    po_bound(variant, d, w, L, n, &bound);
+    if (cap < bound) return PO_ERR_CAPACITY;
+    uint64_t n_blocks = (n + L - 1) / L;
+    unsigned db = d / 8, wb = w / 8;
+    uint64_t table_off = PO_HEADER_BYTES;
+    uint64_t payload_off = table_off + po_table_bytes(n_blocks, d);
+    memset(out, 0, payload_off);
+
+    uint64_t payload_words = 0;
+    /* scratch for one block: offsets and packed words (at most n_b + 1) */
+    uint64_t *u = (uint64_t *)malloc((L + 2) * sizeof(uint64_t));
+    uint64_t *words = (uint64_t *)malloc((L + 2) * sizeof(uint64_t));
+    if (!u || !words) { free(u); free(words); return PO_ERR_INVALID_ARG; }
+
+    for (uint64_t b = 0; b < n_blocks; ++b) {
+        uint64_t start = b * L;
+        uint64_t n_b = n - start < L ? n - start : L;
+        /* Sec. 3.1: minimum and maximum of the block */
+        uint64_t vmin = UINT64_MAX, vmax = 0;
+        for (uint64_t i = 0; i < n_b; ++i) {
+            uint64_t v = d == 16 ? ((const uint16_t *)in)[start + i]
+                                 : ((const uint32_t *)in)[start + i];
+            if (v < vmin) vmin = v;
+            if (v > vmax) vmax = v;
+        }
+        uint64_t B = vmax - vmin + 1; /* base B = vmax - vmin + 1 */
+        for (uint64_t i = 0; i < n_b; ++i) {
+            uint64_t v = d == 16 ? ((const uint16_t *)in)[start + i]
+                                 : ((const uint32_t *)in)[start + i];
+            u[i] = v - vmin; /* offsets in [0, B) */
+        }
+        /* Fig. 2: the minimum, then the base, stored once per block */
+        put_le(out + table_off + b * 2 * db, vmin, db);
+        put_le(out + table_off + b * 2 * db + db, B - 1, db);
+        uint64_t W = variant == 0 ? po_basic_pack(B, w, u, n_b, words)
+                                  : po_adv_pack(B, w, u, n_b, words);
+        for (uint64_t j = 0; j < W; ++j)
+            put_le(out + payload_off + (payload_words + j) * wb, words[j], wb);
+        payload_words += W;
+    }
+    /* header */
+    memcpy(out, "PCMP", 4);
+    put_le(out + 4, 1, 2);
+    out[6] = (uint8_t)variant;
+    out[7] = (uint8_t)d;
+    out[8] = (uint8_t)w;
+    put_le(out + 12, L, 4);
+    put_le(out + 16, n, 8);
+    put_le(out + 24, n_blocks, 8);
+    put_le(out + 32, payload_words, 8);
+    *out_bytes = payload_off + payload_words * wb;
+    free(u);
+    free(words);
+    return PO_OK;
+}
+
+/* Header fields, for tests. */
+int po_read_header(const uint8_t *in, uint64_t in_bytes, unsigned *variant, unsigned *d,
+                   unsigned *w, uint64_t *L, uint64_t *n, uint64_t *n_blocks,
+                   uint64_t *payload_words)
+{
+    if (in_bytes < PO_HEADER_BYTES) return PO_ERR_CORRUPT;
+    if (memcmp(in, "PCMP", 4) != 0) return PO_ERR_CORRUPT;
+    if (get_le(in + 4, 2) != 1) return PO_ERR_CORRUPT;
+    for (unsigned i = 9; i < 12; ++i) if (in[i] != 0) return PO_ERR_CORRUPT;
+    for (unsigned i = 40; i < 64; ++i) if (in[i] != 0) return PO_ERR_CORRUPT;
+    *variant = in[6];
+    *d = in[7];
+    *w = in[8];
+    *L = get_le(in + 12, 4);
+    *n = get_le(in + 16, 8);
+    *n_blocks = get_le(in + 24, 8);
+    *payload_words = get_le(in + 32, 8);
+    if (!po_params_ok(*variant, *d, *w, *L)) return PO_ERR_CORRUPT;
+    if (*n_blocks != (*n + *L - 1) / *L) return PO_ERR_CORRUPT;
+    return PO_OK;
+}
+
+int po_decompress(const uint8_t *in, uint64_t in_bytes, void *out, uint64_t cap,
+                  uint64_t *n_out)
+{
+    unsigned variant, d, w;
+    uint64_t L, n, n_blocks, payload_words;
+    *n_out = 0;
+    int st = po_read_header(in, in_bytes, &variant, &d, &w, &L, &n, &n_blocks,
+                            &payload_words);
+    if (st != PO_OK) return st;
+    if (n > cap) return PO_ERR_CAPACITY;
+    unsigned db = d / 8, wb = w / 8;
+    uint64_t table_off = PO_HEADER_BYTES;
+    /* the table must fit before any of it is read */
+    if (n_blocks > (in_bytes - table_off) / (2 * db)) return PO_ERR_CORRUPT;
+    uint64_t payload_off = table_off + po_table_bytes(n_blocks, d);
+    if (payload_off > in_bytes) return PO_ERR_CORRUPT;
+    for (uint64_t i = table_off + n_blocks * 2 * db; i < payload_off; ++i)
+        if (in[i] != 0) return PO_ERR_CORRUPT;
+    /* block word counts from the table alone, then the payload size */
+    uint64_t sum = 0;
+    uint64_t dmax = d == 16 ? 0xFFFFull : 0xFFFFFFFFull;
+    for (uint64_t b = 0; b < n_blocks; ++b) {
+        uint64_t n_b = n - b * L < L ? n - b * L : L;
+        uint64_t vmin = get_le(in + table_off + b * 2 * db, db);
+        uint64_t Bm1 = get_le(in + table_off + b * 2 * db + db, db);
+        if (vmin + Bm1 > dmax) return PO_ERR_CORRUPT;
+        sum += po_count(variant, Bm1 + 1, w, n_b);
+    }
+    if (sum != payload_words) return PO_ERR_CORRUPT;
+    if (payload_words > (in_bytes - payload_off) / wb) return PO_ERR_CORRUPT;
+
+    uint64_t *u_buf = (uint64_t *)malloc((L + 2) * sizeof(uint64_t));
+    uint64_t *w_buf = (uint64_t *)malloc((L + 2) * sizeof(uint64_t));
+    if (!u_buf || !w_buf) { free(u_buf); free(w_buf); return PO_ERR_INVALID_ARG; }
+    uint64_t off = 0;
+    for (uint64_t b = 0; b < n_blocks; ++b) {
+        uint64_t start = b * L;
+        uint64_t n_b = n - start < L ? n - start : L;
+        uint64_t vmin = get_le(in + table_off + b * 2 * db, db);
+        uint64_t B = get_le(in + table_off + b * 2 * db + db, db) + 1;
+        uint64_t W = po_count(variant, B, w, n_b);
+        for (uint64_t j = 0; j < W; ++j)
+            w_buf[j] = get_le(in + payload_off + (off + j) * wb, wb);
+        st = variant == 0 ? po_basic_unpack(B, w, w_buf, W, n_b, u_buf)
+                          : po_adv_unpack(B, w, w_buf, W, n_b, u_buf);
+        if (st != PO_OK) { free(u_buf); free(w_buf); return st; }
+        for (uint64_t i = 0; i < n_b; ++i) {
+            uint64_t v = u_buf[i] + vmin;
+            if (d == 16) ((uint16_t *)out)[start + i] = (uint16_t)v;
+            else ((uint32_t *)out)[start + i] = (uint32_t)v;
+        }
+        off += W;
+    }
+    free(u_buf);
+    free(w_buf);
+    *n_out = n;
+    return PO_OK;
+}

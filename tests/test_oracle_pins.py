@@ -1,0 +1,265 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+None of these re-types the oracle's formulas: they compare it with values
+worked by hand from the paper's equations (tests/golden), with the paper's own
+floating-point form of Eq. 1, with exhaustive enumeration (bijectivity), with
+a textbook routine it must reduce to (fixed-width bit packing), with the
+closed-form packed length, and with the compression ratios the paper reports
+for its simulated distribution (Sec. 4.2).
+"""
+import itertools
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1805_01844_gb300 import datagen
+
+
+def _read_golden(golden_dir, name):
+    out = {}
+    for line in open(os.path.join(golden_dir, name)):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        k, v = line.split(":", 1)
+        out[k.strip()] = v.strip()
+    return out
+
+
+# ----------------------------------------------------------------- Eq. 1
+
+
+def test_eq1_table_worked_by_hand(golden_dir):
+    n = 0
+    for line in open(os.path.join(golden_dir, "eq1_p_table.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        B, w, p = (int(t) for t in line.split())
+        assert oracle.eq1_p(B, w) == p, (B, w, p)
+        n += 1
+    assert n >= 20
+
+
+def test_eq1_agrees_with_papers_logarithm_form():
+    """Eq. 1 as printed, p = floor(ln(2^32 - 1) / ln B), evaluated in floating
+    point wherever the quotient is not within rounding of an integer."""
+    rng = np.random.default_rng(1)
+    Bs = list(range(2, 5000)) + [int(b) for b in rng.integers(5000, 1 << 32, 3000)]
+    checked = 0
+    for B in Bs:
+        q = math.log(2.0 ** 32 - 1) / math.log(B)
+        if abs(q - round(q)) < 1e-9:
+            continue
+        assert oracle.eq1_p(B, 32) == math.floor(q), B
+        checked += 1
+    assert checked > 7000
+
+
+# ------------------------------------------------------ worked examples
+
+
+def test_basic_worked_example(golden_dir):
+    g = _read_golden(golden_dir, "basic_worked_example.txt")
+    vals = np.array([int(t) for t in g["values"].split()], dtype=np.uint16)
+    w = int(g["word_bits"])
+    vmin, B = int(g["vmin"]), int(g["B"])
+    assert int(vals.min()) == vmin and int(vals.max()) - vmin + 1 == B
+    words = oracle.pack_block(0, B, w, vals.astype(np.uint64) - vmin)
+    assert [int(x) for x in words] == [int(t) for t in g["words"].split()]
+    stream = oracle.compress(vals, 0, w, len(vals))
+    assert stream == bytes.fromhex(g["stream_hex"])
+    assert np.array_equal(oracle.decompress(stream), vals)
+
+
+def test_advanced_schedules(golden_dir):
+    for line in open(os.path.join(golden_dir, "advanced_schedules.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        parts = [p.split() for p in line.split("|")]
+        B, w = int(parts[0][0]), int(parts[0][1])
+        want = [tuple(int(t) for t in trip) for trip in parts[1:]]
+        got = oracle.adv_schedule(B, w, 10_000)[: len(want)]
+        assert [(p, R, Rp) for p, R, Rp, _ in got] == want, (B, w)
+
+
+def test_advanced_worked_example(golden_dir):
+    g = _read_golden(golden_dir, "advanced_worked_example.txt")
+    B, w = int(g["B"]), int(g["word_bits"])
+    u = [int(t) for t in g["offsets"].split()]
+    words = oracle.pack_block(1, B, w, u)
+    assert [int(x) for x in words] == [int(t) for t in g["words"].split()]
+    assert list(oracle.unpack_block(1, B, w, words, len(u))) == u
+
+
+# --------------------------------------------- invariants of the series
+
+
+@pytest.mark.parametrize("w", [8, 12, 16, 32, 64])
+def test_split_base_invariants(w):
+    """Sec. 3.2: R_i R'_i >= B, 1 <= R_i < B, R'_{i-1} B^p_i R_i <= C, and p_i is
+    maximal; q advances by p_i + 1 per word."""
+    rng = np.random.default_rng(w)
+    C = (1 << w) - 1
+    Bs = [b for b in list(range(2, 200)) + [int(b) for b in rng.integers(2, 1 << min(w, 33), 200)]
+          if b <= C or w == 32]
+    for B in Bs:
+        sched = oracle.adv_schedule(B, w, 300)
+        Rprev, q = 1, 0
+        for p, R, Rp, qi in sched:
+            assert qi == q
+            assert Rprev * B ** p * R <= C
+            assert Rprev * B ** (p + 1) > C
+            assert 1 <= R < B or (B > C and R <= C)
+            assert R * Rp >= B and R * (Rp - 1) < B
+            Rprev, q = Rp, q + p + 1
+
+
+# -------------------------------------------------- exhaustive bijectivity
+
+
+CASES = [  # (variant, w, B, max_len); B = 256 > 2^8 - 1 is the p = 0 case
+    (0, 8, 3, 7), (0, 8, 7, 5), (0, 12, 5, 5), (0, 16, 7, 5), (0, 8, 16, 4),
+    (1, 8, 3, 9), (1, 8, 7, 5), (1, 8, 6, 5), (1, 12, 5, 6), (1, 8, 100, 2),
+    (1, 8, 256, 2), (0, 8, 256, 2), (1, 8, 2, 12), (1, 16, 3, 10),
+]
+
+
+@pytest.mark.parametrize("variant,w,B,max_len", CASES)
+def test_exhaustive_bijectivity(variant, w, B, max_len):
+    """Every tuple in [0, B)^n (n <= max_len) packs into words <= 2^w - 1, the
+    map is injective, and unpacking inverts it."""
+    C = (1 << w) - 1
+    for n in range(1, max_len + 1):
+        seen = set()
+        for tup in itertools.product(range(B), repeat=n):
+            words = oracle.pack_block(variant, B, w, tup)
+            assert all(int(x) <= C for x in words)
+            key = tuple(int(x) for x in words)
+            assert key not in seen
+            seen.add(key)
+            assert tuple(int(x) for x in oracle.unpack_block(variant, B, w, words, n)) == tup
+        assert len(seen) == B ** n
+
+
+# ---------------------------------- textbook reduction: fixed-width bit packing
+
+
+@pytest.mark.parametrize("k,w", [(1, 32), (2, 32), (4, 32), (8, 32), (4, 64), (8, 64), (16, 64), (2, 64)])
+def test_basic_power_of_two_base_is_lsb_first_bit_packing(k, w):
+    """With B = 2^k the basic method stores p = floor((w-1)/k) k-bit fields per
+    word, first field in the lowest bits: plain bit packing with shifts."""
+    rng = np.random.default_rng(k * 100 + w)
+    B = 1 << k
+    n = 1000
+    u = rng.integers(0, B, n, dtype=np.uint64)
+    fields = (w - 1) // k  # B^p <= 2^w - 1  <=>  p k <= w - 1
+    expect = []
+    for j in range(0, n, fields):
+        word = 0
+        for i, x in enumerate(u[j:j + fields]):
+            word |= int(x) << (k * i)
+        expect.append(word)
+    got = oracle.pack_block(0, B, w, u)
+    assert [int(x) for x in got] == expect
+
+
+# --------------------------------------------------- closed-form lengths
+
+
+@pytest.mark.parametrize("w", [32, 64])
+def test_stream_length_closed_form(golden_dir, w):
+    """Stream bytes = 64 + pad16(table) + sum_b ceil(n_b / p(B_b)) * w/8 with p
+    taken from the hand-worked Eq. 1 table."""
+    table = {}
+    for line in open(os.path.join(golden_dir, "eq1_p_table.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        B, ww, p = (int(t) for t in line.split())
+        if ww == w and B <= 65536:
+            table[B] = p
+    L = 1000
+    Bs = sorted(table)
+    x = np.concatenate([datagen.edge_block(B, L, seed=i, vmin=(i * 7) % (65537 - B))
+                        for i, B in enumerate(Bs)] + [datagen.edge_block(9, 123, seed=99)])
+    stream = oracle.compress(x, 0, w, L)
+    n_blocks = len(Bs) + 1
+    table_bytes = (n_blocks * 4 + 15) // 16 * 16
+    words = sum(-(-L // table[B]) for B in Bs) + -(-123 // table[9])
+    assert len(stream) == 64 + table_bytes + words * (w // 8)
+    h = oracle.header(stream)
+    assert h["payload_words"] == words and h["n_blocks"] == n_blocks
+
+
+# ------------------------------------------------------ round trips, errors
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("dtype", [np.uint16, np.uint32])
+@pytest.mark.parametrize("w", [32, 64])
+def test_round_trip_edge_sizes(variant, dtype, w):
+    rng = np.random.default_rng(5)
+    hi = np.iinfo(dtype).max
+    for n, L in [(0, 16), (1, 1), (1, 7), (17, 16), (1000, 1), (4097, 1024), (3000, 154)]:
+        for kind in ("noise", "const", "full", "two"):
+            if kind == "noise":
+                x = np.clip(rng.normal(300, 5, n).round(), 0, hi).astype(dtype)
+            elif kind == "const":
+                x = np.full(n, hi, dtype=dtype)
+            elif kind == "full":
+                x = rng.integers(0, hi, n, dtype=dtype, endpoint=True)
+                if n >= 2:
+                    x[0], x[-1] = 0, hi
+            else:
+                x = rng.integers(0, 2, n).astype(dtype) * hi
+            s = oracle.compress(x, variant, w, L)
+            assert len(s) <= oracle.bound(variant, np.dtype(dtype).itemsize * 8, w, L, n)
+            assert np.array_equal(oracle.decompress(s), x)
+
+
+def test_corrupt_and_capacity_detection():
+    x = datagen.white_noise(5000, seed=3)
+    for variant in (0, 1):
+        s = bytearray(oracle.compress(x, variant, 64, 1024))
+        with pytest.raises(oracle.OracleError) as e:
+            oracle.decompress(bytes(s[:-1]))
+        assert e.value.code == oracle.ERR_CORRUPT
+        bad = bytearray(s)
+        bad[0] ^= 1
+        with pytest.raises(oracle.OracleError) as e:
+            oracle.decompress(bytes(bad))
+        assert e.value.code == oracle.ERR_CORRUPT
+        bad = bytearray(s)
+        bad[-8:] = b"\xff" * 8  # last word all ones: above B^k
+        with pytest.raises(oracle.OracleError) as e:
+            oracle.decompress(bytes(bad))
+        assert e.value.code == oracle.ERR_CORRUPT
+        with pytest.raises(oracle.OracleError) as e:
+            oracle.decompress(bytes(s), capacity=4999)
+        assert e.value.code == oracle.ERR_CAPACITY
+
+
+# --------------------------------------- Sec. 4.2: the paper's simulated ratios
+
+
+def test_paper_simulated_ratios():
+    """Sec. 4.2: on A(3000, 500, 2000, 45000, 4, 1855) the advanced method
+    reaches 2.47054 with blocks of 154 elements and 2.10361 unblocked (ratio
+    against 32-bit words).  The paper's random numbers are unknown, so this pins
+    the reading of the method (advanced series, per-block min/base header)
+    statistically: 300 vectors, ratio = 4 N / (stream bytes - 64-byte stream
+    header), within 3 % (blocked) and 1 % (unblocked)."""
+    tot = {154: [0, 0], 1855: [0, 0]}
+    for s in range(300):
+        x = datagen.paper_distribution(3000, 500, 2000, 45000, 4, 1855, seed=s)
+        for L in tot:
+            st = oracle.compress(x, 1, 32, L)
+            tot[L][0] += 4 * x.size
+            tot[L][1] += len(st) - 64
+    blocked = tot[154][0] / tot[154][1]
+    unblocked = tot[1855][0] / tot[1855][1]
+    assert abs(blocked - 2.47054) / 2.47054 < 0.03, blocked
+    assert abs(unblocked - 2.10361) / 2.10361 < 0.01, unblocked
+    assert blocked > 1.15 * unblocked  # "larger than 17 %"
