@@ -1,0 +1,453 @@
+"""Benchmark of the GPU polynomial compression path (arXiv:1805.01844).
+
+One step = one compress + one decompress (the whole hot path) of the
+Cherenkov-camera workload: 10,000 events x 2 gains x 40 time samples x 1855
+pixels of uint16 (2.97 GB), drawn on the GPU from the seeded generator in
+paper_1805_01844_gb300.datagen (synthetic stand-in for the paper's CTA
+waveform files, Sec. 4.3.1).  Inputs stay resident in HBM; they are far
+larger than L2, so no flush is needed between steps.
+
+Prints one JSON line.  `value` is the round-trip throughput in uncompressed
+GB/s (input bytes / (compress + decompress time)); the per-direction
+throughputs, the compression ratio, the roofline of the dominant kernel, the
+oracle timed on the host cores and an end-to-end figure through host buffers
+are reported beside it.
+
+  python bench.py [--steps K] [--warmup W] [--variant basic|advanced]
+                  [--block-len L] [--word-bits 32|64] [--impl ours|reference]
+Under torchrun each rank compresses its own copy of the workload (weak
+scaling, no collective on the data path).
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+GB = 1e9
+WORKLOAD = dict(n_events=10000, n_gains=2, n_time=40, n_pixels=1855)
+METRIC = "compress/decompress input GB/s on 1 GB300 (% HBM peak) and ratio, learned vs plain"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--variant", choices=["basic", "advanced"], default="basic")
+    ap.add_argument("--block-len", type=int, default=1024)
+    ap.add_argument("--word-bits", type=int, default=64, choices=[32, 64])
+    ap.add_argument("--events", type=int, default=WORKLOAD["n_events"])
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-events", type=int, default=0,
+                    help="events in the oracle's CPU sample (0 = sized to ~15 s)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload_name(args):
+    return "cherenkov_events_%dx%dx%dx%d_u16" % (args.events, WORKLOAD["n_gains"], WORKLOAD["n_time"],
+                                                WORKLOAD["n_pixels"])
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            j = json.load(f)
+        return float(j["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1805_01844_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode())
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel_key):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    try:
+        with open(path) as f:
+            j = json.load(f)
+    except Exception:
+        return None
+    e = j.get(kernel_key)
+    if not e or e.get("source_hash") != kernel_source_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 100 ms; only the
+    samples that arrive inside [mark_start, mark_stop] are summarised."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.gpu = gpu_index
+        self.lines = []
+        self.t0 = self.t1 = None
+
+    def start(self):
+        import threading
+
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+
+        def reader():
+            for line in self.proc.stdout:
+                self.lines.append((time.perf_counter(), line))
+
+        self.thread = threading.Thread(target=reader, daemon=True)
+        self.thread.start()
+
+    def mark_start(self):
+        self.t0 = time.perf_counter()
+
+    def mark_stop(self):
+        self.t1 = time.perf_counter()
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0,
+                    "note": "nvidia-smi unavailable"}
+        time.sleep(0.15)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for t, line in self.lines:
+            if self.t0 is None or t < self.t0 or t > self.t1 + 0.1:
+                continue
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = max(mx, float(parts[2]))
+            except ValueError:
+                continue
+            for name, flag in zip(names, parts[5:9]):
+                if flag.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_info():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ------------------------------------------------------------------ oracle leg
+
+
+def oracle_sample_timing(x_host_events, variant, w, L, target_s=15.0, fixed_events=0):
+    """Time the CPU oracle (single thread, as it stands) compressing and
+    decompressing a prefix of the events; returns (GB/s, events, seconds)."""
+    import oracle
+
+    per_event = x_host_events[0].size * 2
+    if fixed_events:
+        n_ev = fixed_events
+    else:
+        probe = x_host_events[:2].reshape(-1)
+        t0 = time.perf_counter()
+        s = oracle.compress(probe, variant, w, L)
+        oracle.decompress(s)
+        dt = (time.perf_counter() - t0) / 2
+        n_ev = max(1, min(len(x_host_events), int(target_s / max(dt, 1e-6))))
+    x = x_host_events[:n_ev].reshape(-1)
+    t0 = time.perf_counter()
+    s = oracle.compress(x, variant, w, L)
+    t1 = time.perf_counter()
+    y = oracle.decompress(s)
+    t2 = time.perf_counter()
+    assert (y == x).all()
+    return n_ev * per_event / (t2 - t0) / GB, n_ev, t2 - t0, len(s)
+
+
+def run_reference(args):
+    """The reference arm: the CPU oracle as it stands, on the host cores, on a
+    bounded sample of the same workload (rank 0 only)."""
+    import numpy as np
+
+    from paper_1805_01844_gb300 import datagen
+
+    world, rank, _ = dist_info()
+    if rank != 0:
+        return
+    variant = 0 if args.variant == "basic" else 1
+    n_ev = args.cpu_events or 8
+    x = datagen.cherenkov_events(n_ev, seed=0)
+    import oracle
+
+    oracle.build.build()
+    per_step = x.size * 2
+    for _ in range(args.warmup):
+        oracle.decompress(oracle.compress(x.reshape(-1), variant, args.word_bits, args.block_len))
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        s = oracle.compress(x.reshape(-1), variant, args.word_bits, args.block_len)
+        oracle.decompress(s)
+    dt = time.perf_counter() - t0
+    value = per_step * args.steps / dt / GB
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u16",
+        "data": "synthetic", "ratio": per_step / len(s),
+        "config": {"workload": workload_name(args), "variant": args.variant,
+                   "block_len": args.block_len, "word_bits": args.word_bits},
+        "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                         "sample": "first %d events (%.1f MB) of the workload, generated on the host"
+                                   % (n_ev, per_step / 1e6)},
+        "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------- GPU leg
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import numpy as np
+    import torch
+
+    import paper_1805_01844_gb300 as pc
+    from paper_1805_01844_gb300 import datagen, native
+
+    world, rank, local = dist_info()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+    native.load()
+    variant = pc.BASIC if args.variant == "basic" else pc.ADVANCED
+    L, w = args.block_len, args.word_bits
+
+    x = datagen.cherenkov_events_torch(args.events, dev, seed=0).reshape(-1)
+    n = x.numel()
+    raw_bytes = n * 2
+    codec = pc.Codec(variant, 16, w, L, max_samples=n, device=dev)
+    sbuf = torch.empty(codec.bound(n), dtype=torch.uint8, device=dev)
+    ybuf = torch.empty(n, dtype=torch.int16, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        _, nb = codec.compress(x, out=sbuf)
+        codec.decompress(sbuf, sbuf.numel(), n, out=ybuf)
+        return nb
+
+    # correctness before timing: exact round trip on the device, sampled blocks
+    # against the oracle (rank 0)
+    nb = step()
+    st = codec.device_status()
+    assert st == 0, native.strerror(st)
+    stream_bytes = int(nb.item())
+    assert torch.equal(ybuf, x), "round trip failed"
+    parity = "not checked"
+    if rank == 0:
+        parity = sampled_parity(x, sbuf, stream_bytes, variant, w, L)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.mark_start()
+    t_start = time.perf_counter()
+    for k in range(args.steps):
+        ev[k][0].record(stream)
+        codec.compress(x, out=sbuf)
+        ev[k][1].record(stream)
+        codec.decompress(sbuf, sbuf.numel(), n, out=ybuf)
+        ev[k][2].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    wall = time.perf_counter() - t_start
+    clocks.mark_stop()
+    clk = clocks.stop()
+    st = codec.device_status()
+    assert st == 0, native.strerror(st)
+    tc = [ev[k][0].elapsed_time(ev[k][1]) for k in range(args.steps)]
+    td = [ev[k][1].elapsed_time(ev[k][2]) for k in range(args.steps)]
+    total_ms = ev[0][0].elapsed_time(ev[-1][2])
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    tc_ms = sum(tc) / len(tc)
+    td_ms = sum(td) / len(td)
+    value = world * raw_bytes * args.steps / (total_ms / 1e3) / GB
+    comp_gbs = raw_bytes / (tc_ms / 1e3) / GB
+    dec_gbs = raw_bytes / (td_ms / 1e3) / GB
+    peak, peak_kind = peaks()
+    alg_bytes = raw_bytes + stream_bytes  # read + write of either kernel
+    dominant = "compress" if tc_ms >= td_ms else "decompress"
+    dom_ms = max(tc_ms, td_ms)
+    key = "%s_u16_w%d_%s_L%d" % (dominant, w, args.variant, L)
+    achieved = alg_bytes / (dom_ms / 1e3) / GB
+
+    e2e = None
+    if not args.no_e2e and rank == 0:
+        e2e = end_to_end(codec, x, n, args.e2e_steps, dev)
+
+    cpu = None
+    if not args.no_cpu_baseline and rank == 0 and world == 1:
+        ev_host = x.view(args.events, -1)[: max(args.cpu_events, min(args.events, 2000))]
+        ev_host = ev_host.cpu().numpy().view(np.uint16)
+        gbs, n_ev, secs, _ = oracle_sample_timing(
+            ev_host.reshape(-1, WORKLOAD["n_gains"] * WORKLOAD["n_time"] * WORKLOAD["n_pixels"]),
+            variant, w, L, fixed_events=args.cpu_events)
+        cpu = {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle",
+               "sample": "first %d events (%.1f MB) of the workload, compress + decompress, %.1f s, "
+                         "single thread" % (n_ev, n_ev * ev_host[0].size * 2 / 1e6, secs)}
+
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u16", "data": "synthetic",
+        "config": {"workload": workload_name(args), "variant": args.variant, "block_len": L,
+                   "word_bits": w, "input_bytes": raw_bytes,
+                   "l2": "inputs (%.2f GB) far larger than L2; no flush" % (raw_bytes / GB)},
+        "compress_gbs": comp_gbs, "decompress_gbs": dec_gbs,
+        "compress_pct_hbm": 100 * comp_gbs / peak, "decompress_pct_hbm": 100 * dec_gbs / peak,
+        "ratio": raw_bytes / stream_bytes, "stream_bytes": stream_bytes,
+        "compress_ms": tc_ms, "decompress_ms": td_ms, "parity": parity,
+        "roofline": {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                     "alg_bytes_per_launch": alg_bytes, "traffic": recorded_traffic(key)},
+        "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 2 * args.steps,
+        "clocks": clk, "wall_s_timed": wall,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def sampled_parity(x, sbuf, stream_bytes, variant, w, L, n_samples=64, seed=0):
+    """Check sampled blocks of the GPU stream against the oracle: table
+    entries and payload words of blocks spread over the whole stream, with
+    payload offsets recomputed from the table by the oracle's word counts."""
+    import numpy as np
+
+    import oracle
+
+    n = x.numel()
+    n_blocks = -(-n // L)
+    table = sbuf[64: 64 + 4 * n_blocks].cpu().numpy().view(np.uint32)
+    vmin = (table & 0xFFFF).astype(np.int64)
+    B = (table >> 16).astype(np.int64) + 1
+    nb = np.full(n_blocks, L, dtype=np.int64)
+    nb[-1] = n - (n_blocks - 1) * L
+    counts = np.zeros(n_blocks, dtype=np.int64)
+    for b_val in np.unique(B):
+        for nb_val in np.unique(nb[B == b_val]):
+            m = (B == b_val) & (nb == nb_val)
+            counts[m] = oracle.pack_count(variant, int(b_val), w, int(nb_val))
+    offs = np.concatenate([[0], np.cumsum(counts)])
+    payload_off = 64 + (4 * n_blocks + 15) // 16 * 16
+    assert payload_off + offs[-1] * (w // 8) == stream_bytes, "stream size differs from the oracle's count"
+    rng = np.random.default_rng(seed)
+    picks = sorted(set([0, n_blocks - 1] + [int(b) for b in rng.integers(0, n_blocks, n_samples)]))
+    wdt = np.uint64 if w == 64 else np.uint32
+    for b in picks:
+        xs = x[b * L: b * L + nb[b]].cpu().numpy().view(np.uint16)
+        lo, hi = int(xs.min()), int(xs.max())
+        assert (vmin[b], B[b]) == (lo, hi - lo + 1), "table entry of block %d" % b
+        want = oracle.pack_block(variant, hi - lo + 1, w, xs.astype(np.uint64) - lo)
+        a = payload_off + offs[b] * (w // 8)
+        got = sbuf[a: a + counts[b] * (w // 8)].cpu().numpy().view(wdt)
+        assert np.array_equal(got.astype(np.uint64), want), "payload of block %d" % b
+    return "ok: %d sampled blocks byte-identical to the oracle, stream size equal" % len(picks)
+
+
+def end_to_end(codec, x, n, steps, dev):
+    """Same round trip through the public API with host buffers: pinned host
+    samples -> H2D -> compress -> D2H of the stream (its exact size) ->
+    decompress -> D2H of the samples, all inside the timed region."""
+    import torch
+
+    host_in = torch.empty(n, dtype=torch.int16, pin_memory=True)
+    host_in.copy_(x.cpu())
+    host_stream = torch.empty(codec.bound(n), dtype=torch.uint8, pin_memory=True)
+    host_out = torch.empty(n, dtype=torch.int16, pin_memory=True)
+    xin = torch.empty_like(x)
+    sbuf = torch.empty(codec.bound(n), dtype=torch.uint8, device=dev)
+    ybuf = torch.empty(n, dtype=torch.int16, device=dev)
+
+    def one():
+        xin.copy_(host_in, non_blocking=True)
+        _, nb = codec.compress(xin, out=sbuf)
+        nbytes = int(nb.item())
+        host_stream[:nbytes].copy_(sbuf[:nbytes], non_blocking=True)
+        codec.decompress(sbuf, nbytes, n, out=ybuf)
+        host_out.copy_(ybuf, non_blocking=True)
+        torch.cuda.synchronize()
+        return nbytes
+
+    one()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    tot_stream = 0
+    for _ in range(steps):
+        tot_stream += one()
+    dt = time.perf_counter() - t0
+    assert torch.equal(host_out, host_in)
+    raw = n * 2
+    return {"value": raw * steps / dt / GB, "unit": "GB/s", "h2d_bytes_per_step": raw,
+            "d2h_bytes_per_step": tot_stream // steps + raw + 8}
+
+
+if __name__ == "__main__":
+    main()

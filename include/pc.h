@@ -1,0 +1,168 @@
+/*
+ * pc.h -- C ABI of the GB300 polynomial compression library (libpc.so).
+ *
+ * Lossless compression of small-range integer samples dominated by white
+ * noise, after Aubert et al., "Polynomial data compression for large-scale
+ * physics experiments" (arXiv:1805.01844):
+ *   - the samples are cut into blocks of block_len consecutive samples
+ *     (Sec. 3.3, blocked compression);
+ *   - each block stores its minimum and its base B = max - min + 1 once
+ *     (Sec. 3.1 and Fig. 2) and packs the offsets v - min as base-B digits
+ *     into 32- or 64-bit words, either
+ *       basic    (Sec. 3.1, Eqs. 1-2): p = max{p : B^p <= 2^w - 1} digits per
+ *                word, first sample in the lowest power, or
+ *       advanced (Sec. 3.2, Eqs. 3-11 and the series after them): the last
+ *                base of a word is split into R_i * R'_i >= B so that one
+ *                sample straddles two consecutive words, first sample in the
+ *                highest power;
+ *   - decompression inverts the packing by repeated division by B.
+ *
+ * Everything runs on the GPU in hand-written sm_103a kernels; there is no CPU
+ * path.  All buffers are owned by the caller, the library allocates nothing
+ * and keeps no state between calls, and all work is ordered on the caller's
+ * CUDA stream.  Entry points return after enqueuing work; the host return
+ * code covers argument checks and launch errors, while conditions found on
+ * the device (a corrupt stream, a wait that ran out) are recorded in the
+ * workspace and read back with pc_last_device_status().  No kernel traps, and
+ * every device-side wait is bounded (about one second).
+ *
+ * STREAM FORMAT, version 1 (all fields little-endian):
+ *   offset 0   header, 64 bytes
+ *              "PCMP" | u16 version = 1 | u8 variant | u8 dtype_bits |
+ *              u8 word_bits | 3 zero bytes | u32 block_len | u64 n_samples |
+ *              u64 n_blocks = ceil(n_samples / block_len) | u64 payload_words |
+ *              24 zero bytes
+ *   offset 64  block table: per block (min, B - 1), each field dtype_bits
+ *              wide, zero-padded to a multiple of 16 bytes.  B - 1 is stored
+ *              because B = 2^dtype_bits does not fit in dtype_bits.
+ *   then       payload: for each block in order, its packed words
+ *              (word_bits each).  A block with B = 1 has no words.
+ *   The word count of a block is a function of (variant, B, word_bits,
+ *   samples in the block) only, so any block can be located from the table
+ *   alone ("readable by part", Sec. 4.3).
+ */
+#ifndef PC_H
+#define PC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PC_OK = 0,
+    PC_ERR_INVALID_ARG = 1,  /* bad parameter, NULL or misaligned pointer, workspace too small */
+    PC_ERR_CAPACITY = 2,     /* output buffer smaller than required */
+    PC_ERR_CORRUPT = 3,      /* the input is not a valid stream */
+    PC_ERR_CUDA = 4,         /* a CUDA launch or copy failed */
+    PC_ERR_TIMEOUT = 5,      /* a bounded device-side wait ran out */
+    PC_ERR_UNSUPPORTED = 6   /* valid parameters outside what the kernels support */
+} pc_status;
+
+/* Compression parameters (also the stream's own header fields). */
+typedef struct {
+    uint32_t variant;    /* 0 = basic (Sec. 3.1, Eq. 2), 1 = advanced (Sec. 3.2) */
+    uint32_t dtype_bits; /* sample width: 16 (uint16) or 32 (uint32) */
+    uint32_t word_bits;  /* packed word width: 32 or 64 (the paper uses 32) */
+    uint32_t block_len;  /* samples per block, 1 .. PC_MAX_BLOCK_LEN (Sec. 3.3) */
+} pc_params;
+
+#define PC_HEADER_BYTES 64u
+#define PC_MAX_BLOCK_LEN 8192u
+#define PC_VARIANT_BASIC 0u
+#define PC_VARIANT_ADVANCED 1u
+
+/* A cudaStream_t passed as an opaque pointer; NULL is the legacy default
+ * stream. */
+typedef void *pc_stream_t;
+
+/* Upper bound on the stream size, in bytes, of n_samples samples compressed
+ * with *params: header + table + every block at its largest word count over
+ * all bases B in [1, 2^dtype_bits] (basic: ceil(n_b / p(2^d)); advanced: at
+ * most ceil((n_b + 1) / p_1(2^d)) words, n_b + 1 when p_1 = 0).  Host only.
+ * Errors: PC_ERR_INVALID_ARG for bad params or NULL max_bytes;
+ * PC_ERR_UNSUPPORTED for block_len > PC_MAX_BLOCK_LEN. */
+pc_status pc_bound(const pc_params *params, uint64_t n_samples, uint64_t *max_bytes);
+
+/* Bytes of device workspace pc_compress / pc_decompress need for streams of
+ * at most n_samples samples with *params (a few status words plus 8 bytes per
+ * tile of blocks).  Host only.  Errors as for pc_bound. */
+pc_status pc_workspace_size(const pc_params *params, uint64_t n_samples, uint64_t *bytes);
+
+/* Compress n_samples samples (uint16 or uint32 per params->dtype_bits) from
+ * device memory d_in into a version-1 stream at device memory d_out.
+ *   d_in           device pointer, 16-byte aligned (may be NULL if n_samples = 0)
+ *   d_out          device pointer, 16-byte aligned, out_capacity bytes; must be
+ *                  at least pc_bound(params, n_samples) (else PC_ERR_CAPACITY)
+ *   d_out_bytes    device pointer to one uint64_t: the stream size, written
+ *                  by the device when the work completes
+ *   d_workspace    device pointer, 16-byte aligned, workspace_bytes >=
+ *                  pc_workspace_size(params, n_samples) (else PC_ERR_INVALID_ARG);
+ *                  cleared by this call, must not be shared with work that
+ *                  overlaps on the GPU
+ *   stream         CUDA stream the work is ordered on
+ * The stream bytes are identical for any launch configuration: each block's
+ * words land at the exclusive prefix sum of the word counts before it, found
+ * in one pass by a decoupled look-back over tiles of blocks.
+ * Device-side status (PC_ERR_TIMEOUT if a look-back wait ran out) is read
+ * with pc_last_device_status(d_workspace, stream). */
+pc_status pc_compress(const void *d_in, uint64_t n_samples, const pc_params *params,
+                      void *d_out, uint64_t out_capacity, uint64_t *d_out_bytes,
+                      void *d_workspace, uint64_t workspace_bytes, pc_stream_t stream);
+
+/* Decompress the stream of in_bytes bytes at device memory d_in into device
+ * memory d_out (uint16 or uint32 samples).
+ *   params         the parameters the stream was written with; the device
+ *                  checks that the header matches them (else PC_ERR_CORRUPT)
+ *   d_in           device pointer, 16-byte aligned
+ *   d_out          device pointer, 16-byte aligned, room for
+ *                  out_capacity_samples samples; a stream with more samples
+ *                  is rejected on the device with PC_ERR_CAPACITY and nothing
+ *                  is written
+ *   d_n_samples    device pointer to one uint64_t: n_samples of the stream,
+ *                  written by the device
+ *   d_workspace    as for pc_compress, sized for out_capacity_samples
+ * Every read stays inside [d_in, d_in + in_bytes).  The device rejects
+ * (PC_ERR_CORRUPT) a bad header, a table entry with min + B - 1 above the
+ * dtype range, a payload shorter than the table implies or a word count that
+ * differs from the header, and any word that is not the image of valid
+ * digits (a value >= B^k, a non-zero padding digit, a re-joined split sample
+ * >= B).  The decoder therefore accepts exactly the streams pc_compress can
+ * produce.  After an error the content of d_out is unspecified.
+ * in_bytes < 64 returns PC_ERR_CORRUPT from the host. */
+pc_status pc_decompress(const void *d_in, uint64_t in_bytes, const pc_params *params,
+                        void *d_out, uint64_t out_capacity_samples, uint64_t *d_n_samples,
+                        void *d_workspace, uint64_t workspace_bytes, pc_stream_t stream);
+
+/* Parse a stream header that the caller has copied to host memory (at least
+ * 64 bytes).  Fills *params and *n_samples.  Host only; PC_ERR_CORRUPT if the
+ * header is not a valid version-1 header. */
+pc_status pc_parse_header(const void *host_header, uint64_t nbytes, pc_params *params,
+                          uint64_t *n_samples);
+
+/* Synchronise `stream` and return the device-side status recorded in the
+ * workspace by the last pc_compress / pc_decompress that used it: PC_OK,
+ * PC_ERR_CORRUPT, PC_ERR_CAPACITY, PC_ERR_INVALID_ARG (workspace too small
+ * for the stream's tiles) or PC_ERR_TIMEOUT.  PC_ERR_CUDA if the
+ * synchronisation or the copy fails. */
+pc_status pc_last_device_status(const void *d_workspace, pc_stream_t stream);
+
+/* Self-test of the bounded device wait used by the look-back: launches one
+ * block that waits on a status word nothing ever sets, with a limit of
+ * limit_us microseconds, and records PC_ERR_TIMEOUT in the workspace when the
+ * wait gives up (read it with pc_last_device_status).  The same wait routine
+ * guards every look-back in pc_compress / pc_decompress.  d_workspace needs
+ * pc_workspace_size(params, 0) bytes for any params. */
+pc_status pc_selftest_bounded_wait(void *d_workspace, uint64_t workspace_bytes,
+                                   uint32_t limit_us, pc_stream_t stream);
+
+/* Static description of an error code. */
+const char *pc_strerror(pc_status status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PC_H */

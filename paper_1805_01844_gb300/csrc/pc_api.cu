@@ -1,0 +1,210 @@
+// pc_api.cu -- host side of the C ABI declared in include/pc.h: argument
+// checks, sizes, workspace clearing and kernel launches.  No allocation, no
+// global state, no synchronisation except in pc_last_device_status.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstring>
+
+#include "pc.h"
+#include "pc_kernels.h"
+
+using namespace pcx;
+
+namespace {
+
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+bool aligned8(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 7u) == 0; }
+
+pc_status check_params(const pc_params *p)
+{
+    if (!p) return PC_ERR_INVALID_ARG;
+    if (p->variant > 1 || (p->dtype_bits != 16 && p->dtype_bits != 32) ||
+        (p->word_bits != 32 && p->word_bits != 64) || p->block_len == 0)
+        return PC_ERR_INVALID_ARG;
+    if (p->block_len > PC_MAX_BLOCK_LEN) return PC_ERR_UNSUPPORTED;
+    return PC_OK;
+}
+
+uint64_t tiles_for(const pc_params *p, uint64_t n)
+{
+    const TileCfg cfg = tile_cfg(p->variant, p->dtype_bits, p->word_bits, p->block_len);
+    return ceil_div(ceil_div(n, p->block_len), cfg.tb);
+}
+
+}  // namespace
+
+extern "C" {
+
+pc_status pc_bound(const pc_params *params, uint64_t n_samples, uint64_t *max_bytes)
+{
+    pc_status st = check_params(params);
+    if (st != PC_OK) return st;
+    if (!max_bytes) return PC_ERR_INVALID_ARG;
+    const uint64_t L = params->block_len;
+    const uint64_t n_blocks = ceil_div(n_samples, L);
+    uint64_t total = PC_HEADER_BYTES + table_bytes(n_blocks, params->dtype_bits);
+    if (n_blocks > 0) {
+        const uint64_t last = n_samples - (n_blocks - 1) * L;
+        const uint64_t wbytes = params->word_bits / 8;
+        total += (n_blocks - 1) * words_bound(params->variant, params->dtype_bits, params->word_bits, L) * wbytes;
+        total += words_bound(params->variant, params->dtype_bits, params->word_bits, last) * wbytes;
+    }
+    *max_bytes = total;
+    return PC_OK;
+}
+
+pc_status pc_workspace_size(const pc_params *params, uint64_t n_samples, uint64_t *bytes)
+{
+    pc_status st = check_params(params);
+    if (st != PC_OK) return st;
+    if (!bytes) return PC_ERR_INVALID_ARG;
+    uint64_t tiles = tiles_for(params, n_samples);
+    if (tiles < 1) tiles = 1;  // room for the self-test's single status word
+    *bytes = sizeof(WsHeader) + 8 * (tiles + 1);
+    return PC_OK;
+}
+
+pc_status pc_compress(const void *d_in, uint64_t n_samples, const pc_params *params, void *d_out,
+                      uint64_t out_capacity, uint64_t *d_out_bytes, void *d_workspace,
+                      uint64_t workspace_bytes, pc_stream_t stream)
+{
+    pc_status st = check_params(params);
+    if (st != PC_OK) return st;
+    if ((!d_in && n_samples) || !d_out || !d_out_bytes || !d_workspace) return PC_ERR_INVALID_ARG;
+    if (!aligned16(d_in) || !aligned16(d_out) || !aligned8(d_out_bytes) || !aligned16(d_workspace))
+        return PC_ERR_INVALID_ARG;
+    if (tiles_for(params, n_samples) >> 31) return PC_ERR_UNSUPPORTED;  // tile tickets are 32-bit
+    uint64_t need = 0, ws_need = 0;
+    pc_bound(params, n_samples, &need);
+    if (out_capacity < need) return PC_ERR_CAPACITY;
+    pc_workspace_size(params, n_samples, &ws_need);
+    if (workspace_bytes < ws_need) return PC_ERR_INVALID_ARG;
+
+    LaunchArgs a{};
+    a.in = d_in;
+    a.n = n_samples;
+    a.L = params->block_len;
+    a.d = params->dtype_bits;
+    a.w = params->word_bits;
+    a.variant = params->variant;
+    a.out = d_out;
+    a.out_count = d_out_bytes;
+    a.ws = static_cast<WsHeader *>(d_workspace);
+    a.status = reinterpret_cast<uint64_t *>(static_cast<uint8_t *>(d_workspace) + sizeof(WsHeader));
+    a.n_blocks = ceil_div(n_samples, params->block_len);
+    a.n_tiles = tiles_for(params, n_samples);
+    a.ws_tiles = (workspace_bytes - sizeof(WsHeader)) / 8;
+    a.limit_ns = kWaitLimitNs;
+    a.stream = static_cast<cudaStream_t>(stream);
+    const uint64_t clear = sizeof(WsHeader) + 8 * a.n_tiles;
+    if (cudaMemsetAsync(d_workspace, 0, clear, a.stream) != cudaSuccess) return PC_ERR_CUDA;
+    if (launch_compress(a) != cudaSuccess) return PC_ERR_CUDA;
+    return PC_OK;
+}
+
+pc_status pc_decompress(const void *d_in, uint64_t in_bytes, const pc_params *params, void *d_out,
+                        uint64_t out_capacity_samples, uint64_t *d_n_samples, void *d_workspace,
+                        uint64_t workspace_bytes, pc_stream_t stream)
+{
+    pc_status st = check_params(params);
+    if (st != PC_OK) return st;
+    if (!d_in || (!d_out && out_capacity_samples) || !d_n_samples || !d_workspace) return PC_ERR_INVALID_ARG;
+    if (!aligned16(d_in) || !aligned16(d_out) || !aligned8(d_n_samples) || !aligned16(d_workspace))
+        return PC_ERR_INVALID_ARG;
+    if (in_bytes < PC_HEADER_BYTES) return PC_ERR_CORRUPT;
+    if (workspace_bytes < sizeof(WsHeader) + 16) return PC_ERR_INVALID_ARG;
+
+    LaunchArgs a{};
+    a.in = d_in;
+    a.in_bytes = in_bytes;
+    a.L = params->block_len;
+    a.d = params->dtype_bits;
+    a.w = params->word_bits;
+    a.variant = params->variant;
+    a.out = d_out;
+    a.cap = out_capacity_samples;
+    a.out_count = d_n_samples;
+    a.ws = static_cast<WsHeader *>(d_workspace);
+    a.status = reinterpret_cast<uint64_t *>(static_cast<uint8_t *>(d_workspace) + sizeof(WsHeader));
+    a.ws_tiles = (workspace_bytes - sizeof(WsHeader)) / 8;
+    a.limit_ns = kWaitLimitNs;
+    a.stream = static_cast<cudaStream_t>(stream);
+    // clear as many status words as a stream of out_capacity_samples can use
+    uint64_t tiles = tiles_for(params, out_capacity_samples);
+    if (tiles > a.ws_tiles) tiles = a.ws_tiles;
+    a.ws_tiles = tiles < 1 ? 1 : tiles;
+    const uint64_t clear = sizeof(WsHeader) + 8 * a.ws_tiles;
+    if (cudaMemsetAsync(d_workspace, 0, clear, a.stream) != cudaSuccess) return PC_ERR_CUDA;
+    if (launch_decompress(a) != cudaSuccess) return PC_ERR_CUDA;
+    return PC_OK;
+}
+
+pc_status pc_parse_header(const void *host_header, uint64_t nbytes, pc_params *params, uint64_t *n_samples)
+{
+    if (!host_header || !params || !n_samples) return PC_ERR_INVALID_ARG;
+    if (nbytes < PC_HEADER_BYTES) return PC_ERR_CORRUPT;
+    const uint8_t *h = static_cast<const uint8_t *>(host_header);
+    auto le = [&](unsigned off, unsigned k) {
+        uint64_t v = 0;
+        for (unsigned i = 0; i < k; ++i) v |= (uint64_t)h[off + i] << (8 * i);
+        return v;
+    };
+    if (std::memcmp(h, "PCMP", 4) != 0 || le(4, 2) != 1) return PC_ERR_CORRUPT;
+    for (unsigned i = 9; i < 12; ++i)
+        if (h[i]) return PC_ERR_CORRUPT;
+    for (unsigned i = 40; i < 64; ++i)
+        if (h[i]) return PC_ERR_CORRUPT;
+    pc_params p;
+    p.variant = h[6];
+    p.dtype_bits = h[7];
+    p.word_bits = h[8];
+    p.block_len = (uint32_t)le(12, 4);
+    const uint64_t n = le(16, 8), nb = le(24, 8);
+    if (check_params(&p) == PC_ERR_INVALID_ARG) return PC_ERR_CORRUPT;
+    if (nb != n / p.block_len + (n % p.block_len != 0)) return PC_ERR_CORRUPT;
+    *params = p;
+    *n_samples = n;
+    return PC_OK;
+}
+
+pc_status pc_last_device_status(const void *d_workspace, pc_stream_t stream)
+{
+    if (!d_workspace) return PC_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return PC_ERR_CUDA;
+    uint32_t code = 0;
+    const WsHeader *ws = static_cast<const WsHeader *>(d_workspace);
+    if (cudaMemcpy(&code, &ws->status, sizeof(code), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return PC_ERR_CUDA;
+    return static_cast<pc_status>(code);
+}
+
+pc_status pc_selftest_bounded_wait(void *d_workspace, uint64_t workspace_bytes, uint32_t limit_us,
+                                   pc_stream_t stream)
+{
+    if (!d_workspace || !aligned16(d_workspace) || workspace_bytes < sizeof(WsHeader) + 16)
+        return PC_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (cudaMemsetAsync(d_workspace, 0, sizeof(WsHeader) + 16, s) != cudaSuccess) return PC_ERR_CUDA;
+    WsHeader *ws = static_cast<WsHeader *>(d_workspace);
+    uint64_t *status = reinterpret_cast<uint64_t *>(static_cast<uint8_t *>(d_workspace) + sizeof(WsHeader));
+    if (launch_selftest_wait(ws, status, (uint64_t)limit_us * 1000ull, s) != cudaSuccess) return PC_ERR_CUDA;
+    return PC_OK;
+}
+
+const char *pc_strerror(pc_status status)
+{
+    switch (status) {
+    case PC_OK: return "ok";
+    case PC_ERR_INVALID_ARG: return "invalid argument";
+    case PC_ERR_CAPACITY: return "output capacity too small";
+    case PC_ERR_CORRUPT: return "corrupt or truncated stream";
+    case PC_ERR_CUDA: return "CUDA error";
+    case PC_ERR_TIMEOUT: return "bounded device wait ran out";
+    case PC_ERR_UNSUPPORTED: return "unsupported parameters";
+    }
+    return "unknown status";
+}
+
+}  // extern "C"

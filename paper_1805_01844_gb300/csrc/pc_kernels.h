@@ -1,0 +1,32 @@
+// pc_kernels.h -- internal interface between the host API (pc_api.cu) and
+// the kernel translation units.  Not installed; no torch or user types.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "pc_common.cuh"
+
+namespace pcx {
+
+struct LaunchArgs {
+    const void *in;        // compress: samples; decompress: stream bytes
+    uint64_t n;            // compress: samples
+    uint64_t in_bytes;     // decompress: stream bytes available
+    uint32_t L, d, w, variant;
+    void *out;             // compress: stream; decompress: samples
+    uint64_t cap;          // decompress: sample capacity
+    uint64_t *out_count;   // compress: stream bytes; decompress: samples
+    WsHeader *ws;
+    uint64_t *status;      // look-back words, ws_tiles of them
+    uint64_t n_blocks, n_tiles, ws_tiles;
+    uint64_t limit_ns;
+    cudaStream_t stream;
+};
+
+cudaError_t launch_compress(const LaunchArgs &a);
+cudaError_t launch_decompress(const LaunchArgs &a);
+cudaError_t launch_selftest_wait(WsHeader *ws, uint64_t *status, uint64_t limit_ns, cudaStream_t stream);
+
+}  // namespace pcx

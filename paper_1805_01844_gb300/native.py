@@ -1,0 +1,130 @@
+"""ctypes binding of libpc.so (include/pc.h): argument marshalling only.
+
+Every step of compression and decompression runs in the library's CUDA
+kernels; this module passes device pointers, sizes and the CUDA stream of
+torch tensors through the C ABI and turns status codes into exceptions.  It
+fails loudly when the library is missing: there is no other code path.
+"""
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libpc.so")
+
+PC_OK, PC_ERR_INVALID_ARG, PC_ERR_CAPACITY, PC_ERR_CORRUPT = 0, 1, 2, 3
+PC_ERR_CUDA, PC_ERR_TIMEOUT, PC_ERR_UNSUPPORTED = 4, 5, 6
+HEADER_BYTES = 64
+MAX_BLOCK_LEN = 8192
+BASIC, ADVANCED = 0, 1
+
+EXPORTS = ("pc_bound", "pc_workspace_size", "pc_compress", "pc_decompress",
+           "pc_parse_header", "pc_last_device_status", "pc_selftest_bounded_wait",
+           "pc_strerror")
+
+
+class PcParams(ctypes.Structure):
+    _fields_ = [("variant", ctypes.c_uint32), ("dtype_bits", ctypes.c_uint32),
+                ("word_bits", ctypes.c_uint32), ("block_len", ctypes.c_uint32)]
+
+    def __repr__(self):
+        return "PcParams(variant=%d, dtype_bits=%d, word_bits=%d, block_len=%d)" % (
+            self.variant, self.dtype_bits, self.word_bits, self.block_len)
+
+
+class PcError(RuntimeError):
+    def __init__(self, code, what):
+        msg = "%s: %s (status %d)" % (what, strerror(code) if _lib else "", code)
+        super().__init__(msg)
+        self.code = code
+
+
+_lib = None
+
+
+def load(path=LIB_PATH):
+    """Load libpc.so (build it with paper_1805_01844_gb300.build.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("libpc.so not found at %s: build it first "
+                           "(python -c 'import __graft_entry__ as g; g.build()')" % path)
+    L = ctypes.CDLL(path)
+    u64, u32, vp = ctypes.c_uint64, ctypes.c_uint32, ctypes.c_void_p
+    pp = ctypes.POINTER(PcParams)
+    u64p = ctypes.POINTER(ctypes.c_uint64)
+    st = ctypes.c_int
+    L.pc_bound.argtypes = [pp, u64, u64p]
+    L.pc_bound.restype = st
+    L.pc_workspace_size.argtypes = [pp, u64, u64p]
+    L.pc_workspace_size.restype = st
+    L.pc_compress.argtypes = [vp, u64, pp, vp, u64, vp, vp, u64, vp]
+    L.pc_compress.restype = st
+    L.pc_decompress.argtypes = [vp, u64, pp, vp, u64, vp, vp, u64, vp]
+    L.pc_decompress.restype = st
+    L.pc_parse_header.argtypes = [vp, u64, pp, u64p]
+    L.pc_parse_header.restype = st
+    L.pc_last_device_status.argtypes = [vp, vp]
+    L.pc_last_device_status.restype = st
+    L.pc_selftest_bounded_wait.argtypes = [vp, u64, u32, vp]
+    L.pc_selftest_bounded_wait.restype = st
+    L.pc_strerror.argtypes = [st]
+    L.pc_strerror.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+def strerror(code):
+    return load().pc_strerror(int(code)).decode()
+
+
+def _check(code, what):
+    if code != PC_OK:
+        raise PcError(code, what)
+
+
+def params(variant=BASIC, dtype_bits=16, word_bits=64, block_len=1024):
+    return PcParams(int(variant), int(dtype_bits), int(word_bits), int(block_len))
+
+
+def bound(p, n_samples):
+    out = ctypes.c_uint64(0)
+    _check(load().pc_bound(ctypes.byref(p), int(n_samples), ctypes.byref(out)), "pc_bound")
+    return int(out.value)
+
+
+def workspace_size(p, n_samples):
+    out = ctypes.c_uint64(0)
+    _check(load().pc_workspace_size(ctypes.byref(p), int(n_samples), ctypes.byref(out)),
+           "pc_workspace_size")
+    return int(out.value)
+
+
+def parse_header(host_bytes):
+    """(PcParams, n_samples) from the first 64 bytes of a stream (host bytes)."""
+    buf = ctypes.create_string_buffer(bytes(host_bytes[:HEADER_BYTES]), HEADER_BYTES)
+    p = PcParams()
+    n = ctypes.c_uint64(0)
+    _check(load().pc_parse_header(buf, len(host_bytes[:HEADER_BYTES]), ctypes.byref(p),
+                                  ctypes.byref(n)), "pc_parse_header")
+    return p, int(n.value)
+
+
+def compress_raw(d_in, n_samples, p, d_out, out_capacity, d_out_bytes, d_ws, ws_bytes, stream):
+    """pc_compress on raw device addresses (ints); returns the host status."""
+    return load().pc_compress(d_in or None, int(n_samples), ctypes.byref(p), d_out,
+                              int(out_capacity), d_out_bytes, d_ws, int(ws_bytes), stream or None)
+
+
+def decompress_raw(d_in, in_bytes, p, d_out, cap_samples, d_n, d_ws, ws_bytes, stream):
+    """pc_decompress on raw device addresses (ints); returns the host status."""
+    return load().pc_decompress(d_in, int(in_bytes), ctypes.byref(p), d_out or None,
+                                int(cap_samples), d_n, d_ws, int(ws_bytes), stream or None)
+
+
+def last_device_status(d_ws, stream):
+    return int(load().pc_last_device_status(d_ws, stream or None))
+
+
+def selftest_bounded_wait(d_ws, ws_bytes, limit_us, stream):
+    return int(load().pc_selftest_bounded_wait(d_ws, int(ws_bytes), int(limit_us), stream or None))

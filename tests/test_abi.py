@@ -1,0 +1,94 @@
+"""Host-side checks of the C ABI (no GPU needed): the library loads, exports
+every entry point include/pc.h declares, and its host-only calls agree with
+the oracle and reject bad arguments before touching the device."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1805_01844_gb300 import build as pcbuild
+from paper_1805_01844_gb300 import datagen, native
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    pcbuild.build()
+    return native.load()
+
+
+def declared_entry_points():
+    src = open(os.path.join(ROOT, "include", "pc.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(pc_[a-z_]+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol(lib):
+    names = declared_entry_points()
+    assert len(names) >= 8
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(names) == set(native.EXPORTS)
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("d", [16, 32])
+@pytest.mark.parametrize("w", [32, 64])
+def test_bound_matches_oracle(lib, variant, d, w):
+    for L in (1, 7, 154, 1024, 4096, 8192):
+        for n in (0, 1, L - 1, L, L + 1, 10 * L + 3, 123457):
+            if n < 0:
+                continue
+            p = native.params(variant, d, w, L)
+            assert native.bound(p, n) == oracle.bound(variant, d, w, L, n), (L, n)
+
+
+def test_parse_header_of_oracle_streams(lib):
+    x = datagen.white_noise(5000, seed=1)
+    for variant in (0, 1):
+        for w in (32, 64):
+            s = oracle.compress(x, variant, w, 333)
+            p, n = native.parse_header(s)
+            assert (p.variant, p.dtype_bits, p.word_bits, p.block_len, n) == (variant, 16, w, 333, 5000)
+    bad = bytearray(oracle.compress(x, 0, 64, 100))
+    bad[3] = ord("X")
+    with pytest.raises(native.PcError) as e:
+        native.parse_header(bytes(bad))
+    assert e.value.code == native.PC_ERR_CORRUPT
+
+
+def test_argument_checks_happen_on_the_host(lib):
+    """Bad parameters, NULL or misaligned pointers and a short output buffer
+    are rejected before any CUDA call (so this runs without a GPU)."""
+    good = native.params(0, 16, 64, 1024)
+    fake = 1 << 40  # a 16-byte aligned address that is never dereferenced
+    ws = native.workspace_size(good, 4096)
+    cap = native.bound(good, 4096)
+    cases = [
+        (native.params(2, 16, 64, 1024), fake, fake, cap, fake, native.PC_ERR_INVALID_ARG),
+        (native.params(0, 8, 64, 1024), fake, fake, cap, fake, native.PC_ERR_INVALID_ARG),
+        (native.params(0, 16, 48, 1024), fake, fake, cap, fake, native.PC_ERR_INVALID_ARG),
+        (native.params(0, 16, 64, 0), fake, fake, cap, fake, native.PC_ERR_INVALID_ARG),
+        (native.params(0, 16, 64, 8193), fake, fake, cap, fake, native.PC_ERR_UNSUPPORTED),
+        (good, fake + 2, fake, cap, fake, native.PC_ERR_INVALID_ARG),
+        (good, fake, fake + 8, cap, fake, native.PC_ERR_INVALID_ARG),
+        (good, fake, fake, cap, fake + 4, native.PC_ERR_INVALID_ARG),
+        (good, fake, fake, cap - 1, fake, native.PC_ERR_CAPACITY),
+        (good, None, fake, cap, fake, native.PC_ERR_INVALID_ARG),
+    ]
+    for p, d_in, d_out, c, d_ws, want in cases:
+        st = native.compress_raw(d_in, 4096, p, d_out, c, fake, d_ws, ws, None)
+        assert st == want, (p, want, st)
+    assert native.compress_raw(fake, 4096, good, fake, cap, fake, fake, ws - 1, None) == native.PC_ERR_INVALID_ARG
+    # decompress: a stream shorter than its header is corrupt without looking
+    assert native.decompress_raw(fake, 63, good, fake, 10, fake, fake, ws, None) == native.PC_ERR_CORRUPT
+    assert native.decompress_raw(fake, 640, good, fake + 1, 10, fake, fake, ws, None) == native.PC_ERR_INVALID_ARG
+
+
+def test_strerror(lib):
+    for code in range(7):
+        assert native.strerror(code)
