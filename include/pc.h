@@ -158,6 +158,31 @@ pc_status pc_last_device_status(const void *d_workspace, pc_stream_t stream);
 pc_status pc_selftest_bounded_wait(void *d_workspace, uint64_t workspace_bytes,
                                    uint32_t limit_us, pc_stream_t stream);
 
+/* Compression without any device allocation, for callers that cannot
+ * allocate device memory once they run: a data-acquisition loop that must not
+ * call cudaMalloc mid-readout (it can fail under memory pressure or
+ * synchronise the device), or code inside a framework that owns the device
+ * allocator.  The paper has no counterpart; it is an interface of this
+ * library.  Same arguments, checks and output as pc_compress, but the
+ * workspace is a static device array of PC_NOALLOC_SCRATCH_BYTES bytes inside
+ * libpc.so, held by every GPU that loads the library until the process exits.
+ *   - n_samples whose pc_workspace_size exceeds PC_NOALLOC_SCRATCH_BYTES is
+ *     rejected with PC_ERR_UNSUPPORTED (1 MiB: about 131,000 tiles, e.g.
+ *     4.29e9 uint16 samples with block_len 1024, basic variant);
+ *   - the first call on a device looks up the array's device address with
+ *     cudaGetSymbolAddress (with that device current); make that first call
+ *     before any stream capture;
+ *   - every call on a device shares the array: calls that overlap on the GPU
+ *     race and must be serialised by the caller (same stream, or events);
+ *   - the device-side status lives in the shared array and is not readable;
+ *     a bounded look-back wait that ran out leaves *d_out_bytes unwritten, so
+ *     set it to 0 before the call to detect that.
+ * Calls no cudaMalloc, cudaFree or other allocating routine. */
+#define PC_NOALLOC_SCRATCH_BYTES (1u << 20)
+pc_status pc_compress_noalloc(const void *d_in, uint64_t n_samples, const pc_params *params,
+                              void *d_out, uint64_t out_capacity, uint64_t *d_out_bytes,
+                              pc_stream_t stream);
+
 /* Static description of an error code. */
 const char *pc_strerror(pc_status status);
 

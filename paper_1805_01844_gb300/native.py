@@ -19,7 +19,8 @@ BASIC, ADVANCED = 0, 1
 
 EXPORTS = ("pc_bound", "pc_workspace_size", "pc_compress", "pc_decompress",
            "pc_parse_header", "pc_last_device_status", "pc_selftest_bounded_wait",
-           "pc_strerror")
+           "pc_strerror", "pc_compress_noalloc")
+NOALLOC_SCRATCH_BYTES = 1 << 20
 
 
 class PcParams(ctypes.Structure):
@@ -68,6 +69,8 @@ def load(path=LIB_PATH):
     L.pc_last_device_status.restype = st
     L.pc_selftest_bounded_wait.argtypes = [vp, u64, u32, vp]
     L.pc_selftest_bounded_wait.restype = st
+    L.pc_compress_noalloc.argtypes = [vp, u64, pp, vp, u64, vp, vp]
+    L.pc_compress_noalloc.restype = st
     L.pc_strerror.argtypes = [st]
     L.pc_strerror.restype = ctypes.c_char_p
     _lib = L
@@ -128,3 +131,10 @@ def last_device_status(d_ws, stream):
 
 def selftest_bounded_wait(d_ws, ws_bytes, limit_us, stream):
     return int(load().pc_selftest_bounded_wait(d_ws, int(ws_bytes), int(limit_us), stream or None))
+
+
+def compress_noalloc_raw(d_in, n_samples, p, d_out, out_capacity, d_out_bytes, stream):
+    """pc_compress_noalloc on raw device addresses: no workspace argument, the
+    library's static scratch is used.  Returns the host status."""
+    return load().pc_compress_noalloc(d_in or None, int(n_samples), ctypes.byref(p), d_out,
+                                      int(out_capacity), d_out_bytes, stream or None)
