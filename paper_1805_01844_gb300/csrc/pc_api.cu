@@ -26,10 +26,34 @@ pc_status check_params(const pc_params *p)
     return PC_OK;
 }
 
-uint64_t tiles_for(const pc_params *p, uint64_t n)
+WsLayout layout_for(const pc_params *p, uint64_t n, bool orbit)
 {
-    const TileCfg cfg = tile_cfg(p->variant, p->dtype_bits, p->word_bits, p->block_len);
-    return ceil_div(ceil_div(n, p->block_len), cfg.tb);
+    return ws_layout(p->variant, p->dtype_bits, p->word_bits, p->block_len, n, orbit);
+}
+
+// The workspace decides the advanced variant's mode: with room for the series
+// table (pc_workspace_size) the table is used; with only the look-back words
+// and offsets, each block walks its series.  false if it is too small.
+bool pick_layout(const pc_params *p, uint64_t n, uint64_t workspace_bytes, WsLayout &lay)
+{
+    lay = layout_for(p, n, true);
+    if (workspace_bytes >= lay.bytes) return true;
+    lay = layout_for(p, n, false);
+    return workspace_bytes >= lay.bytes;
+}
+
+void fill_workspace(LaunchArgs &a, void *d_workspace, const WsLayout &lay)
+{
+    uint8_t *base = static_cast<uint8_t *>(d_workspace);
+    a.ws = reinterpret_cast<WsHeader *>(base);
+    a.status = reinterpret_cast<uint64_t *>(base + lay.off_status);
+    a.n_status = lay.n_status;
+    a.offsets = reinterpret_cast<uint64_t *>(base + lay.off_offsets);
+    a.n_offsets = lay.n_offsets;
+    a.orbit = lay.orbit;
+    a.orb_flags = lay.orbit ? reinterpret_cast<uint32_t *>(base + lay.off_flags) : nullptr;
+    a.orb_hdr = lay.orbit ? reinterpret_cast<uint64_t *>(base + lay.off_hdr) : nullptr;
+    a.orb_slots = lay.orbit ? static_cast<void *>(base + lay.off_slots) : nullptr;
 }
 
 }  // namespace
@@ -59,9 +83,7 @@ pc_status pc_workspace_size(const pc_params *params, uint64_t n_samples, uint64_
     pc_status st = check_params(params);
     if (st != PC_OK) return st;
     if (!bytes) return PC_ERR_INVALID_ARG;
-    uint64_t tiles = tiles_for(params, n_samples);
-    if (tiles < 1) tiles = 1;  // room for the self-test's single status word
-    *bytes = sizeof(WsHeader) + 8 * (tiles + 1);
+    *bytes = layout_for(params, n_samples, true).bytes;
     return PC_OK;
 }
 
@@ -74,12 +96,17 @@ pc_status pc_compress(const void *d_in, uint64_t n_samples, const pc_params *par
     if ((!d_in && n_samples) || !d_out || !d_out_bytes || !d_workspace) return PC_ERR_INVALID_ARG;
     if (!aligned16(d_in) || !aligned16(d_out) || !aligned8(d_out_bytes) || !aligned16(d_workspace))
         return PC_ERR_INVALID_ARG;
-    if (tiles_for(params, n_samples) >> 31) return PC_ERR_UNSUPPORTED;  // tile tickets are 32-bit
-    uint64_t need = 0, ws_need = 0;
+    WsLayout lay;
+    const bool fits = pick_layout(params, n_samples, workspace_bytes, lay);
+    const uint64_t n_blocks = ceil_div(n_samples, params->block_len);
+    const TileCfg cfg = tile_cfg(kKernelCompress, params->variant, params->dtype_bits, params->word_bits,
+                                 params->block_len, lay.orbit);
+    const uint64_t n_tiles = ceil_div(n_blocks, cfg.tb);
+    if (n_tiles >> 31) return PC_ERR_UNSUPPORTED;  // tile tickets are 32-bit
+    uint64_t need = 0;
     pc_bound(params, n_samples, &need);
     if (out_capacity < need) return PC_ERR_CAPACITY;
-    pc_workspace_size(params, n_samples, &ws_need);
-    if (workspace_bytes < ws_need) return PC_ERR_INVALID_ARG;
+    if (!fits) return PC_ERR_INVALID_ARG;
 
     LaunchArgs a{};
     a.in = d_in;
@@ -90,15 +117,12 @@ pc_status pc_compress(const void *d_in, uint64_t n_samples, const pc_params *par
     a.variant = params->variant;
     a.out = d_out;
     a.out_count = d_out_bytes;
-    a.ws = static_cast<WsHeader *>(d_workspace);
-    a.status = reinterpret_cast<uint64_t *>(static_cast<uint8_t *>(d_workspace) + sizeof(WsHeader));
-    a.n_blocks = ceil_div(n_samples, params->block_len);
-    a.n_tiles = tiles_for(params, n_samples);
-    a.ws_tiles = (workspace_bytes - sizeof(WsHeader)) / 8;
+    fill_workspace(a, d_workspace, lay);
+    a.n_blocks = n_blocks;
+    a.n_tiles = n_tiles;
     a.limit_ns = kWaitLimitNs;
     a.stream = static_cast<cudaStream_t>(stream);
-    const uint64_t clear = sizeof(WsHeader) + 8 * a.n_tiles;
-    if (cudaMemsetAsync(d_workspace, 0, clear, a.stream) != cudaSuccess) return PC_ERR_CUDA;
+    if (cudaMemsetAsync(d_workspace, 0, lay.clear_bytes, a.stream) != cudaSuccess) return PC_ERR_CUDA;
     if (launch_compress(a) != cudaSuccess) return PC_ERR_CUDA;
     return PC_OK;
 }
@@ -113,7 +137,10 @@ pc_status pc_decompress(const void *d_in, uint64_t in_bytes, const pc_params *pa
     if (!aligned16(d_in) || !aligned16(d_out) || !aligned8(d_n_samples) || !aligned16(d_workspace))
         return PC_ERR_INVALID_ARG;
     if (in_bytes < PC_HEADER_BYTES) return PC_ERR_CORRUPT;
-    if (workspace_bytes < sizeof(WsHeader) + 16) return PC_ERR_INVALID_ARG;
+    // the workspace holds the look-back words and the decoding-tile offsets of
+    // a stream of up to out_capacity_samples samples (and the series table)
+    WsLayout lay;
+    if (!pick_layout(params, out_capacity_samples, workspace_bytes, lay)) return PC_ERR_INVALID_ARG;
 
     LaunchArgs a{};
     a.in = d_in;
@@ -125,17 +152,11 @@ pc_status pc_decompress(const void *d_in, uint64_t in_bytes, const pc_params *pa
     a.out = d_out;
     a.cap = out_capacity_samples;
     a.out_count = d_n_samples;
-    a.ws = static_cast<WsHeader *>(d_workspace);
-    a.status = reinterpret_cast<uint64_t *>(static_cast<uint8_t *>(d_workspace) + sizeof(WsHeader));
-    a.ws_tiles = (workspace_bytes - sizeof(WsHeader)) / 8;
+    fill_workspace(a, d_workspace, lay);
     a.limit_ns = kWaitLimitNs;
     a.stream = static_cast<cudaStream_t>(stream);
-    // clear as many status words as a stream of out_capacity_samples can use
-    uint64_t tiles = tiles_for(params, out_capacity_samples);
-    if (tiles > a.ws_tiles) tiles = a.ws_tiles;
-    a.ws_tiles = tiles < 1 ? 1 : tiles;
-    const uint64_t clear = sizeof(WsHeader) + 8 * a.ws_tiles;
-    if (cudaMemsetAsync(d_workspace, 0, clear, a.stream) != cudaSuccess) return PC_ERR_CUDA;
+    // header, table flags, look-back words: cleared; offsets are written before they are read
+    if (cudaMemsetAsync(d_workspace, 0, lay.clear_bytes, a.stream) != cudaSuccess) return PC_ERR_CUDA;
     if (launch_decompress(a) != cudaSuccess) return PC_ERR_CUDA;
     return PC_OK;
 }

@@ -26,6 +26,18 @@ constexpr uint32_t kWarps = kThreads / 32;
 constexpr uint32_t kPad = 64;           // > largest digit count per word (63, B = 2, w = 64)
 constexpr uint32_t kMaxTileBlocks = 32;  // one look-back / chain-walk lane per block
 constexpr uint64_t kWaitLimitNs = 1000000000ull;  // bounded device waits: 1 s
+#ifndef PCX_TILE_BUDGET_BASIC
+#define PCX_TILE_BUDGET_BASIC (72u * 1024u)
+#endif
+#ifndef PCX_TILE_BUDGET_ADVANCED
+#define PCX_TILE_BUDGET_ADVANCED (100u * 1024u)
+#endif
+#ifndef PCX_COMPRESS_SLOTS
+#define PCX_COMPRESS_SLOTS 1
+#endif
+// shared memory a tile may use; sets the blocks per tile
+constexpr uint32_t kTileBudgetBasic = PCX_TILE_BUDGET_BASIC;
+constexpr uint32_t kTileBudgetAdvanced = PCX_TILE_BUDGET_ADVANCED;
 
 // Workspace: this 64-byte header, then one 64-bit look-back status word per
 // tile.  A status word is (flag << 62) | value with flag 0 = not ready,
@@ -34,7 +46,7 @@ struct WsHeader {
     uint32_t ticket;    // next tile to hand out (tiles are taken in order)
     uint32_t status;    // first device-side error, a pc_status; 0 = none
     uint32_t timeouts;  // bounded waits that ran out
-    uint32_t reserved0;
+    uint32_t orbit_cursor;  // next free slot of the series table (advanced)
     uint64_t reserved[6];
 };
 static_assert(sizeof(WsHeader) == 64, "workspace header is 64 bytes");
@@ -104,10 +116,12 @@ struct TileCfg {
     uint32_t tb;          // blocks per tile
     uint32_t S;           // staged samples per block (block_len + kPad)
     uint32_t stage_bytes; // bytes per staged block (multiple of 16)
+    uint32_t slots;       // tiles in flight per CTA (2: one loads while the other is packed)
     uint32_t wcap;        // schedule entries per block (advanced), else 0
-    uint32_t off_sched;   // u64 [tb][wcap]: R | p << 32 | q << 40
-    uint32_t off_tops;    // u32 [tb][wcap]: decoded high parts r'_{i-1}
-    uint32_t off_blk;     // per-block scalars, see BlockVars
+    uint32_t slot_bytes;  // bytes of one slot
+    uint32_t off_sched;   // within a slot: u64 [tb][wcap]: R | p << 32 | q << 40
+    uint32_t off_tops;    // within a slot: u32 [tb][wcap]: decoded high parts r'_{i-1}
+    uint32_t off_blk;     // within a slot: per-block scalars, see BlockVars
     uint32_t smem;        // total dynamic shared memory
 };
 
@@ -117,21 +131,56 @@ struct BlockVars {        // per-tile arrays in shared memory
     uint32_t W[kMaxTileBlocks];
     uint32_t woff[kMaxTileBlocks];
     uint32_t p[kMaxTileBlocks];
+    // decoding only: per-block division constants (see k_decode)
+    uint64_t Dh[kMaxTileBlocks];   // B^h*, the largest power of B <= 2^32
+    uint64_t MD[kMaxTileBlocks];   // floor((2^64 - 1) / Dh)
+    uint32_t mg_m[kMaxTileBlocks]; // magic reciprocal of B (Magic32)
+    uint32_t mg_a[kMaxTileBlocks];
+    uint32_t mg_s[kMaxTileBlocks];
+    uint32_t hstar[kMaxTileBlocks];
+    // compression only: vmin * (1 + B + ... + B^(p-1)) mod 2^w (see basic_word);
+    // advanced: K for p = p_1, K2 for p = p_1 - 1
+    uint64_t K[kMaxTileBlocks];
+    uint64_t K2[kMaxTileBlocks];
+    // advanced: per-block view of the series table (mode 1) or serial walk (mode 0)
+    uint32_t mode[kMaxTileBlocks];
+    uint32_t p1[kMaxTileBlocks];
+    uint32_t orb_off[kMaxTileBlocks];
+    uint32_t orb_Q[kMaxTileBlocks];
+    uint32_t orb_P[kMaxTileBlocks];
+    uint32_t orb_SQ[kMaxTileBlocks];
+    uint32_t orb_G[kMaxTileBlocks];
+    uint32_t orb_mgm[kMaxTileBlocks];
+    uint32_t orb_mga[kMaxTileBlocks];
+    uint32_t orb_mgs[kMaxTileBlocks];
     uint64_t excl;        // payload words before this tile
-    uint32_t tile;
+    uint64_t tile;        // tile index, >= n_tiles when the slot is empty
+    uint32_t agg;         // payload words of this tile
     uint32_t ok;
     uint32_t bad;
-    uint32_t pad_[3];
+    uint32_t pad_;
 };
 
-PCX_HD TileCfg tile_cfg(uint32_t variant, uint32_t d, uint32_t w, uint32_t L)
+enum : uint32_t { kKernelCompress = 0, kKernelDecode = 1 };
+
+// Tile of the compression kernel (kind 0) or of the decoding kernel (kind 1).
+// Compression keeps two tiles in flight per CTA when a block is a whole
+// number of 16-byte vectors (asynchronous copies need 16-byte granules) and
+// two blocks' slots fit the budget.
+PCX_HD TileCfg tile_cfg(uint32_t kind, uint32_t variant, uint32_t d, uint32_t w, uint32_t L, bool orbit)
 {
     TileCfg c;
     c.S = L + kPad;
     c.stage_bytes = (uint32_t)round_up((uint64_t)c.S * (d / 8), 16);
-    c.wcap = variant == PC_VARIANT_ADVANCED ? (uint32_t)words_bound(variant, d, w, L) : 0u;
-    uint32_t per_block = c.stage_bytes + c.wcap * 12u;
-    uint32_t budget = variant == PC_VARIANT_ADVANCED ? 96u * 1024u : 64u * 1024u;
+    // the serial walk keeps a block's schedule in shared memory; with the series
+    // table, 16-bit data never walks (every base is <= 65536)
+    const bool walk = variant == PC_VARIANT_ADVANCED && !(orbit && d == 16);
+    c.wcap = walk ? (uint32_t)words_bound(variant, d, w, L) : 0u;
+    const uint32_t budget = variant == PC_VARIANT_ADVANCED ? kTileBudgetAdvanced : kTileBudgetBasic;
+    const uint32_t one = c.stage_bytes + c.wcap * 12u;
+    c.slots = (PCX_COMPRESS_SLOTS == 2 && kind == kKernelCompress && (L * (d / 8)) % 16 == 0 &&
+               2u * one <= budget) ? 2u : 1u;
+    const uint32_t per_block = c.slots * one;
     uint32_t tb = budget / per_block;
     if (tb < 1) tb = 1;
     if (tb > kMaxTileBlocks) tb = kMaxTileBlocks;
@@ -145,8 +194,49 @@ PCX_HD TileCfg tile_cfg(uint32_t variant, uint32_t d, uint32_t w, uint32_t L)
     off = (uint32_t)round_up(off, 16);
     c.off_blk = off;
     off += (uint32_t)sizeof(BlockVars);
-    c.smem = (uint32_t)round_up(off, 16);
+    c.slot_bytes = (uint32_t)round_up(off, 16);
+    c.smem = c.slots * c.slot_bytes;
     return c;
+}
+
+// Blocks per tile of the decompression offsets kernel (one thread per block).
+constexpr uint32_t kOffsetTileBlocks = kThreads;
+
+// Workspace layout: the header; the flags of the series table (advanced with
+// the table); the look-back words; the decoding-tile offsets plus the total
+// (decompression); the headers and slots of the series table.  The header,
+// the flags and the look-back words are cleared by every call.
+constexpr uint64_t kOrbitFlagsBytes = 262160;     // (65536 + 1) u32, padded to 16
+constexpr uint64_t kOrbitHdrBytes = 524304;       // (65536 + 1) u64, padded to 16
+constexpr uint64_t kOrbitSlotBytes = 16ull << 20; // 2^20 slots of 16 bytes
+
+struct WsLayout {
+    uint64_t n_status;     // look-back words
+    uint64_t n_offsets;    // decoding-tile offsets
+    bool orbit;            // series table present
+    uint64_t off_flags, off_status, off_offsets, off_hdr, off_slots;
+    uint64_t clear_bytes;  // bytes cleared per call, from offset 0
+    uint64_t bytes;
+};
+
+PCX_HD WsLayout ws_layout(uint32_t variant, uint32_t d, uint32_t w, uint32_t L, uint64_t n, bool orbit)
+{
+    const uint64_t n_blocks = ceil_div(n, L);
+    WsLayout lay;
+    lay.orbit = orbit && variant == PC_VARIANT_ADVANCED;
+    const uint64_t ctiles = ceil_div(n_blocks, tile_cfg(kKernelCompress, variant, d, w, L, lay.orbit).tb);
+    const uint64_t otiles = ceil_div(n_blocks, kOffsetTileBlocks);
+    const uint64_t dtiles = ceil_div(n_blocks, tile_cfg(kKernelDecode, variant, d, w, L, lay.orbit).tb);
+    lay.n_status = (ctiles > otiles ? ctiles : otiles) + 1;  // + 1: the self-test uses two words
+    lay.n_offsets = dtiles + 1;
+    lay.off_flags = sizeof(WsHeader);
+    lay.off_status = lay.off_flags + (lay.orbit ? kOrbitFlagsBytes : 0);
+    lay.clear_bytes = lay.off_status + 8 * lay.n_status;
+    lay.off_offsets = lay.clear_bytes;
+    lay.off_hdr = round_up(lay.off_offsets + 8 * lay.n_offsets, 16);
+    lay.off_slots = lay.off_hdr + (lay.orbit ? kOrbitHdrBytes : 0);
+    lay.bytes = lay.off_slots + (lay.orbit ? kOrbitSlotBytes : 0);
+    return lay;
 }
 
 PCX_HD uint64_t table_bytes(uint64_t n_blocks, uint32_t d)

@@ -1,20 +1,22 @@
-// pc_decompress.cu -- the decompression kernel (sm_103a).
+// pc_decompress.cu -- the decompression kernels (sm_103a).
 //
-// A persistent grid; each CTA validates the stream header, then takes tiles
-// of blocks in order from an atomic ticket.  Per tile:
-//   1. block table entries -> (min, B) -> word counts (basic: Eq. 1, 2;
-//      advanced: the split-base series of Sec. 3.2, one lane per block);
-//   2. warp scan + decoupled look-back -> payload offset of the tile, checked
-//      against the stream bounds before anything is read;
-//   3. one warp per block, lanes over words: polynomial division of each word
-//      into its digits (Sec. 3.1), with per-block magic reciprocals of B and
-//      of B^h (the largest power <= 2^32) so that the per-digit path has no
-//      division instruction, and validity checks of every word;
-//   4. coalesced 16-byte stores of the tile's samples.
+// Two launches on the caller's stream:
+//   k_offsets  every CTA validates the stream header; one thread per block
+//              turns its table entry (min, B) into a word count (basic: Eq. 1,
+//              2; advanced: the split-base series of Sec. 3.2), and a block
+//              scan plus the bounded decoupled look-back over tiles gives the
+//              payload offset of each decoding tile;
+//   k_decode   round-robin over decoding tiles with no look-back left: one
+//              warp per block, lanes over words; polynomial division of each
+//              word into its digits (Sec. 3.1) with per-block magic
+//              reciprocals of B and of B^h (the largest power <= 2^32), so the
+//              per-digit path has no division instruction, plus validity
+//              checks of every word; coalesced 16-byte stores of the samples.
 #include <cuda_runtime.h>
 
 #include "pc_device.cuh"
 #include "pc_kernels.h"
+#include "pc_orbit.cuh"
 
 namespace pcx {
 
@@ -40,95 +42,300 @@ __device__ __forceinline__ uint64_t divmod_inv64(uint64_t s, uint64_t D, uint64_
     return q;
 }
 
-// Digits of x (< B^k), least significant first, into dst[0..k), plus vmin.
-template <typename T>
-__device__ __forceinline__ void put_digits(T *dst, uint32_t x, uint32_t k, uint32_t B32, Magic32 mg,
-                                           uint32_t vmin)
+// Digits of x (< B^k), least significant first, into dst[0..k), plus vmin;
+// returns the top digit (x div B^(k-1)), which is < B for a valid word.
+// K digits fully unrolled; one indexed branch per call picks K.
+template <typename T, uint32_t K>
+__device__ __forceinline__ uint32_t put_digits_k(T *dst, uint32_t x, uint32_t B32, Magic32 mg, uint32_t vmin)
 {
-    for (uint32_t i = 0; i + 1 < k; ++i) {
+#pragma unroll
+    for (uint32_t i = 0; i + 1 < K; ++i) {
         const uint32_t q = magic_div(x, mg);
         dst[i] = (T)(x - q * B32 + vmin);
         x = q;
     }
-    dst[k - 1] = (T)(x + vmin);
+    dst[K - 1] = (T)(x + vmin);
+    return x;
 }
 
-template <typename T, uint32_t WB, uint32_t VAR>
-__global__ void __launch_bounds__(kThreads)
-k_decompress(const uint8_t *__restrict__ in, uint64_t in_bytes, uint32_t L, T *__restrict__ out,
-             uint64_t cap, uint64_t *__restrict__ n_out, WsHeader *ws, uint64_t *status,
-             uint64_t ws_tiles, uint64_t limit_ns)
+template <typename T>
+__device__ __forceinline__ uint32_t put_digits(T *dst, uint32_t x, uint32_t k, uint32_t B32, Magic32 mg,
+                                               uint32_t vmin)
 {
-    using Word = typename WordT<T, WB>::type;
-    constexpr uint32_t D = sizeof(T) * 8;
-    constexpr uint32_t DB = D / 8, WBY = WB / 8;
+    switch (k) {
+    case 1: dst[0] = (T)(x + vmin); return x;
+    case 2: return put_digits_k<T, 2>(dst, x, B32, mg, vmin);
+    case 3: return put_digits_k<T, 3>(dst, x, B32, mg, vmin);
+    case 4: return put_digits_k<T, 4>(dst, x, B32, mg, vmin);
+    case 5: return put_digits_k<T, 5>(dst, x, B32, mg, vmin);
+    case 6: return put_digits_k<T, 6>(dst, x, B32, mg, vmin);
+    case 7: return put_digits_k<T, 7>(dst, x, B32, mg, vmin);
+    case 8: return put_digits_k<T, 8>(dst, x, B32, mg, vmin);
+    default:
+        for (uint32_t i = 0; i + 1 < k; ++i) {
+            const uint32_t q = magic_div(x, mg);
+            dst[i] = (T)(x - q * B32 + vmin);
+            x = q;
+        }
+        dst[k - 1] = (T)(x + vmin);
+        return x;
+    }
+}
+
+// Advanced words hold their first sample in the highest power, so digits
+// come out last sample first.  rev_exact: x holds exactly k digits; written to
+// last[0], last[-1], ..., last[-(k-1)] (k - 1 divisions, the top one is x).
+// rev_quot: k divisions; the k digits are written the same way and the
+// remaining quotient is returned.
+template <typename T>
+__device__ __forceinline__ void rev_exact(T *last, uint32_t x, uint32_t k, uint32_t B32, Magic32 mg,
+                                          uint32_t vmin)
+{
+    for (uint32_t i = 0; i + 1 < k; ++i) {
+        const uint32_t q = magic_div(x, mg);
+        *(last - i) = (T)(x - q * B32 + vmin);
+        x = q;
+    }
+    *(last - (k - 1)) = (T)(x + vmin);
+}
+
+template <typename T, uint32_t K>
+__device__ __forceinline__ uint32_t rev_quot_k(T *last, uint32_t x, uint32_t B32, Magic32 mg, uint32_t vmin)
+{
+#pragma unroll
+    for (uint32_t i = 0; i < K; ++i) {
+        const uint32_t q = magic_div(x, mg);
+        *(last - i) = (T)(x - q * B32 + vmin);
+        x = q;
+    }
+    return x;
+}
+
+template <typename T>
+__device__ __forceinline__ uint32_t rev_quot(T *last, uint32_t x, uint32_t k, uint32_t B32, Magic32 mg,
+                                             uint32_t vmin)
+{
+    switch (k) {
+    case 0: return x;
+    case 1: return rev_quot_k<T, 1>(last, x, B32, mg, vmin);
+    case 2: return rev_quot_k<T, 2>(last, x, B32, mg, vmin);
+    case 3: return rev_quot_k<T, 3>(last, x, B32, mg, vmin);
+    case 4: return rev_quot_k<T, 4>(last, x, B32, mg, vmin);
+    case 5: return rev_quot_k<T, 5>(last, x, B32, mg, vmin);
+    case 6: return rev_quot_k<T, 6>(last, x, B32, mg, vmin);
+    case 7: return rev_quot_k<T, 7>(last, x, B32, mg, vmin);
+    case 8: return rev_quot_k<T, 8>(last, x, B32, mg, vmin);
+    default:
+        for (uint32_t i = 0; i < k; ++i) {
+            const uint32_t q = magic_div(x, mg);
+            *(last - i) = (T)(x - q * B32 + vmin);
+            x = q;
+        }
+        return x;
+    }
+}
+
+// s = body R + r for R < 2^16 by 16-bit long division with R's magic
+// reciprocal (every partial dividend is < R 2^16 <= 2^32).
+__device__ __forceinline__ uint64_t divmod_small64(uint64_t s, uint32_t R, Magic32 mg, uint32_t &r)
+{
+    uint32_t x = (uint32_t)(s >> 48);
+    const uint32_t q3 = magic_div(x, mg);
+    uint32_t rr = x - q3 * R;
+    x = (rr << 16) | ((uint32_t)(s >> 32) & 0xFFFFu);
+    const uint32_t q2 = magic_div(x, mg);
+    rr = x - q2 * R;
+    x = (rr << 16) | ((uint32_t)(s >> 16) & 0xFFFFu);
+    const uint32_t q1 = magic_div(x, mg);
+    rr = x - q1 * R;
+    x = (rr << 16) | ((uint32_t)s & 0xFFFFu);
+    const uint32_t q0 = magic_div(x, mg);
+    r = x - q0 * R;
+    return ((uint64_t)q3 << 48) | ((uint64_t)q2 << 32) | ((uint64_t)q1 << 16) | q0;
+}
+
+// Header of a stream, validated by every CTA of the offsets kernel against
+// the expected parameters, the buffer size, the output capacity and the
+// workspace.  Returns a pc_status.
+template <typename T, uint32_t WB, uint32_t VAR>
+__device__ uint32_t check_header(const uint8_t *in, uint64_t in_bytes, uint32_t L, uint64_t cap,
+                                 uint64_t status_cap, uint64_t offsets_cap, uint32_t dtb,
+                                 uint64_t &n, uint64_t &nb, uint64_t &pw)
+{
+    constexpr uint32_t D = sizeof(T) * 8, DB = D / 8, WBY = WB / 8;
+    const uint32_t *h = reinterpret_cast<const uint32_t *>(in);
+    const uint64_t *h64 = reinterpret_cast<const uint64_t *>(in);
+    n = h64[2];
+    nb = h64[3];
+    pw = h64[4];
+    if (h[0] != 0x504D4350u || h[1] != (1u | (VAR << 16) | (D << 24)) || h[2] != WB || h[3] != L ||
+        h64[5] != 0 || h64[6] != 0 || h64[7] != 0)
+        return PC_ERR_CORRUPT;
+    if (nb != n / L + (n % L != 0)) return PC_ERR_CORRUPT;
+    if (n > cap) return PC_ERR_CAPACITY;
+    if (nb > (in_bytes - PC_HEADER_BYTES) / (2 * DB)) return PC_ERR_CORRUPT;
+    const uint64_t poff = PC_HEADER_BYTES + table_bytes(nb, D);
+    if (poff > in_bytes || pw > (in_bytes - poff) / WBY) return PC_ERR_CORRUPT;
+    if (ceil_div(nb, kOffsetTileBlocks) > status_cap || ceil_div(nb, dtb) + 1 > offsets_cap)
+        return PC_ERR_INVALID_ARG;
+    return PC_OK;
+}
+
+// Word count of a block from its table entry (basic: Eq. 1-2; advanced: the
+// length of the split-base series of Sec. 3.2).
+template <uint32_t WB, uint32_t VAR, bool ORB>
+__device__ __forceinline__ uint32_t block_words(uint64_t B, uint32_t n_b, const OrbitTable &ot, WsHeader *ws,
+                                                uint64_t limit_ns)
+{
+    if (B <= 1) return 0;
+    if constexpr (VAR == PC_VARIANT_BASIC) {
+        const uint32_t p = basic_p(B, WB);
+        return (n_b + p - 1) / p;
+    } else {
+        if (ORB && B <= kOrbitMaxB) {
+            const uint64_t h = orbit_get<WB>(ot, (uint32_t)B, ws, limit_ns);
+            if (h == ~0ull) return 0;
+            return orbit_words(ot, orbit_view(ot, h), n_b);
+        }
+        return walk_series<WB>(B, n_b, nullptr, 0);
+    }
+}
+
+// Offsets kernel: one thread per block reads its table entry and word count;
+// a block-wide scan and the bounded decoupled look-back over tiles of
+// kOffsetTileBlocks blocks give every block's payload offset, of which the
+// first block of each decoding tile is stored (plus the total).
+template <typename T, uint32_t WB, uint32_t VAR, bool ORB>
+__global__ void __launch_bounds__(kThreads)
+k_offsets(const uint8_t *__restrict__ in, uint64_t in_bytes, uint32_t L, uint64_t cap,
+          uint64_t *__restrict__ n_out, WsHeader *ws, uint64_t *status, uint64_t status_cap,
+          uint64_t *offsets, uint64_t offsets_cap, uint32_t dtb, uint64_t limit_ns, OrbitTable ot)
+{
+    constexpr uint32_t D = sizeof(T) * 8, DB = D / 8;
     constexpr uint64_t kDmax = D == 16 ? 0xFFFFull : 0xFFFFFFFFull;
-    extern __shared__ __align__(16) uint8_t smem[];
-    const TileCfg cfg = tile_cfg(VAR, D, WB, L);
-    BlockVars &bv = *reinterpret_cast<BlockVars *>(smem + cfg.off_blk);
-    uint64_t *sched_all = reinterpret_cast<uint64_t *>(smem + cfg.off_sched);
-    uint32_t *tops_all = reinterpret_cast<uint32_t *>(smem + cfg.off_tops);
-    __shared__ uint64_t hdr[4];  // n, n_blocks, payload_words, error code
+    __shared__ uint64_t hdr[4];
+    __shared__ uint32_t warp_tot[kWarps];
+    __shared__ uint64_t s_excl;
+    __shared__ uint32_t s_tile, s_ok;
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
 
-    // ---- header: every CTA validates it (64 bytes, L2-resident)
     if (threadIdx.x == 0) {
-        const uint32_t *h = reinterpret_cast<const uint32_t *>(in);
-        const uint64_t *h64 = reinterpret_cast<const uint64_t *>(in);
-        uint64_t code = 0;
-        const uint64_t n = h64[2], nb = h64[3], pw = h64[4];
-        if (h[0] != 0x504D4350u || h[1] != (1u | (VAR << 16) | (D << 24)) || h[2] != WB || h[3] != L ||
-            h64[5] != 0 || h64[6] != 0 || h64[7] != 0)
-            code = PC_ERR_CORRUPT;
-        else if (nb != n / L + (n % L != 0))
-            code = PC_ERR_CORRUPT;
-        else if (n > cap)
-            code = PC_ERR_CAPACITY;
-        else if (nb > (in_bytes - PC_HEADER_BYTES) / (2 * DB))
-            code = PC_ERR_CORRUPT;
-        else {
-            const uint64_t poff = PC_HEADER_BYTES + table_bytes(nb, D);
-            if (poff > in_bytes || pw > (in_bytes - poff) / WBY)
-                code = PC_ERR_CORRUPT;
-            else if (ceil_div(nb, cfg.tb) > ws_tiles)
-                code = PC_ERR_INVALID_ARG;
-        }
+        uint64_t n, nb, pw;
+        const uint32_t code = check_header<T, WB, VAR>(in, in_bytes, L, cap, status_cap, offsets_cap, dtb,
+                                                       n, nb, pw);
         hdr[0] = n;
         hdr[1] = nb;
         hdr[2] = pw;
         hdr[3] = code;
     }
     __syncthreads();
-    if (hdr[3] != 0) {
+    if (hdr[3] != PC_OK) {
         if (blockIdx.x == 0 && threadIdx.x == 0) record_error(ws, (uint32_t)hdr[3]);
         return;
     }
     const uint64_t n = hdr[0], n_blocks = hdr[1], payload_words = hdr[2];
-    const uint64_t n_tiles = ceil_div(n_blocks, cfg.tb);
+    const uint64_t n_tiles = ceil_div(n_blocks, kOffsetTileBlocks);
+    const uint64_t n_dtiles = ceil_div(n_blocks, dtb);
     const uint64_t payload_off = PC_HEADER_BYTES + table_bytes(n_blocks, D);
-    const Word *payload = reinterpret_cast<const Word *>(in + payload_off);
     if (n_tiles == 0) {
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             if (payload_words != 0) record_error(ws, PC_ERR_CORRUPT);
+            offsets[0] = 0;
             *n_out = 0;
         }
         return;
     }
 
     for (;;) {
-        if (threadIdx.x == 0) {
-            bv.tile = atomicAdd(&ws->ticket, 1u);
-            bv.bad = 0;
+        if (threadIdx.x == 0) s_tile = atomicAdd(&ws->ticket, 1u);
+        __syncthreads();
+        const uint64_t tile = s_tile;
+        if (tile >= n_tiles) break;
+        const uint64_t b = tile * kOffsetTileBlocks + threadIdx.x;
+        uint32_t W = 0;
+        if (b < n_blocks) {
+            uint64_t vmin, Bm1;
+            if constexpr (D == 16) {
+                const uint32_t e = reinterpret_cast<const uint32_t *>(in + PC_HEADER_BYTES)[b];
+                vmin = e & 0xFFFFu;
+                Bm1 = e >> 16;
+            } else {
+                const uint64_t e = reinterpret_cast<const uint64_t *>(in + PC_HEADER_BYTES)[b];
+                vmin = e & 0xFFFFFFFFull;
+                Bm1 = e >> 32;
+            }
+            if (vmin + Bm1 > kDmax) {
+                record_error(ws, PC_ERR_CORRUPT);
+                Bm1 = 0;
+            }
+            const uint32_t n_b = (uint32_t)umin64(L, n - b * L);
+            W = block_words<WB, VAR, ORB>(Bm1 + 1, n_b, ot, ws, limit_ns);
+        }
+        // block-wide exclusive scan of W
+        const uint32_t incl = warp_incl_scan_u32(W);
+        if (lane == 31) warp_tot[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            const uint32_t t = lane < kWarps ? warp_tot[lane] : 0u;
+            const uint32_t ti = warp_incl_scan_u32(t);
+            if (lane < kWarps) warp_tot[lane] = ti - t;
+            const uint32_t agg = __shfl_sync(0xFFFFFFFFu, ti, 31);
+            uint64_t excl = 0;
+            const bool ok = lookback_warp(status, tile, agg, ws, limit_ns, &excl);
+            if (lane == 0) {
+                s_excl = excl;
+                s_ok = ok ? 1u : 0u;
+            }
         }
         __syncthreads();
-        const uint64_t tile = bv.tile;
-        if (tile >= n_tiles) break;
+        if (s_ok && b < n_blocks) {
+            const uint64_t off = s_excl + warp_tot[warp] + (incl - W);
+            if (b % dtb == 0) offsets[b / dtb] = off;
+            if (b == n_blocks - 1) {
+                const uint64_t total = off + W;
+                offsets[n_dtiles] = total;
+                if (total != payload_words) record_error(ws, PC_ERR_CORRUPT);
+                for (uint64_t o = PC_HEADER_BYTES + n_blocks * 2 * DB; o < payload_off; ++o)
+                    if (in[o] != 0) record_error(ws, PC_ERR_CORRUPT);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Decoding kernel: no look-back left.  Tiles are taken round-robin; per tile
+// the table gives (min, B, W) per block, the offsets kernel the payload
+// offset; one warp per block loads its words four per lane at a time and
+// splits them into digits in shared memory; the tile's samples then leave in
+// coalesced 16-byte streaming stores.
+template <typename T, uint32_t WB, uint32_t VAR, bool ORB>
+__global__ void __launch_bounds__(kThreads, 3)
+k_decode(const uint8_t *__restrict__ in, uint32_t L, T *__restrict__ out, uint64_t *__restrict__ n_out,
+         WsHeader *ws, const uint64_t *__restrict__ offsets, OrbitTable ot, uint64_t limit_ns)
+{
+    using Word = typename WordT<T, WB>::type;
+    constexpr uint32_t D = sizeof(T) * 8;
+    constexpr uint32_t KB = 4;  // words per lane in flight
+    extern __shared__ __align__(16) uint8_t smem[];
+    const TileCfg cfg = tile_cfg(kKernelDecode, VAR, D, WB, L, ORB);
+    BlockVars &bv = *reinterpret_cast<BlockVars *>(smem + cfg.off_blk);
+    uint64_t *sched_all = reinterpret_cast<uint64_t *>(smem + cfg.off_sched);
+    uint32_t *tops_all = reinterpret_cast<uint32_t *>(smem + cfg.off_tops);
+    const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+
+    if (*reinterpret_cast<volatile uint32_t *>(&ws->status) != PC_OK) return;  // the offsets kernel rejected the stream
+    const uint64_t *h64 = reinterpret_cast<const uint64_t *>(in);
+    const uint64_t n = h64[2], n_blocks = h64[3];
+    const uint64_t n_tiles = ceil_div(n_blocks, cfg.tb);
+    const uint64_t payload_off = PC_HEADER_BYTES + table_bytes(n_blocks, D);
+    const Word *payload = reinterpret_cast<const Word *>(in + payload_off);
+
+    for (uint64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
         const uint64_t blk0 = tile * cfg.tb;
         const uint32_t nblk = (uint32_t)umin64(cfg.tb, n_blocks - blk0);
         const uint64_t g0 = blk0 * L;
         const uint64_t cnt = umin64(n - g0, (uint64_t)nblk * L);
-
-        // 1-2. table -> counts -> scan -> look-back -> bounds
+        if (threadIdx.x == 0) bv.bad = 0;
         if (warp == 0) {
             uint32_t W = 0;
             if (lane < nblk) {
@@ -143,23 +350,46 @@ k_decompress(const uint8_t *__restrict__ in, uint64_t in_bytes, uint32_t L, T *_
                     vmin = e & 0xFFFFFFFFull;
                     Bm1 = e >> 32;
                 }
-                if (vmin + Bm1 > kDmax) {
-                    record_error(ws, PC_ERR_CORRUPT);
-                    Bm1 = 0;
-                }
-                const uint64_t B = Bm1 + 1;
+                const uint64_t B = Bm1 + 1;  // entries were range-checked by the offsets kernel
                 const uint32_t n_b = (uint32_t)umin64(L, cnt - (uint64_t)lane * L);
                 if (B > 1) {
+                    // division constants of this block, computed once by its lane
+                    const Magic32 mg = magic32(B);
+                    bv.mg_m[lane] = mg.m;
+                    bv.mg_a[lane] = mg.a;
+                    bv.mg_s[lane] = mg.s;
+                    uint32_t hs = 1;
+                    uint64_t Dh = B;
+                    while (Dh <= (1ull << 32) / B) {
+                        Dh *= B;
+                        ++hs;
+                    }
+                    bv.hstar[lane] = hs;
+                    bv.Dh[lane] = Dh;
+                    bv.MD[lane] = ~0ull / Dh;
                     if constexpr (VAR == PC_VARIANT_BASIC) {
                         const uint32_t p = basic_p(B, WB);
                         bv.p[lane] = p;
                         W = (n_b + p - 1) / p;
+                    } else if (ORB && B <= kOrbitMaxB) {
+                        const uint64_t h = orbit_get<WB>(ot, (uint32_t)B, ws, limit_ns);
+                        if (h != ~0ull) {
+                            const OrbitView v = orbit_view(ot, h);
+                            W = orbit_words(ot, v, n_b);
+                            bv.orb_off[lane] = v.off;
+                            bv.orb_Q[lane] = v.Q;
+                            bv.orb_P[lane] = v.P;
+                            bv.orb_SQ[lane] = v.SQ;
+                            bv.orb_G[lane] = v.G;
+                            bv.orb_mgm[lane] = v.mgP.m;
+                            bv.orb_mga[lane] = v.mgP.a;
+                            bv.orb_mgs[lane] = v.mgP.s;
+                        }
+                        bv.mode[lane] = 1;
                     } else {
                         W = walk_series<WB>(B, n_b, sched_all + (uint64_t)lane * cfg.wcap, cfg.wcap);
-                        if (W == ~0u) {
-                            record_error(ws, PC_ERR_INVALID_ARG);
-                            W = 0;
-                        }
+                        if (W == ~0u) W = 0;  // not reachable: B was range-checked
+                        bv.mode[lane] = 0;
                     }
                 }
                 bv.vmin[lane] = (uint32_t)vmin;
@@ -168,94 +398,170 @@ k_decompress(const uint8_t *__restrict__ in, uint64_t in_bytes, uint32_t L, T *_
             }
             const uint32_t incl = warp_incl_scan_u32(W);
             if (lane < nblk) bv.woff[lane] = incl - W;
-            const uint32_t agg = __shfl_sync(0xFFFFFFFFu, incl, 31);
-            uint64_t excl = 0;
-            bool ok = lookback_warp(status, tile, agg, ws, limit_ns, &excl);
-            if (lane == 0) {
-                const uint64_t end = excl + agg;
-                if (ok && end > payload_words) {  // payload_words fits in in_bytes (header check)
-                    record_error(ws, PC_ERR_CORRUPT);
-                    ok = false;
-                }
-                if (ok && tile == n_tiles - 1) {
-                    if (end != payload_words) record_error(ws, PC_ERR_CORRUPT);
-                    for (uint64_t o = PC_HEADER_BYTES + n_blocks * 2 * DB; o < payload_off; ++o)
-                        if (in[o] != 0) record_error(ws, PC_ERR_CORRUPT);
-                }
-                bv.excl = excl;
-                bv.ok = ok ? 1u : 0u;
-            }
+            if (lane == 0) bv.excl = offsets[tile];
         }
         __syncthreads();
 
-        if (bv.ok) {
-            // 3. decode, one warp per block
-            for (uint32_t b = warp; b < nblk; b += kWarps) {
-                T *u = reinterpret_cast<T *>(smem + (uint64_t)b * cfg.stage_bytes);
-                const uint32_t W = bv.W[b];
-                const uint32_t vmin = bv.vmin[b];
-                const uint64_t B = bv.B[b];
-                const uint32_t n_b = (uint32_t)umin64(L, cnt - (uint64_t)b * L);
-                if (W == 0) {  // B = 1: every sample is the minimum
-                    for (uint32_t i = lane; i < n_b; i += 32) u[i] = (T)vmin;
-                    continue;
-                }
-                const Word *src = payload + bv.excl + bv.woff[b];
-                const uint32_t B32 = (uint32_t)B;
-                bool bad = false;
-                if constexpr (VAR == PC_VARIANT_BASIC) {
-                    const uint32_t p = bv.p[b];
-                    const Magic32 mg = magic32(B);
-                    // B^p bounds every full word; B^k the last (k real digits)
-                    const uint32_t k_last = n_b - (W - 1) * p;
-                    uint64_t lim_full = 1, lim_last = 1;
-                    for (uint32_t i = 0; i < p; ++i) {
-                        if (i < k_last) lim_last *= B;
-                        lim_full *= B;
+        // decode, one warp per block
+        for (uint32_t b = warp; b < nblk; b += kWarps) {
+            T *u = reinterpret_cast<T *>(smem + (uint64_t)b * cfg.stage_bytes);
+            const uint32_t W = bv.W[b];
+            const uint32_t vmin = bv.vmin[b];
+            const uint64_t B = bv.B[b];
+            const uint32_t n_b = (uint32_t)umin64(L, cnt - (uint64_t)b * L);
+            if (W == 0) {  // B = 1: every sample is the minimum
+                for (uint32_t i = lane; i < n_b; i += 32) u[i] = (T)vmin;
+                continue;
+            }
+            const Word *src = payload + bv.excl + bv.woff[b];
+            const uint32_t B32 = (uint32_t)B;
+            bool bad = false;
+            if constexpr (VAR == PC_VARIANT_BASIC) {
+                const uint32_t p = bv.p[b];
+                const Magic32 mg{bv.mg_m[b], bv.mg_a[b], bv.mg_s[b]};
+                const uint32_t hstar = bv.hstar[b];
+                const uint64_t Dh = bv.Dh[b], MD = bv.MD[b];
+                // a full word is valid iff its top digit is < B; the last word's
+                // digits past the block (written to the padding) must be 0
+                for (uint32_t j0 = 0; j0 < W; j0 += 32 * KB) {
+                    Word sv[KB];
+#pragma unroll
+                    for (uint32_t k = 0; k < KB; ++k) {
+                        const uint32_t j = j0 + lane + 32 * k;
+                        sv[k] = j < W ? __ldcs(src + j) : Word(0);
                     }
-                    uint32_t hstar = 1;  // largest h with B^h <= 2^32
-                    uint64_t Dh = B;
-                    while (Dh <= (1ull << 32) / B) {
-                        Dh *= B;
-                        ++hstar;
-                    }
-                    const uint64_t MD = ~0ull / Dh;
-                    for (uint32_t j = lane; j < W; j += 32) {
-                        const uint64_t s = src[j];
-                        bad |= s >= (j == W - 1 ? lim_last : lim_full);
-                        T *dst = u + (uint64_t)j * p;
+#pragma unroll
+                    for (uint32_t k = 0; k < KB; ++k) {
+                        const uint32_t j = j0 + lane + 32 * k;
+                        if (j >= W) break;
+                        const uint64_t s = sv[k];
+                        T *dst = u + j * p;
+                        uint32_t top;
                         if (WB == 32 || p <= hstar) {
-                            put_digits<T>(dst, (uint32_t)s, p, B32, mg, vmin);
+                            top = put_digits<T>(dst, (uint32_t)s, p, B32, mg, vmin);
+                            if (WB == 64) bad |= (s >> 32) != 0;
                         } else {
-                            uint64_t qv = s;
-                            uint32_t rem = p;
-                            while (rem > hstar) {
-                                uint64_t piece;
-                                qv = divmod_inv64(qv, Dh, MD, piece);
-                                put_digits<T>(dst, (uint32_t)piece, hstar, B32, mg, vmin);
+                            uint64_t lo;
+                            uint64_t qv = divmod_inv64(s, Dh, MD, lo);
+                            put_digits<T>(dst, (uint32_t)lo, hstar, B32, mg, vmin);
+                            uint32_t rem = p - hstar;
+                            if (rem > hstar) {  // p = 2 h* + 1: one more piece of h* digits
+                                qv = divmod_inv64(qv, Dh, MD, lo);
+                                put_digits<T>(dst + hstar, (uint32_t)lo, hstar, B32, mg, vmin);
                                 dst += hstar;
                                 rem -= hstar;
                             }
-                            put_digits<T>(dst, (uint32_t)qv, rem, B32, mg, vmin);
+                            bad |= (qv >> 32) != 0;
+                            top = put_digits<T>(dst + hstar, (uint32_t)qv, rem, B32, mg, vmin);
+                        }
+                        bad |= top >= B;
+                    }
+                }
+                // padding digits of the last word must be zero
+                if (lane == 0) {
+                    const uint32_t end = W * p;
+                    for (uint32_t i = n_b; i < end; ++i) bad |= (uint32_t)u[i] != vmin;
+                }
+            } else if (ORB && bv.mode[b]) {
+                // one pass, lanes over consecutive words: word i yields its p_i
+                // whole samples, its low part r_i and the high part r'_{i-1}
+                // that, with r_{i-1} from the lane before, re-joins sample q_i - 1
+                const OrbitView v{bv.orb_off[b], bv.orb_Q[b], bv.orb_P[b], bv.orb_SQ[b], bv.orb_G[b],
+                                  Magic32{bv.orb_mgm[b], bv.orb_mga[b], bv.orb_mgs[b]}};
+                const Magic32 mg{bv.mg_m[b], bv.mg_a[b], bv.mg_s[b]};
+                const uint32_t hstar = bv.hstar[b];
+                const uint64_t Dh = bv.Dh[b], MD = bv.MD[b];
+                uint32_t cR = 1, cr = 0;  // carry: R and r of the word before this chunk
+                uint32_t qlast = 0, plast = 0;
+                for (uint32_t j0 = 0; j0 < W; j0 += 32) {
+                    const uint32_t i = j0 + lane;
+                    const bool valid = i < W;
+                    SeriesEntry e;
+                    uint64_t s = 0;
+                    if (valid) {
+                        e = orbit_entry(ot, v, i);
+                        s = __ldcs(src + i);
+                    } else {
+                        e = SeriesEntry{1u, 0u, 0u, Magic32{0xFFFFFFFFu, 0xFFFFFFFFu, 0u}};
+                    }
+                    uint32_t r = 0;
+                    uint64_t body = 0;
+                    if (valid) {
+                        if constexpr (WB == 32) {
+                            const uint32_t q32 = magic_div((uint32_t)s, e.mgR);
+                            r = (uint32_t)s - q32 * e.R;
+                            body = q32;
+                        } else {
+                            body = divmod_small64(s, e.R, e.mgR, r);
                         }
                     }
-                } else {
-                    const uint64_t *sched = sched_all + (uint64_t)b * cfg.wcap;
-                    uint32_t *tops = tops_all + (uint64_t)b * cfg.wcap;
-                    const uint64_t MB = ~0ull / B;
-                    // phase A: digits, low parts r_i into the split slots, high parts aside
-                    for (uint32_t i = lane; i < W; i += 32) {
+                    uint32_t Rp = __shfl_up_sync(0xFFFFFFFFu, e.R, 1);
+                    uint32_t rp = __shfl_up_sync(0xFFFFFFFFu, r, 1);
+                    if (lane == 0) {
+                        Rp = cR;
+                        rp = cr;
+                    }
+                    cR = __shfl_sync(0xFFFFFFFFu, e.R, 31);
+                    cr = __shfl_sync(0xFFFFFFFFu, r, 31);
+                    if (!valid) continue;
+                    // p_i whole digits, last sample first, then the high part
+                    T *last = u + e.q + e.p - 1;
+                    uint32_t rem = e.p;
+                    while (rem >= hstar && (body >> 32) != 0) {
+                        uint64_t lo;
+                        body = divmod_inv64(body, Dh, MD, lo);
+                        rev_exact<T>(last, (uint32_t)lo, hstar, B32, mg, vmin);
+                        last -= hstar;
+                        rem -= hstar;
+                    }
+                    bad |= (body >> 32) != 0;
+                    const uint32_t top = rev_quot<T>(last, (uint32_t)body, rem, B32, mg, vmin);
+                    if (i == 0) {
+                        bad |= top != 0;
+                    } else {
+                        const uint64_t val = (uint64_t)top * Rp + rp;
+                        bad |= val >= B;
+                        u[e.q - 1] = (T)(val + vmin);
+                    }
+                    if (e.q + e.p >= n_b) bad |= r != 0;  // the split slot is padding
+                    if (i == W - 1) {
+                        qlast = e.q;
+                        plast = e.p;
+                    }
+                }
+                // whole digits past the block (padding) must be zero
+                const uint32_t src_lane = (W - 1) & 31u;
+                qlast = __shfl_sync(0xFFFFFFFFu, qlast, src_lane);
+                plast = __shfl_sync(0xFFFFFFFFu, plast, src_lane);
+                if (lane == 0)
+                    for (uint32_t i = n_b; i < qlast + plast; ++i) bad |= (uint32_t)u[i] != vmin;
+            } else {
+                const uint64_t *sched = sched_all + (uint64_t)b * cfg.wcap;
+                uint32_t *tops = tops_all + (uint64_t)b * cfg.wcap;
+                const uint64_t MB = ~0ull / B;
+                // phase A: digits, low parts r_i into the split slots, high parts aside
+                for (uint32_t j0 = 0; j0 < W; j0 += 32 * KB) {
+                    Word sv[KB];
+#pragma unroll
+                    for (uint32_t k = 0; k < KB; ++k) {
+                        const uint32_t j = j0 + lane + 32 * k;
+                        sv[k] = j < W ? __ldcs(src + j) : Word(0);
+                    }
+#pragma unroll
+                    for (uint32_t k = 0; k < KB; ++k) {
+                        const uint32_t i = j0 + lane + 32 * k;
+                        if (i >= W) break;
                         const uint64_t e = sched[i];
                         const uint32_t R = (uint32_t)e;
                         const uint32_t p = (uint32_t)(e >> 32) & 0xFFu;
                         const uint32_t q = (uint32_t)(e >> 40);
-                        const uint64_t s = src[i];
+                        const uint64_t s = sv[k];
                         uint64_t body = s / R;
                         const uint32_t r = (uint32_t)(s - body * R);
-                        for (uint32_t k = p; k > 0; --k) {
+                        for (uint32_t kk = p; kk > 0; --kk) {
                             uint64_t dgt;
                             body = divmod_inv64(body, B, MB, dgt);
-                            const uint32_t idx = q + k - 1;
+                            const uint32_t idx = q + kk - 1;
                             if (idx < n_b) u[idx] = (T)(dgt + vmin);
                             else bad |= dgt != 0;
                         }
@@ -268,64 +574,360 @@ k_decompress(const uint8_t *__restrict__ in, uint64_t in_bytes, uint32_t L, T *_
                         if (split >= n_b) bad |= r != 0;
                         else u[split] = (T)r;
                     }
-                    __syncwarp();
-                    // phase B: re-join each split sample, e = r'_{i-1} R_{i-1} + r_{i-1}
-                    for (uint32_t i = lane; i < W; i += 32) {
-                        if (i == 0) continue;
-                        const uint32_t Rp = (uint32_t)sched[i - 1];
-                        const uint32_t q = (uint32_t)(sched[i] >> 40);
-                        const uint64_t val = (uint64_t)tops[i] * Rp + (uint32_t)u[q - 1];
-                        bad |= val >= B;
-                        u[q - 1] = (T)(val + vmin);
-                    }
                 }
-                if (bad) atomicOr(&bv.bad, 1u);
                 __syncwarp();
+                // phase B: re-join each split sample, e = r'_{i-1} R_{i-1} + r_{i-1}
+                for (uint32_t i = lane; i < W; i += 32) {
+                    if (i == 0) continue;
+                    const uint32_t Rp = (uint32_t)sched[i - 1];
+                    const uint32_t q = (uint32_t)(sched[i] >> 40);
+                    const uint64_t val = (uint64_t)tops[i] * Rp + (uint32_t)u[q - 1];
+                    bad |= val >= B;
+                    u[q - 1] = (T)(val + vmin);
+                }
             }
-            __syncthreads();
-            if (threadIdx.x == 0 && bv.bad) record_error(ws, PC_ERR_CORRUPT);
-            // 4. samples out
-            store_tile<T>(out, g0, cnt, L, smem, cfg.stage_bytes);
-            if (tile == n_tiles - 1 && threadIdx.x == 0) *n_out = n;
+            if (bad) atomicOr(&bv.bad, 1u);
+            __syncwarp();
         }
+        __syncthreads();
+        if (threadIdx.x == 0 && bv.bad) record_error(ws, PC_ERR_CORRUPT);
+        store_tile<T>(out, g0, cnt, L, smem, cfg.stage_bytes);
+        if (tile == n_tiles - 1 && threadIdx.x == 0) *n_out = n;
         __syncthreads();
     }
 }
 
-template <typename T, uint32_t WB, uint32_t VAR>
+// Per-block decoding parameters, held by one lane each in k_decode_w.
+struct DecBlock {
+    uint64_t B, Dh, MD;
+    uint32_t vmin, W, woff, p, n_b, hstar;
+    Magic32 mg;
+    OrbitView ov;
+};
+
+template <uint32_t WB, uint32_t VAR, bool ORB>
+__device__ __forceinline__ DecBlock dec_setup(const uint8_t *in, uint64_t gb, uint32_t n_b, const OrbitTable &ot,
+                                              WsHeader *ws, uint64_t limit_ns, uint32_t D)
+{
+    DecBlock d{};
+    uint64_t vmin, Bm1;
+    if (D == 16) {
+        const uint32_t e = reinterpret_cast<const uint32_t *>(in + PC_HEADER_BYTES)[gb];
+        vmin = e & 0xFFFFu;
+        Bm1 = e >> 16;
+    } else {
+        const uint64_t e = reinterpret_cast<const uint64_t *>(in + PC_HEADER_BYTES)[gb];
+        vmin = e & 0xFFFFFFFFull;
+        Bm1 = e >> 32;
+    }
+    d.B = Bm1 + 1;  // entries were range-checked by the offsets kernel
+    d.vmin = (uint32_t)vmin;
+    d.n_b = n_b;
+    if (d.B <= 1) return d;
+    d.mg = magic32(d.B);
+    d.hstar = 1;
+    d.Dh = d.B;
+    while (d.Dh <= (1ull << 32) / d.B) {
+        d.Dh *= d.B;
+        ++d.hstar;
+    }
+    d.MD = ~0ull / d.Dh;
+    if constexpr (VAR == PC_VARIANT_BASIC) {
+        d.p = basic_p(d.B, WB);
+        d.W = (n_b + d.p - 1) / d.p;
+    } else {
+        const uint64_t h = orbit_get<WB>(ot, (uint32_t)d.B, ws, limit_ns);  // B <= 65536 here
+        if (h != ~0ull) {
+            d.ov = orbit_view(ot, h);
+            d.W = orbit_words(ot, d.ov, n_b);
+        }
+    }
+    return d;
+}
+
+__device__ __forceinline__ DecBlock shfl_block(const DecBlock &x, int src)
+{
+    DecBlock d;
+    const unsigned F = 0xFFFFFFFFu;
+    d.B = __shfl_sync(F, x.B, src);
+    d.Dh = __shfl_sync(F, x.Dh, src);
+    d.MD = __shfl_sync(F, x.MD, src);
+    d.vmin = __shfl_sync(F, x.vmin, src);
+    d.W = __shfl_sync(F, x.W, src);
+    d.woff = __shfl_sync(F, x.woff, src);
+    d.p = __shfl_sync(F, x.p, src);
+    d.n_b = __shfl_sync(F, x.n_b, src);
+    d.hstar = __shfl_sync(F, x.hstar, src);
+    d.mg.m = __shfl_sync(F, x.mg.m, src);
+    d.mg.a = __shfl_sync(F, x.mg.a, src);
+    d.mg.s = __shfl_sync(F, x.mg.s, src);
+    d.ov.off = __shfl_sync(F, x.ov.off, src);
+    d.ov.Q = __shfl_sync(F, x.ov.Q, src);
+    d.ov.P = __shfl_sync(F, x.ov.P, src);
+    d.ov.SQ = __shfl_sync(F, x.ov.SQ, src);
+    d.ov.G = __shfl_sync(F, x.ov.G, src);
+    d.ov.mgP.m = __shfl_sync(F, x.ov.mgP.m, src);
+    d.ov.mgP.a = __shfl_sync(F, x.ov.mgP.a, src);
+    d.ov.mgP.s = __shfl_sync(F, x.ov.mgP.s, src);
+    return d;
+}
+
+constexpr uint32_t kDecWarps = 4;       // warps per CTA of k_decode_w
+constexpr uint32_t kWarpTileBlocks = 32; // blocks per warp tile (one lane each)
+
+// Warp-granular decoding (basic, and advanced with the series table on 16-bit
+// data): no shared barrier at all.  A warp owns 32 consecutive blocks; lane b
+// sets up block b (table entry, word count, division constants, series view),
+// then the warp decodes the blocks one by one into its own shared-memory slot
+// and stores each block's samples with 16-byte streaming stores.
+template <typename T, uint32_t WB, uint32_t VAR, bool ORB>
+__global__ void __launch_bounds__(kDecWarps * 32)
+k_decode_w(const uint8_t *__restrict__ in, uint32_t L, T *__restrict__ out, uint64_t *__restrict__ n_out,
+           WsHeader *ws, const uint64_t *__restrict__ offsets, OrbitTable ot, uint64_t limit_ns)
+{
+    using Word = typename WordT<T, WB>::type;
+    constexpr uint32_t D = sizeof(T) * 8;
+    constexpr uint32_t KB = 4;
+    extern __shared__ __align__(16) uint8_t smem[];
+    const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+    const uint32_t slot_bytes = (uint32_t)round_up((uint64_t)(L + kPad) * sizeof(T), 16);
+    T *u = reinterpret_cast<T *>(smem + warp * slot_bytes);
+
+    if (*reinterpret_cast<volatile uint32_t *>(&ws->status) != PC_OK) return;
+    const uint64_t *h64 = reinterpret_cast<const uint64_t *>(in);
+    const uint64_t n = h64[2], n_blocks = h64[3];
+    const uint64_t n_wt = ceil_div(n_blocks, kWarpTileBlocks);
+    const uint64_t payload_off = PC_HEADER_BYTES + table_bytes(n_blocks, D);
+    const Word *payload = reinterpret_cast<const Word *>(in + payload_off);
+    const uint64_t gw0 = (uint64_t)blockIdx.x * kDecWarps + warp, nw = (uint64_t)gridDim.x * kDecWarps;
+    bool bad = false;
+
+    for (uint64_t wt = gw0; wt < n_wt; wt += nw) {
+        const uint64_t blk0 = wt * kWarpTileBlocks;
+        const uint32_t nblk = (uint32_t)umin64(kWarpTileBlocks, n_blocks - blk0);
+        DecBlock mine{};
+        if (lane < nblk) {
+            const uint64_t gb = blk0 + lane;
+            const uint32_t n_b = (uint32_t)umin64(L, n - gb * L);
+            mine = dec_setup<WB, VAR, ORB>(in, gb, n_b, ot, ws, limit_ns, D);
+        }
+        const uint32_t incl = warp_incl_scan_u32(mine.W);
+        mine.woff = incl - mine.W;
+        const uint64_t base = offsets[wt];
+
+        for (uint32_t b = 0; b < nblk; ++b) {
+            const DecBlock k = shfl_block(mine, (int)b);
+            const uint64_t gb = blk0 + b;
+            const uint32_t vmin = k.vmin, W = k.W, n_b = k.n_b;
+            if (W == 0) {
+                for (uint32_t i = lane; i < n_b; i += 32) u[i] = (T)vmin;
+            } else if constexpr (VAR == PC_VARIANT_BASIC) {
+                const Word *src = payload + base + k.woff;
+                const uint32_t p = k.p, hstar = k.hstar, B32 = (uint32_t)k.B;
+                for (uint32_t j0 = 0; j0 < W; j0 += 32 * KB) {
+                    Word sv[KB];
+#pragma unroll
+                    for (uint32_t q = 0; q < KB; ++q) {
+                        const uint32_t j = j0 + lane + 32 * q;
+                        sv[q] = j < W ? __ldcs(src + j) : Word(0);
+                    }
+#pragma unroll
+                    for (uint32_t q = 0; q < KB; ++q) {
+                        const uint32_t j = j0 + lane + 32 * q;
+                        if (j >= W) break;
+                        const uint64_t s = sv[q];
+                        T *dst = u + j * p;
+                        uint32_t top;
+                        if (WB == 32 || p <= hstar) {
+                            top = put_digits<T>(dst, (uint32_t)s, p, B32, k.mg, vmin);
+                            if (WB == 64) bad |= (s >> 32) != 0;
+                        } else {
+                            uint64_t lo;
+                            uint64_t qv = divmod_inv64(s, k.Dh, k.MD, lo);
+                            put_digits<T>(dst, (uint32_t)lo, hstar, B32, k.mg, vmin);
+                            uint32_t rem = p - hstar;
+                            if (rem > hstar) {
+                                qv = divmod_inv64(qv, k.Dh, k.MD, lo);
+                                put_digits<T>(dst + hstar, (uint32_t)lo, hstar, B32, k.mg, vmin);
+                                dst += hstar;
+                                rem -= hstar;
+                            }
+                            bad |= (qv >> 32) != 0;
+                            top = put_digits<T>(dst + hstar, (uint32_t)qv, rem, B32, k.mg, vmin);
+                        }
+                        bad |= top >= k.B;
+                    }
+                }
+                __syncwarp();
+                if (lane == 0)
+                    for (uint32_t i = n_b; i < W * p; ++i) bad |= (uint32_t)u[i] != vmin;
+            } else {
+                const Word *src = payload + base + k.woff;
+                const uint32_t hstar = k.hstar, B32 = (uint32_t)k.B;
+                uint32_t cR = 1, cr = 0, qlast = 0, plast = 0;
+                for (uint32_t j0 = 0; j0 < W; j0 += 32) {
+                    const uint32_t i = j0 + lane;
+                    const bool valid = i < W;
+                    SeriesEntry e;
+                    uint64_t s = 0;
+                    if (valid) {
+                        e = orbit_entry(ot, k.ov, i);
+                        s = __ldcs(src + i);
+                    } else {
+                        e = SeriesEntry{1u, 0u, 0u, Magic32{0xFFFFFFFFu, 0xFFFFFFFFu, 0u}};
+                    }
+                    uint32_t r = 0;
+                    uint64_t body = 0;
+                    if (valid) {
+                        if constexpr (WB == 32) {
+                            const uint32_t q32 = magic_div((uint32_t)s, e.mgR);
+                            r = (uint32_t)s - q32 * e.R;
+                            body = q32;
+                        } else {
+                            body = divmod_small64(s, e.R, e.mgR, r);
+                        }
+                    }
+                    uint32_t Rp = __shfl_up_sync(0xFFFFFFFFu, e.R, 1);
+                    uint32_t rp = __shfl_up_sync(0xFFFFFFFFu, r, 1);
+                    if (lane == 0) {
+                        Rp = cR;
+                        rp = cr;
+                    }
+                    cR = __shfl_sync(0xFFFFFFFFu, e.R, 31);
+                    cr = __shfl_sync(0xFFFFFFFFu, r, 31);
+                    if (!valid) continue;
+                    T *last = u + e.q + e.p - 1;
+                    uint32_t rem = e.p;
+                    while (rem >= hstar && (body >> 32) != 0) {
+                        uint64_t lo;
+                        body = divmod_inv64(body, k.Dh, k.MD, lo);
+                        rev_exact<T>(last, (uint32_t)lo, hstar, B32, k.mg, vmin);
+                        last -= hstar;
+                        rem -= hstar;
+                    }
+                    bad |= (body >> 32) != 0;
+                    const uint32_t top = rev_quot<T>(last, (uint32_t)body, rem, B32, k.mg, vmin);
+                    if (i == 0) {
+                        bad |= top != 0;
+                    } else {
+                        const uint64_t val = (uint64_t)top * Rp + rp;
+                        bad |= val >= k.B;
+                        u[e.q - 1] = (T)(val + vmin);
+                    }
+                    if (e.q + e.p >= n_b) bad |= r != 0;
+                    if (i == W - 1) {
+                        qlast = e.q;
+                        plast = e.p;
+                    }
+                }
+                __syncwarp();
+                const uint32_t src_lane = (W - 1) & 31u;
+                qlast = __shfl_sync(0xFFFFFFFFu, qlast, src_lane);
+                plast = __shfl_sync(0xFFFFFFFFu, plast, src_lane);
+                if (lane == 0)
+                    for (uint32_t i = n_b; i < qlast + plast; ++i) bad |= (uint32_t)u[i] != vmin;
+            }
+            __syncwarp();
+            // this block's samples out
+            T *dstg = out + gb * L;
+            if ((L * sizeof(T)) % 16 == 0) {
+                constexpr uint32_t VE = 16 / sizeof(T);
+                const uint32_t nv = n_b / VE;
+                const uint4 *sv4 = reinterpret_cast<const uint4 *>(u);
+                uint4 *dv4 = reinterpret_cast<uint4 *>(dstg);
+                for (uint32_t v = lane; v < nv; v += 32) __stcs(dv4 + v, sv4[v]);
+                for (uint32_t i = nv * VE + lane; i < n_b; i += 32) dstg[i] = u[i];
+            } else {
+                for (uint32_t i = lane; i < n_b; i += 32) dstg[i] = u[i];
+            }
+            __syncwarp();
+        }
+        if (wt == n_wt - 1 && lane == 0) *n_out = n;
+    }
+    if (__any_sync(0xFFFFFFFFu, bad) && lane == 0) record_error(ws, PC_ERR_CORRUPT);
+}
+
+template <typename T, uint32_t WB, uint32_t VAR, bool ORB>
 static cudaError_t launch_decompress_t(const LaunchArgs &a)
 {
-    auto kern = k_decompress<T, WB, VAR>;
-    const TileCfg cfg = tile_cfg(VAR, sizeof(T) * 8, WB, a.L);
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.smem);
-    if (e != cudaSuccess) return e;
-    int per_sm = 0, dev = 0, sms = 0;
+    cudaError_t e;
+    int dev = 0, sms = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, cfg.smem)) != cudaSuccess)
-        return e;
-    if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    uint64_t grid = (uint64_t)per_sm * sms;
-    if (a.ws_tiles < grid) grid = a.ws_tiles;
-    if (grid < 1) grid = 1;
-    kern<<<(unsigned)grid, kThreads, cfg.smem, a.stream>>>(
-        static_cast<const uint8_t *>(a.in), a.in_bytes, a.L, static_cast<T *>(a.out), a.cap,
-        a.out_count, a.ws, a.status, a.ws_tiles, a.limit_ns);
-    return cudaGetLastError();
+    const TileCfg cfg = tile_cfg(kKernelDecode, VAR, sizeof(T) * 8, WB, a.L, ORB);
+    const OrbitTable ot{a.orb_flags, a.orb_hdr, static_cast<ulonglong2 *>(a.orb_slots), &a.ws->orbit_cursor};
+    // 1. offsets (look-back over tiles of kOffsetTileBlocks blocks)
+    {
+        auto kern = k_offsets<T, WB, VAR, ORB>;
+        int per_sm = 0;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, 0)) != cudaSuccess)
+            return e;
+        if (per_sm < 1) return cudaErrorInvalidConfiguration;
+        uint64_t grid = (uint64_t)per_sm * sms;
+        const uint64_t need = a.n_status;  // never more tiles than status words
+        if (need < grid) grid = need;
+        if (grid < 1) grid = 1;
+        constexpr bool kWarpTiles = VAR == PC_VARIANT_BASIC || (ORB && sizeof(T) == 2);
+        const uint32_t dtb = kWarpTiles ? kWarpTileBlocks : cfg.tb;
+        kern<<<(unsigned)grid, kThreads, 0, a.stream>>>(
+            static_cast<const uint8_t *>(a.in), a.in_bytes, a.L, a.cap, a.out_count, a.ws, a.status,
+            a.n_status, a.offsets, a.n_offsets, dtb, a.limit_ns, ot);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    // 2. decode: warp tiles where no serial walk is needed, CTA tiles otherwise
+    constexpr bool kWarpPath = VAR == PC_VARIANT_BASIC || (ORB && sizeof(T) == 2);
+    if constexpr (kWarpPath) {
+        auto kern = k_decode_w<T, WB, VAR, ORB>;
+        const uint32_t smem = kDecWarps * (uint32_t)round_up((uint64_t)(a.L + kPad) * sizeof(T), 16);
+        if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+            cudaSuccess)
+            return e;
+        int per_sm = 0;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kDecWarps * 32, smem)) !=
+            cudaSuccess)
+            return e;
+        if (per_sm < 1) return cudaErrorInvalidConfiguration;
+        uint64_t grid = (uint64_t)per_sm * sms;
+        const uint64_t need = ceil_div(a.n_offsets, kDecWarps);  // warp tiles <= offsets - 1
+        if (need < grid) grid = need;
+        if (grid < 1) grid = 1;
+        kern<<<(unsigned)grid, kDecWarps * 32, smem, a.stream>>>(
+            static_cast<const uint8_t *>(a.in), a.L, static_cast<T *>(a.out), a.out_count, a.ws, a.offsets, ot,
+            a.limit_ns);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    } else {
+        auto kern = k_decode<T, WB, VAR, ORB>;
+        if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.smem)) !=
+            cudaSuccess)
+            return e;
+        int per_sm = 0;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, cfg.smem)) != cudaSuccess)
+            return e;
+        if (per_sm < 1) return cudaErrorInvalidConfiguration;
+        uint64_t grid = (uint64_t)per_sm * sms;
+        const uint64_t need = a.n_offsets;  // decoding tiles + 1
+        if (need < grid) grid = need;
+        if (grid < 1) grid = 1;
+        kern<<<(unsigned)grid, kThreads, cfg.smem, a.stream>>>(
+            static_cast<const uint8_t *>(a.in), a.L, static_cast<T *>(a.out), a.out_count, a.ws, a.offsets, ot,
+            a.limit_ns);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_decompress(const LaunchArgs &a)
 {
     const uint32_t key = (a.d == 32 ? 4u : 0u) | (a.w == 64 ? 2u : 0u) | (a.variant ? 1u : 0u);
     switch (key) {
-    case 0: return launch_decompress_t<uint16_t, 32, 0>(a);
-    case 1: return launch_decompress_t<uint16_t, 32, 1>(a);
-    case 2: return launch_decompress_t<uint16_t, 64, 0>(a);
-    case 3: return launch_decompress_t<uint16_t, 64, 1>(a);
-    case 4: return launch_decompress_t<uint32_t, 32, 0>(a);
-    case 5: return launch_decompress_t<uint32_t, 32, 1>(a);
-    case 6: return launch_decompress_t<uint32_t, 64, 0>(a);
-    default: return launch_decompress_t<uint32_t, 64, 1>(a);
+    case 0: return launch_decompress_t<uint16_t, 32, 0, false>(a);
+    case 1: return a.orbit ? launch_decompress_t<uint16_t, 32, 1, true>(a) : launch_decompress_t<uint16_t, 32, 1, false>(a);
+    case 2: return launch_decompress_t<uint16_t, 64, 0, false>(a);
+    case 3: return a.orbit ? launch_decompress_t<uint16_t, 64, 1, true>(a) : launch_decompress_t<uint16_t, 64, 1, false>(a);
+    case 4: return launch_decompress_t<uint32_t, 32, 0, false>(a);
+    case 5: return a.orbit ? launch_decompress_t<uint32_t, 32, 1, true>(a) : launch_decompress_t<uint32_t, 32, 1, false>(a);
+    case 6: return launch_decompress_t<uint32_t, 64, 0, false>(a);
+    default: return a.orbit ? launch_decompress_t<uint32_t, 64, 1, true>(a) : launch_decompress_t<uint32_t, 64, 1, false>(a);
     }
 }
 

@@ -32,6 +32,23 @@ __device__ __forceinline__ uint64_t globaltimer()
     return t;
 }
 
+// Ampere-style asynchronous global -> shared copies (16-byte granules, L2
+// only), grouped and awaited per thread; they let the next tile stream in
+// while the current one is packed.
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 __device__ __forceinline__ void record_error(WsHeader *ws, uint32_t code)
 {
     atomicCAS(&ws->status, 0u, code);
@@ -55,22 +72,27 @@ __device__ __forceinline__ uint32_t warp_incl_scan_u32(uint32_t v)
     return v;
 }
 
-// Decoupled look-back, run by one full warp.  Publishes this tile's aggregate,
-// then sums predecessors' aggregates 32 at a time until it meets an inclusive
-// prefix, and publishes its own inclusive prefix.  Every wait is bounded by
-// `limit_ns` of %globaltimer and an iteration cap; when either runs out, or a
-// predecessor published an error, the tile publishes an error (so successors
-// stop waiting on it), records the reason and returns false.
-__device__ __noinline__ static bool lookback_warp(uint64_t *status, uint64_t tile, uint64_t agg, WsHeader *ws,
-                              uint64_t limit_ns, uint64_t *excl_out)
+// Decoupled look-back, in two halves run by one full warp.  The first
+// publishes this tile's aggregate (tile 0 publishes its inclusive prefix
+// directly).  The second sums predecessors' aggregates 32 at a time until it
+// meets an inclusive prefix, then publishes this tile's inclusive prefix.
+// Every wait is bounded by `limit_ns` of %globaltimer and an iteration cap;
+// when either runs out, or a predecessor published an error, the tile
+// publishes an error (so successors stop waiting on it), records the reason
+// and returns false.
+__device__ __forceinline__ void lookback_publish(uint64_t *status, uint64_t tile, uint64_t agg)
+{
+    if ((threadIdx.x & 31u) == 0) st_release(&status[tile], (tile == 0 ? kFlagPrefix : kFlagAgg) | agg);
+}
+
+__device__ __noinline__ static bool lookback_complete(uint64_t *status, uint64_t tile, uint64_t agg,
+                                                      WsHeader *ws, uint64_t limit_ns, uint64_t *excl_out)
 {
     const uint32_t lane = threadIdx.x & 31u;
     if (tile == 0) {
-        if (lane == 0) st_release(&status[0], kFlagPrefix | agg);
         *excl_out = 0;
         return true;
     }
-    if (lane == 0) st_release(&status[tile], kFlagAgg | agg);
     uint64_t excl = 0;
     int64_t base = (int64_t)tile - 1;
     const uint64_t t0 = globaltimer();
@@ -111,6 +133,14 @@ __device__ __noinline__ static bool lookback_warp(uint64_t *status, uint64_t til
     if (lane == 0) st_release(&status[tile], kFlagPrefix | (excl + agg));
     *excl_out = excl;
     return true;
+}
+
+// Both halves back to back.
+__device__ __forceinline__ bool lookback_warp(uint64_t *status, uint64_t tile, uint64_t agg, WsHeader *ws,
+                                              uint64_t limit_ns, uint64_t *excl_out)
+{
+    lookback_publish(status, tile, agg);
+    return lookback_complete(status, tile, agg, ws, limit_ns, excl_out);
 }
 
 // Copy `cnt` samples starting at global element g0 into the tile stage:
@@ -162,6 +192,31 @@ __device__ __forceinline__ void load_tile(const T *__restrict__ in, uint64_t g0,
             uint32_t bi = (uint32_t)(e / L), oi = (uint32_t)(e - (uint64_t)bi * L);
             reinterpret_cast<T *>(stage + (uint64_t)bi * stage_bytes)[oi] = in[g0 + e];
         }
+    }
+}
+
+// load_tile with asynchronous copies for the 16-byte granules (blocks must be
+// a whole number of granules); the ragged tail of the stream, if any, is
+// copied synchronously.  The caller commits the group and waits for it.
+template <typename T>
+__device__ __forceinline__ void load_tile_async(const T *__restrict__ in, uint64_t g0, uint64_t cnt,
+                                                uint32_t L, uint8_t *stage, uint32_t stage_bytes)
+{
+    constexpr uint32_t VE = 16 / sizeof(T);
+    const uint32_t vpb = L / VE;
+    const uint64_t nvec = cnt / VE;
+    const uint4 *src = reinterpret_cast<const uint4 *>(in + g0);
+    uint32_t b = threadIdx.x / vpb, o = threadIdx.x - b * vpb;
+    const uint32_t sb = kThreads / vpb, so = kThreads - sb * vpb;
+    for (uint64_t v = threadIdx.x; v < nvec; v += kThreads) {
+        cp_async16(stage + (uint64_t)b * stage_bytes + o * 16u, src + v);
+        o += so;
+        b += sb;
+        if (o >= vpb) { o -= vpb; ++b; }
+    }
+    for (uint64_t e = nvec * VE + threadIdx.x; e < cnt; e += kThreads) {
+        uint32_t bi = (uint32_t)(e / L), oi = (uint32_t)(e - (uint64_t)bi * L);
+        reinterpret_cast<T *>(stage + (uint64_t)bi * stage_bytes)[oi] = in[g0 + e];
     }
 }
 
@@ -248,7 +303,8 @@ __device__ __forceinline__ void block_minmax(T *blk, uint32_t n_b, uint32_t *vmi
 // R_i = floor(E / R'_{i-1}) with E = E1 or E0 = floor(C / B^(p_1 - 1)).
 // Entries are packed as R | p << 32 | q << 40 (R < 2^32, p < 64, q < 2^24).
 // Returns the word count, or ~0u if it would exceed `cap` (not reachable for
-// valid B; guards the shared-memory array).
+// valid B; guards the shared-memory array).  With sched == nullptr the series
+// is only counted.
 template <uint32_t WB>
 __device__ static uint32_t walk_series(uint64_t B, uint32_t n_b, uint64_t *sched, uint32_t cap)
 {
@@ -276,8 +332,10 @@ __device__ static uint32_t walk_series(uint64_t B, uint32_t n_b, uint64_t *sched
             p = p1 == 0 ? 0 : p1 - 1;
             R = E0 / x;
         }
-        if (i >= cap) return ~0u;
-        sched[i] = R | ((uint64_t)p << 32) | ((uint64_t)q << 40);
+        if (sched) {
+            if (i >= cap) return ~0u;
+            sched[i] = R | ((uint64_t)p << 32) | ((uint64_t)q << 40);
+        }
         ++i;
         const uint32_t split = q + p;
         if (split >= n_b) break;

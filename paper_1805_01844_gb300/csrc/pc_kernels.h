@@ -19,8 +19,15 @@ struct LaunchArgs {
     uint64_t cap;          // decompress: sample capacity
     uint64_t *out_count;   // compress: stream bytes; decompress: samples
     WsHeader *ws;
-    uint64_t *status;      // look-back words, ws_tiles of them
-    uint64_t n_blocks, n_tiles, ws_tiles;
+    uint64_t *status;      // look-back words
+    uint64_t n_status;     // look-back words available
+    uint64_t *offsets;     // decompression: payload offset per decoding tile (+ total)
+    uint64_t n_offsets;    // entries available in offsets
+    uint64_t n_blocks, n_tiles;
+    bool orbit;              // advanced: the series table is in the workspace
+    uint32_t *orb_flags;
+    uint64_t *orb_hdr;
+    void *orb_slots;
     uint64_t limit_ns;
     cudaStream_t stream;
 };

@@ -53,9 +53,14 @@ extern "C" pc_status pc_compress_noalloc(const void *d_in, uint64_t n_samples, c
                                          void *d_out, uint64_t out_capacity, uint64_t *d_out_bytes,
                                          pc_stream_t stream)
 {
+    if (!params) return PC_ERR_INVALID_ARG;
     uint64_t need = 0;
     pc_status st = pc_workspace_size(params, n_samples, &need);
     if (st != PC_OK) return st;
+    // the smallest workspace pc_compress accepts: the look-back words, without
+    // the advanced variant's series table (its blocks then walk the series)
+    need = pcx::ws_layout(params->variant, params->dtype_bits, params->word_bits, params->block_len,
+                          n_samples, false).bytes;
     if (need > PC_NOALLOC_SCRATCH_BYTES) return PC_ERR_UNSUPPORTED;  // stream too long for the static scratch
     void *scratch = nullptr;
     if ((st = scratch_of_current_device(&scratch)) != PC_OK) return st;

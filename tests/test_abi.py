@@ -92,3 +92,36 @@ def test_argument_checks_happen_on_the_host(lib):
 def test_strerror(lib):
     for code in range(7):
         assert native.strerror(code)
+
+
+def test_every_tile_configuration_fits_shared_memory(tmp_path):
+    """Host-compiled check of the kernels' tile layout (pc_common.cuh) for
+    every variant, sample width, word width and block length 1..8192: the
+    dynamic shared memory stays within the 227 KB a CTA can have, tiles hold
+    1..32 blocks, and two-slot pipelining only happens with 16-byte blocks."""
+    import shutil
+    import subprocess
+
+    if shutil.which("g++") is None:
+        pytest.skip("no host C++ compiler")
+    src = tmp_path / "tc.cpp"
+    src.write_text(r'''
+#include <cstdio>
+#include "pc_common.cuh"
+using namespace pcx;
+int main() {
+  for (unsigned k = 0; k < 2; ++k) for (unsigned v = 0; v < 2; ++v)
+  for (unsigned d = 16; d <= 32; d += 16) for (unsigned w = 32; w <= 64; w += 32)
+  for (unsigned L = 1; L <= 8192; ++L) for (int orb = 0; orb < 2; ++orb) {
+    TileCfg c = tile_cfg(k, v, d, w, L, orb != 0);
+    if (c.smem > 227u * 1024u || c.tb < 1 || c.tb > 32) { printf("bad %u %u %u %u %u\n", k, v, d, w, L); return 1; }
+    if (c.slots == 2 && (L * (d / 8)) % 16 != 0) { printf("slots %u\n", L); return 1; }
+  }
+  printf("ok\n");
+  return 0;
+}
+''')
+    exe = tmp_path / "tc"
+    subprocess.check_call(["g++", "-std=c++17", "-O1", "-I" + os.path.join(ROOT, "include"),
+                           "-I" + os.path.join(ROOT, "paper_1805_01844_gb300", "csrc"), str(src), "-o", str(exe)])
+    assert subprocess.run([str(exe)], capture_output=True, text=True).stdout.strip() == "ok"

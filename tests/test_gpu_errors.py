@@ -97,8 +97,10 @@ def test_random_bit_flips_never_misdecode_silently():
 
 
 def test_workspace_too_small_for_stream():
-    """A workspace sized for fewer samples than the stream holds is reported
-    (PC_ERR_INVALID_ARG) instead of being overrun."""
+    """A workspace sized for fewer samples than the output capacity is refused
+    by the host (PC_ERR_INVALID_ARG) before anything is launched; one sized
+    for the capacity but smaller than a stream that exceeds it never gets
+    used past its end either (the capacity check comes first)."""
     d = dev()
     x = datagen.white_noise(200000, 300.0, 5.0, seed=1)
     s = oracle.compress(x, 0, 64, 256)
@@ -110,8 +112,10 @@ def test_workspace_too_small_for_stream():
     n_out = torch.zeros(1, dtype=torch.int64, device=d)
     stream = torch.cuda.current_stream(d).cuda_stream
     assert native.decompress_raw(sd.data_ptr(), len(s), p, out.data_ptr(), x.size, n_out.data_ptr(),
-                                 ws.data_ptr(), ws_bytes, stream) == 0
-    assert native.last_device_status(ws.data_ptr(), stream) == native.PC_ERR_INVALID_ARG
+                                 ws.data_ptr(), ws_bytes, stream) == native.PC_ERR_INVALID_ARG
+    assert native.decompress_raw(sd.data_ptr(), len(s), p, out.data_ptr(), 1000, n_out.data_ptr(),
+                                 ws.data_ptr(), ws_bytes, stream) == native.PC_OK
+    assert native.last_device_status(ws.data_ptr(), stream) == native.PC_ERR_CAPACITY
 
 
 def test_bounded_wait_gives_up():
