@@ -223,6 +223,55 @@ __device__ __forceinline__ void adv_words_orbit(const OrbitTable &ot, const Orbi
     }
 }
 
+// Basic words of one block by one warp, four words per lane in lockstep so
+// that their Horner chains are independent for the scheduler.  Lanes past the
+// last word recompute the last word and do not store it.
+template <typename T, uint32_t WB>
+__device__ __forceinline__ void pack_basic_block(const T *u, uint32_t W, uint32_t p, uint32_t B32, uint64_t K,
+                                                 typename WordOf<T, WB>::type *dst)
+{
+    using Word = typename WordOf<T, WB>::type;
+    const uint32_t lane = threadIdx.x & 31u;
+    for (uint32_t j0 = 0; j0 < W; j0 += 128) {
+        const T *g[4];
+#pragma unroll
+        for (uint32_t k = 0; k < 4; ++k) {
+            const uint32_t j = min(j0 + lane + 32 * k, W - 1);
+            g[k] = u + j * p;
+        }
+        Word acc[4];
+        if constexpr (WB == 32) {
+            uint32_t a[4];
+#pragma unroll
+            for (uint32_t k = 0; k < 4; ++k) a[k] = g[k][p - 1];
+            for (int d = (int)p - 2; d >= 0; --d) {
+#pragma unroll
+                for (uint32_t k = 0; k < 4; ++k) a[k] = a[k] * B32 + (uint32_t)g[k][d];
+            }
+#pragma unroll
+            for (uint32_t k = 0; k < 4; ++k) acc[k] = a[k] - (uint32_t)K;
+        } else {
+            uint32_t lo[4], hi[4];
+#pragma unroll
+            for (uint32_t k = 0; k < 4; ++k) {
+                lo[k] = g[k][p - 1];
+                hi[k] = 0;
+            }
+            for (int d = (int)p - 2; d >= 0; --d) {
+#pragma unroll
+                for (uint32_t k = 0; k < 4; ++k) mad64(lo[k], hi[k], B32, (uint32_t)g[k][d]);
+            }
+#pragma unroll
+            for (uint32_t k = 0; k < 4; ++k) acc[k] = (((uint64_t)hi[k] << 32) | lo[k]) - K;
+        }
+#pragma unroll
+        for (uint32_t k = 0; k < 4; ++k) {
+            const uint32_t j = j0 + lane + 32 * k;
+            if (j < W) dst[j] = acc[k];
+        }
+    }
+}
+
 template <typename T, uint32_t WB, uint32_t VAR, bool ORB>
 __global__ void __launch_bounds__(kThreads)
 k_compress(const T *__restrict__ in, uint64_t n, uint32_t L, uint8_t *__restrict__ out,
@@ -393,9 +442,7 @@ k_compress(const T *__restrict__ in, uint64_t n, uint32_t L, uint8_t *__restrict
             const uint32_t B32 = (uint32_t)bv.B[b];  // B = 2^32 only with p = 1: never multiplies
             Word *dst = payload + bv.excl + bv.woff[b];
             if constexpr (VAR == PC_VARIANT_BASIC) {
-                const uint32_t p = bv.p[b];
-                const uint64_t K = bv.K[b];
-                for (uint32_t j = lane; j < W; j += 32) dst[j] = basic_word<T, WB>(u + j * p, p, B32, K);
+                pack_basic_block<T, WB>(u, W, bv.p[b], B32, bv.K[b], dst);
             } else {
                 if (ORB && bv.mode[b]) {
                     const OrbitView v{bv.orb_off[b], bv.orb_Q[b], bv.orb_P[b], bv.orb_SQ[b], bv.orb_G[b],

@@ -597,6 +597,102 @@ k_decode(const uint8_t *__restrict__ in, uint32_t L, T *__restrict__ out, uint64
     }
 }
 
+// Basic words of one block by one warp, four words per lane in lockstep (four
+// independent division chains).  Digits land at u[j p + i]; lanes past the
+// last word write theirs to `junk`.  Returns true if a word is not the image
+// of valid digits.
+template <typename T, uint32_t WB>
+__device__ __forceinline__ bool decode_basic_block(const typename WordT<T, WB>::type *src, T *u, T *junk,
+                                                   uint32_t W, uint32_t p, uint32_t hstar, uint64_t B,
+                                                   uint32_t vmin, Magic32 mg, uint64_t Dh, uint64_t MD)
+{
+    using Word = typename WordT<T, WB>::type;
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t B32 = (uint32_t)B;
+    bool bad = false;
+    for (uint32_t j0 = 0; j0 < W; j0 += 128) {
+        Word sv[4];
+        T *d[4];
+        bool ok[4];
+#pragma unroll
+        for (uint32_t k = 0; k < 4; ++k) {
+            const uint32_t j = j0 + lane + 32 * k;
+            ok[k] = j < W;
+            sv[k] = ok[k] ? __ldcs(src + j) : Word(0);
+            d[k] = ok[k] ? u + j * p : junk;
+        }
+        uint32_t x[4];
+        uint32_t off = 0, rem = p;
+        if (WB == 64 && p > hstar) {
+            // split each word into pieces of h* digits (B^h* <= 2^32)
+            uint64_t hv[4];
+#pragma unroll
+            for (uint32_t k = 0; k < 4; ++k) {
+                uint64_t lo;
+                hv[k] = divmod_inv64(sv[k], Dh, MD, lo);
+                x[k] = (uint32_t)lo;
+            }
+            for (uint32_t i = 0; i + 1 < hstar; ++i) {
+#pragma unroll
+                for (uint32_t k = 0; k < 4; ++k) {
+                    const uint32_t q = magic_div(x[k], mg);
+                    d[k][i] = (T)(x[k] - q * B32 + vmin);
+                    x[k] = q;
+                }
+            }
+#pragma unroll
+            for (uint32_t k = 0; k < 4; ++k) d[k][hstar - 1] = (T)(x[k] + vmin);
+            off = hstar;
+            rem = p - hstar;
+            if (rem > hstar) {  // p = 2 h* + 1: a middle piece of h* digits
+#pragma unroll
+                for (uint32_t k = 0; k < 4; ++k) {
+                    uint64_t lo;
+                    hv[k] = divmod_inv64(hv[k], Dh, MD, lo);
+                    x[k] = (uint32_t)lo;
+                }
+                for (uint32_t i = 0; i + 1 < hstar; ++i) {
+#pragma unroll
+                    for (uint32_t k = 0; k < 4; ++k) {
+                        const uint32_t q = magic_div(x[k], mg);
+                        d[k][off + i] = (T)(x[k] - q * B32 + vmin);
+                        x[k] = q;
+                    }
+                }
+#pragma unroll
+                for (uint32_t k = 0; k < 4; ++k) d[k][off + hstar - 1] = (T)(x[k] + vmin);
+                off += hstar;
+                rem -= hstar;
+            }
+#pragma unroll
+            for (uint32_t k = 0; k < 4; ++k) {
+                bad |= ok[k] && (hv[k] >> 32) != 0;
+                x[k] = (uint32_t)hv[k];
+            }
+        } else {
+#pragma unroll
+            for (uint32_t k = 0; k < 4; ++k) {
+                if (WB == 64) bad |= ok[k] && ((uint64_t)sv[k] >> 32) != 0;
+                x[k] = (uint32_t)sv[k];
+            }
+        }
+        for (uint32_t i = 0; i + 1 < rem; ++i) {
+#pragma unroll
+            for (uint32_t k = 0; k < 4; ++k) {
+                const uint32_t q = magic_div(x[k], mg);
+                d[k][off + i] = (T)(x[k] - q * B32 + vmin);
+                x[k] = q;
+            }
+        }
+#pragma unroll
+        for (uint32_t k = 0; k < 4; ++k) {
+            d[k][off + rem - 1] = (T)(x[k] + vmin);
+            bad |= ok[k] && x[k] >= B;  // the top digit
+        }
+    }
+    return bad;
+}
+
 // Per-block decoding parameters, held by one lane each in k_decode_w.
 struct DecBlock {
     uint64_t B, Dh, MD;
@@ -687,11 +783,10 @@ k_decode_w(const uint8_t *__restrict__ in, uint32_t L, T *__restrict__ out, uint
 {
     using Word = typename WordT<T, WB>::type;
     constexpr uint32_t D = sizeof(T) * 8;
-    constexpr uint32_t KB = 4;
     extern __shared__ __align__(16) uint8_t smem[];
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
-    const uint32_t slot_bytes = (uint32_t)round_up((uint64_t)(L + kPad) * sizeof(T), 16);
-    T *u = reinterpret_cast<T *>(smem + warp * slot_bytes);
+    const uint32_t slot_bytes = (uint32_t)round_up((uint64_t)(L + 2 * kPad) * sizeof(T), 16);
+    T *u = reinterpret_cast<T *>(smem + warp * slot_bytes);  // block, padding, junk for idle lanes
 
     if (*reinterpret_cast<volatile uint32_t *>(&ws->status) != PC_OK) return;
     const uint64_t *h64 = reinterpret_cast<const uint64_t *>(in);
@@ -723,41 +818,8 @@ k_decode_w(const uint8_t *__restrict__ in, uint32_t L, T *__restrict__ out, uint
                 for (uint32_t i = lane; i < n_b; i += 32) u[i] = (T)vmin;
             } else if constexpr (VAR == PC_VARIANT_BASIC) {
                 const Word *src = payload + base + k.woff;
-                const uint32_t p = k.p, hstar = k.hstar, B32 = (uint32_t)k.B;
-                for (uint32_t j0 = 0; j0 < W; j0 += 32 * KB) {
-                    Word sv[KB];
-#pragma unroll
-                    for (uint32_t q = 0; q < KB; ++q) {
-                        const uint32_t j = j0 + lane + 32 * q;
-                        sv[q] = j < W ? __ldcs(src + j) : Word(0);
-                    }
-#pragma unroll
-                    for (uint32_t q = 0; q < KB; ++q) {
-                        const uint32_t j = j0 + lane + 32 * q;
-                        if (j >= W) break;
-                        const uint64_t s = sv[q];
-                        T *dst = u + j * p;
-                        uint32_t top;
-                        if (WB == 32 || p <= hstar) {
-                            top = put_digits<T>(dst, (uint32_t)s, p, B32, k.mg, vmin);
-                            if (WB == 64) bad |= (s >> 32) != 0;
-                        } else {
-                            uint64_t lo;
-                            uint64_t qv = divmod_inv64(s, k.Dh, k.MD, lo);
-                            put_digits<T>(dst, (uint32_t)lo, hstar, B32, k.mg, vmin);
-                            uint32_t rem = p - hstar;
-                            if (rem > hstar) {
-                                qv = divmod_inv64(qv, k.Dh, k.MD, lo);
-                                put_digits<T>(dst + hstar, (uint32_t)lo, hstar, B32, k.mg, vmin);
-                                dst += hstar;
-                                rem -= hstar;
-                            }
-                            bad |= (qv >> 32) != 0;
-                            top = put_digits<T>(dst + hstar, (uint32_t)qv, rem, B32, k.mg, vmin);
-                        }
-                        bad |= top >= k.B;
-                    }
-                }
+                const uint32_t p = k.p;
+                bad |= decode_basic_block<T, WB>(src, u, u + L + kPad, W, p, k.hstar, k.B, vmin, k.mg, k.Dh, k.MD);
                 __syncwarp();
                 if (lane == 0)
                     for (uint32_t i = n_b; i < W * p; ++i) bad |= (uint32_t)u[i] != vmin;
@@ -878,7 +940,7 @@ static cudaError_t launch_decompress_t(const LaunchArgs &a)
     constexpr bool kWarpPath = VAR == PC_VARIANT_BASIC || (ORB && sizeof(T) == 2);
     if constexpr (kWarpPath) {
         auto kern = k_decode_w<T, WB, VAR, ORB>;
-        const uint32_t smem = kDecWarps * (uint32_t)round_up((uint64_t)(a.L + kPad) * sizeof(T), 16);
+        const uint32_t smem = kDecWarps * (uint32_t)round_up((uint64_t)(a.L + 2 * kPad) * sizeof(T), 16);
         if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
             cudaSuccess)
             return e;
