@@ -163,6 +163,96 @@ pc_status pc_last_device_status(const void *d_workspace, pc_stream_t stream);
 pc_status pc_selftest_bounded_wait(void *d_workspace, uint64_t workspace_bytes,
                                    uint32_t limit_us, pc_stream_t stream);
 
+/* ---- batches: many independent streams in one launch -------------------
+ * Every item is an independent stream with its own parameters (dtype, word
+ * size, variant, block length); the output of each item is exactly the
+ * stream pc_compress would produce for it.  The work is ordered as:
+ *   pc_batch_describe   host only: launch facts and device sizes
+ *   pc_batch_plan       one host-to-device copy of the item descriptors and
+ *                       a tile prefix into caller memory d_plan
+ *   pc_compress_batch   a memset and one persistent kernel on `stream`, which
+ *                       can be captured in a CUDA graph and replayed as long
+ *                       as the plan and the buffers stay in place.
+ * Tiles of all items share one ticket counter; within an item they keep the
+ * in-order look-back of pc_compress.  Bounded waits as for pc_compress. */
+typedef struct {
+    const void *d_in;       /* device samples, 16-byte aligned (NULL if n_samples = 0) */
+    uint64_t n_samples;
+    pc_params params;
+    void *d_out;            /* device stream buffer, 16-byte aligned */
+    uint64_t out_capacity;  /* >= pc_bound(&params, n_samples), else PC_ERR_CAPACITY */
+    uint64_t *d_out_bytes;  /* device: this item's stream size, written by the device */
+} pc_batch_item;
+
+typedef struct {
+    uint32_t n_items;
+    uint32_t smem_bytes;      /* dynamic shared memory of the launch */
+    uint64_t total_tiles;     /* tiles over all items (an empty item counts 1) */
+    uint64_t plan_bytes;      /* device bytes pc_batch_plan writes */
+    uint64_t workspace_bytes; /* device workspace pc_compress_batch needs */
+} pc_batch_info;
+
+/* Validate items (same rules as pc_compress) and fill *info.  Host only. */
+pc_status pc_batch_describe(const pc_batch_item *items, uint32_t n_items, pc_batch_info *info);
+
+/* Copy the descriptors and the tile prefix of items to device memory d_plan
+ * (info->plan_bytes bytes, 16-byte aligned) on `stream`.  items is read before
+ * the call returns. */
+pc_status pc_batch_plan(const pc_batch_item *items, uint32_t n_items, const pc_batch_info *info, void *d_plan,
+                        pc_stream_t stream);
+
+/* Compress every item of a plan: clears the workspace (info->workspace_bytes
+ * bytes, 16-byte aligned) and launches one persistent kernel.  Device-side
+ * status as for pc_compress (pc_last_device_status(d_workspace, stream)). */
+pc_status pc_compress_batch(const pc_batch_info *info, const void *d_plan, void *d_workspace,
+                            uint64_t workspace_bytes, pc_stream_t stream);
+
+/* ---- learned block-parameter chooser ------------------------------------
+ * The paper picks the block size by hand from ratio-versus-size curves
+ * (Sec. 4.2, Fig. 7; Sec. 4.3.2, Fig. 10).  Here a small MLP picks, for every
+ * segment of PC_SEGMENT_SAMPLES samples, one of PC_CHOOSER_OPTIONS parameter
+ * choices: option o = 2 i + j means block length 128 << i (i = 0..5) and
+ * word size 32 (j = 0) or 64 (j = 1).  The choice changes the parameters of
+ * each segment's stream, never the format, so losslessness is untouched.
+ * Features (PC_CHOOSER_FEATURES per segment, FP32, each roughly in [0, 1]):
+ *   0 min / dmax, 1 max / dmax, 2 log2(max - min + 1) / d,
+ *   3..18 fraction of the 32 sub-blocks of 128 samples whose range r has
+ *         floor(log2(r + 1)) = 0..15 (15 also counts larger),
+ *   19 mean / dmax, 20 log2(variance + 1) / 2d, 21 fraction of sub-blocks
+ *   whose range exceeds 4 (smallest sub-block range + 1), 22 d / 32,
+ *   23 (segment index mod 64) / 64;   d = dtype bits, dmax = 2^d - 1.
+ * MLP 24 -> 64 -> 64 -> 12, ReLU, softmax.  Weight buffer (PC_MLP_WEIGHT_BYTES,
+ * 16-byte aligned): BF16 W1[64][24], W2[64][64], W3[12][64], then FP32 b1[64],
+ * b2[64], b3[12].  Training buffers are FP32 in the same order
+ * (PC_MLP_PARAMS values).  All products accumulate in FP32. */
+#define PC_SEGMENT_SAMPLES 4096u
+#define PC_CHOOSER_FEATURES 24u
+#define PC_CHOOSER_HIDDEN 64u
+#define PC_CHOOSER_OPTIONS 12u
+#define PC_MLP_PARAMS 6540u
+#define PC_MLP_WEIGHT_BYTES 13360u
+
+/* Features of every segment of d_in (n_samples of dtype_bits) into
+ * d_features[ceil(n / 4096)][24]. */
+pc_status pc_segment_features(const void *d_in, uint64_t n_samples, uint32_t dtype_bits, float *d_features,
+                              pc_stream_t stream);
+
+/* Logits (optional, [n][12]) and the arg-max option (optional, [n]) of n
+ * feature rows. */
+pc_status pc_mlp_forward(const void *d_weights, const float *d_x, uint64_t n, float *d_logits, uint8_t *d_choice,
+                         pc_stream_t stream);
+
+/* Adds to d_grad[PC_MLP_PARAMS] the gradient of the mean softmax
+ * cross-entropy of n rows with labels d_labels[n] (options), and the summed
+ * loss to *d_loss, at the BF16 weights d_weights. */
+pc_status pc_mlp_grad(const void *d_weights, const float *d_x, const uint8_t *d_labels, uint64_t n, float *d_grad,
+                      float *d_loss, pc_stream_t stream);
+
+/* One Adam step (beta 0.9 / 0.999, eps 1e-8, step >= 1) on the FP32 master
+ * copy; rewrites the BF16 weights from it and clears d_grad. */
+pc_status pc_mlp_adam(float *d_master, void *d_weights, float *d_grad, float *d_m, float *d_v, uint32_t step,
+                      float lr, pc_stream_t stream);
+
 /* Compression without any device allocation, for callers that cannot
  * allocate device memory once they run: a data-acquisition loop that must not
  * call cudaMalloc mid-readout (it can fail under memory pressure or

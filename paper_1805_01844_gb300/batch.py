@@ -1,0 +1,91 @@
+"""Batches of independent streams in one launch (pc_batch_* in include/pc.h),
+and an autotuner for the block length and word size of each stream.
+
+Marshalling only: the compression itself is the library's persistent batch
+kernel.  A Batch can be captured in a CUDA graph (a memset and one kernel)
+and replayed while its tensors stay in place."""
+import torch
+
+from . import native
+from . import _dtype_bits, _stream_handle
+
+
+class Batch:
+    """Compress `tensors` (CUDA, contiguous, 16/32-bit) with per-stream
+    `params` (native.PcParams) in one launch; outputs are v1 streams."""
+
+    def __init__(self, tensors, params, device=None):
+        assert len(tensors) == len(params) and tensors
+        self.device = device or tensors[0].device
+        self.tensors = tensors
+        self.params = params
+        items = []
+        self.nbytes = torch.zeros(len(tensors), dtype=torch.int64, device=self.device)
+        caps, offs, total = [], [], 0
+        for i, (x, p) in enumerate(zip(tensors, params)):
+            if _dtype_bits(x) != p.dtype_bits:
+                raise TypeError("stream %d: sample width does not match dtype_bits" % i)
+            cap = native.bound(p, x.numel())
+            caps.append(cap)
+            offs.append(total)
+            total += (cap + 15) // 16 * 16
+        # every item's output is a 16-byte aligned slice of one buffer
+        self.buffer = torch.empty(max(total, 16), dtype=torch.uint8, device=self.device)
+        self.outs = [self.buffer[o:o + c] for o, c in zip(offs, caps)]
+        base = self.buffer.data_ptr()
+        nb = self.nbytes.data_ptr()
+        for i, (x, p) in enumerate(zip(tensors, params)):
+            items.append(native.PcBatchItem(x.data_ptr() if x.numel() else None, x.numel(), p,
+                                            base + offs[i], caps[i], nb + 8 * i))
+        self._arr, self.info = native.batch_describe(items)
+        self.plan = torch.empty((self.info.plan_bytes + 15) // 16 * 16, dtype=torch.uint8, device=self.device)
+        self.ws = torch.empty((self.info.workspace_bytes + 15) // 16 * 16, dtype=torch.uint8, device=self.device)
+        native.batch_plan(self._arr, self.info, self.plan.data_ptr(),
+                          _stream_handle(None, self.device))
+
+    def compress(self, stream=None):
+        st = native.compress_batch(self.info, self.plan.data_ptr(), self.ws.data_ptr(), self.ws.numel(),
+                                   _stream_handle(stream, self.device))
+        if st != native.PC_OK:
+            raise native.PcError(st, "pc_compress_batch")
+
+    def device_status(self, stream=None):
+        return native.last_device_status(self.ws.data_ptr(), _stream_handle(stream, self.device))
+
+    def capture(self):
+        """A CUDA graph of one batch compression (warm up first)."""
+        self.compress()
+        torch.cuda.synchronize(self.device)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self.compress()
+        return g
+
+    def streams(self):
+        """Host bytes of every output stream (synchronises)."""
+        sizes = self.nbytes.cpu().tolist()
+        return [o[:k].cpu().numpy().tobytes() for o, k in zip(self.outs, sizes)]
+
+
+LENGTHS = (128, 256, 512, 1024, 2048, 4096)
+WORDS = (32, 64)
+
+
+def autotune(x, variant=native.BASIC, sample=1 << 18, lengths=LENGTHS, words=WORDS):
+    """Block length and word size for stream `x`: every candidate compresses
+    the first `sample` samples with the library; the smallest stream wins, a
+    tie going to the longer block (fewer blocks, less per-block work)."""
+    from . import Codec
+
+    d = _dtype_bits(x)
+    head = x[:sample].contiguous()
+    best = None
+    for w in words:
+        for L in lengths:
+            codec = Codec(variant, d, w, L, max_samples=head.numel(), device=x.device)
+            _, nb = codec.compress(head)
+            size = int(nb.item())
+            key = (size, -L, -w)
+            if best is None or key < best[0]:
+                best = (key, native.params(variant, d, w, L))
+    return best[1]

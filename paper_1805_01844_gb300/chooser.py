@@ -1,0 +1,171 @@
+"""Learned block-parameter chooser (pc_segment_features / pc_mlp_* in
+include/pc.h): marshalling of the library's feature, MLP and batch kernels.
+
+Per segment of 4096 samples an MLP picks one of 12 options (block length
+128..4096 x word size 32/64).  The options only change the parameters of each
+segment's stream; every segment is an ordinary version-1 stream, compressed
+in one batch launch, so the format and losslessness are untouched.  The plain
+heuristic (one fixed option for every segment) is the fallback.
+"""
+import numpy as np
+import torch
+
+from . import native
+from .batch import Batch
+
+SEG = native.SEGMENT_SAMPLES
+OPTIONS = native.CHOOSER_OPTIONS
+LENGTHS = (128, 256, 512, 1024, 2048, 4096)
+PLAIN_OPTION = 7  # block length 1024, 64-bit words: the fixed default
+
+
+def option_params(o, dtype_bits, variant):
+    return native.params(variant, dtype_bits, (32, 64)[o % 2], LENGTHS[o // 2])
+
+
+def _bits(x):
+    return 16 if x.element_size() == 2 else 32
+
+
+def _stream(device):
+    return torch.cuda.current_stream(device).cuda_stream
+
+
+def segment_features(x):
+    """Feature rows [ceil(n / 4096), 24] (FP32) of a CUDA sample tensor."""
+    n = x.numel()
+    nseg = -(-n // SEG)
+    out = torch.empty((max(nseg, 1), native.CHOOSER_FEATURES), dtype=torch.float32, device=x.device)
+    st = native.load().pc_segment_features(x.data_ptr() if n else None, n, _bits(x), out.data_ptr(),
+                                           _stream(x.device))
+    if st != native.PC_OK:
+        raise native.PcError(st, "pc_segment_features")
+    return out[:nseg]
+
+
+def segments(x):
+    """Views of x, one per segment (all 16-byte aligned)."""
+    n = x.numel()
+    return [x[s:s + SEG] for s in range(0, n, SEG)]
+
+
+def compress_segments(x, options, variant=native.ADVANCED):
+    """Compress every segment of x with its option in one batch launch;
+    returns the Batch (streams in .outs, sizes in .nbytes)."""
+    d = _bits(x)
+    segs = segments(x)
+    opts = options.tolist() if hasattr(options, "tolist") else list(options)
+    params = [option_params(int(o), d, variant) for o in opts]
+    b = Batch(segs, params)
+    b.compress()
+    return b
+
+
+def exhaustive_sizes(x, variant=native.ADVANCED):
+    """Stream size of every segment under every option: [nseg, 12] int64
+    (12 batch launches, every segment compressed 12 times)."""
+    nseg = -(-x.numel() // SEG)
+    sizes = torch.empty((nseg, OPTIONS), dtype=torch.int64, device=x.device)
+    for o in range(OPTIONS):
+        b = compress_segments(x, [o] * nseg, variant)
+        st = b.device_status()
+        if st != native.PC_OK:
+            raise native.PcError(st, "pc_compress_batch (device)")
+        sizes[:, o] = b.nbytes
+    return sizes
+
+
+class Chooser:
+    """The MLP: BF16 weights for inference, FP32 master, Adam state."""
+
+    def __init__(self, device="cuda", seed=0):
+        self.device = torch.device(device)
+        rng = np.random.default_rng(seed)
+        P = []
+        for fan_out, fan_in in ((64, 24), (64, 64), (12, 64)):
+            P.append(rng.normal(0.0, np.sqrt(2.0 / fan_in), fan_out * fan_in))
+        P += [np.zeros(64), np.zeros(64), np.zeros(12)]
+        master = np.concatenate(P).astype(np.float32)
+        self.master = torch.from_numpy(master).to(self.device)
+        self.weights = torch.empty(native.MLP_WEIGHT_BYTES, dtype=torch.uint8, device=self.device)
+        self._sync_weights()
+        z = lambda: torch.zeros(native.MLP_PARAMS, dtype=torch.float32, device=self.device)  # noqa: E731
+        self.m, self.v, self.grad = z(), z(), z()
+        self.loss = torch.zeros(1, dtype=torch.float32, device=self.device)
+        self.step = 0
+
+    def _sync_weights(self):
+        """BF16 weights (round to nearest even) and FP32 biases from the master."""
+        nw = 64 * 24 + 64 * 64 + 12 * 64
+        wq = self.master[:nw].to(torch.bfloat16).view(torch.uint8)
+        bias = self.master[nw:].contiguous().view(torch.uint8)
+        self.weights[: 2 * nw].copy_(wq)
+        self.weights[2 * nw:].copy_(bias)
+
+    def set_master(self, flat):
+        self.master.copy_(torch.as_tensor(flat, dtype=torch.float32))
+        self._sync_weights()
+
+    def weights_f64(self):
+        """The BF16-rounded weights and FP32 biases as float64 (for checks)."""
+        nw = 64 * 24 + 64 * 64 + 12 * 64
+        w = self.weights[: 2 * nw].view(torch.bfloat16).double().cpu().numpy()
+        b = self.weights[2 * nw:].view(torch.float32).double().cpu().numpy()
+        return np.concatenate([w, b])
+
+    def logits(self, X):
+        n = X.shape[0]
+        out = torch.empty((max(n, 1), OPTIONS), dtype=torch.float32, device=self.device)
+        st = native.load().pc_mlp_forward(self.weights.data_ptr(), X.data_ptr(), n, out.data_ptr(), None,
+                                          _stream(self.device))
+        if st != native.PC_OK:
+            raise native.PcError(st, "pc_mlp_forward")
+        return out[:n]
+
+    def predict(self, X):
+        n = X.shape[0]
+        out = torch.empty(max(n, 1), dtype=torch.uint8, device=self.device)
+        st = native.load().pc_mlp_forward(self.weights.data_ptr(), X.data_ptr(), n, None, out.data_ptr(),
+                                          _stream(self.device))
+        if st != native.PC_OK:
+            raise native.PcError(st, "pc_mlp_forward")
+        return out[:n]
+
+    def loss_grad(self, X, y):
+        """(mean loss, gradient[6540]) at the current BF16 weights."""
+        self.grad.zero_()
+        self.loss.zero_()
+        st = native.load().pc_mlp_grad(self.weights.data_ptr(), X.data_ptr(), y.data_ptr(), X.shape[0],
+                                       self.grad.data_ptr(), self.loss.data_ptr(), _stream(self.device))
+        if st != native.PC_OK:
+            raise native.PcError(st, "pc_mlp_grad")
+        return float(self.loss.item()) / X.shape[0], self.grad.clone()
+
+    def train(self, X, y, epochs=30, batch=512, lr=3e-3, seed=0):
+        """Adam on mini-batches; returns the mean loss of each epoch."""
+        g = torch.Generator(device=self.device)
+        g.manual_seed(seed)
+        n = X.shape[0]
+        lib = native.load()
+        history = []
+        for _ in range(epochs):
+            perm = torch.randperm(n, generator=g, device=self.device)
+            self.loss.zero_()
+            for i in range(0, n, batch):
+                idx = perm[i:i + batch]
+                xb = X[idx].contiguous()
+                yb = y[idx].contiguous()
+                s = _stream(self.device)
+                lib.pc_mlp_grad(self.weights.data_ptr(), xb.data_ptr(), yb.data_ptr(), xb.shape[0],
+                                self.grad.data_ptr(), self.loss.data_ptr(), s)
+                self.step += 1
+                lib.pc_mlp_adam(self.master.data_ptr(), self.weights.data_ptr(), self.grad.data_ptr(),
+                                self.m.data_ptr(), self.v.data_ptr(), self.step, lr, s)
+            history.append(float(self.loss.item()) / n)
+        return history
+
+    def save(self, path):
+        np.save(path, self.master.cpu().numpy())
+
+    def load(self, path):
+        self.set_master(np.load(path))

@@ -47,7 +47,9 @@ struct WsHeader {
     uint32_t status;    // first device-side error, a pc_status; 0 = none
     uint32_t timeouts;  // bounded waits that ran out
     uint32_t orbit_cursor;  // next free slot of the series table (advanced)
-    uint64_t reserved[6];
+    uint32_t reserved_cursor64;  // same, second table of a batch (64-bit words)
+    uint32_t reserved1;
+    uint64_t reserved[5];
 };
 static_assert(sizeof(WsHeader) == 64, "workspace header is 64 bytes");
 
@@ -237,6 +239,23 @@ PCX_HD WsLayout ws_layout(uint32_t variant, uint32_t d, uint32_t w, uint32_t L, 
     lay.off_slots = lay.off_hdr + (lay.orbit ? kOrbitHdrBytes : 0);
     lay.bytes = lay.off_slots + (lay.orbit ? kOrbitSlotBytes : 0);
     return lay;
+}
+
+// Warp-granular decoding: shared memory of one warp (one block's samples
+// with padding and a junk area, two buffers of packed words) and the warps
+// per CTA that fit a 200 KB budget (1 to 4).
+PCX_HD uint32_t decw_warp_bytes(uint32_t variant, uint32_t d, uint32_t w, uint32_t L)
+{
+    const uint64_t slot = round_up((uint64_t)(L + 2 * kPad) * (d / 8), 16);
+    const uint64_t words = round_up(2 * words_bound(variant, d, w, L) * (w / 8), 16);
+    return (uint32_t)(slot + words);
+}
+
+PCX_HD uint32_t decw_warps(uint32_t variant, uint32_t d, uint32_t w, uint32_t L)
+{
+    uint32_t k = (200u * 1024u) / decw_warp_bytes(variant, d, w, L);
+    if (k > 4) k = 4;
+    return k;  // 0: does not fit (no parameters reach this)
 }
 
 PCX_HD uint64_t table_bytes(uint64_t n_blocks, uint32_t d)

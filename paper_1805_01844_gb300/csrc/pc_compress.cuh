@@ -1,0 +1,490 @@
+// pc_compress.cuh -- device code of the fused compression kernels (sm_103a),
+// shared by the single-stream kernel (pc_compress.cu) and the batch kernel
+// (pc_batch.cu).
+//
+// One CTA per tile of `tb` blocks, tiles handed out in order from an atomic
+// ticket.  Per tile:
+//   1. 16-byte streaming loads of the tile's samples into shared memory;
+//   2. per block (one warp each): min / max (Sec. 3.1), B = max - min + 1;
+//   3. word counts: basic W = ceil(n_b / p) with p from Eq. 1; advanced W from
+//      the split-base series of Sec. 3.2, one lane per block;
+//   4. warp scan of the counts, decoupled look-back across tiles for the
+//      payload offset of the tile;
+//   5. block table entries (min, B - 1) and the packed words, each word one
+//      Horner evaluation over its digits, stored coalesced.
+// The last tile writes the header, the table padding and the stream size.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "pc_device.cuh"
+#include "pc_kernels.h"
+#include "pc_orbit.cuh"
+
+namespace pcx {
+
+template <typename T, uint32_t WB>
+struct WordOf;
+template <typename T>
+struct WordOf<T, 32> { using type = uint32_t; };
+template <typename T>
+struct WordOf<T, 64> { using type = uint64_t; };
+
+// (lo, hi) <- (lo, hi) * m + a  in 64-bit arithmetic from 32-bit multiplies;
+// exact whenever the true result is below 2^64.
+__device__ __forceinline__ void mad64(uint32_t &lo, uint32_t &hi, uint32_t m, uint32_t a)
+{
+    uint64_t t = (uint64_t)lo * m + a;
+    hi = hi * m + (uint32_t)(t >> 32);
+    lo = (uint32_t)t;
+}
+
+// Eq. 2, word j of a block: s_j = sum_{i<p} u[j p + i] B^i with u = v - vmin.
+// Evaluated by Horner from the highest digit on the raw samples v, modulo
+// 2^w, minus K = vmin (1 + B + ... + B^(p-1)) mod 2^w: the difference is the
+// true s_j, which is < 2^w.  Padding samples hold vmin, i.e. digit 0.
+template <typename T, uint32_t WB, uint32_t P>
+__device__ __forceinline__ typename WordOf<T, WB>::type horner_k(const T *dg, uint32_t B32)
+{
+    if constexpr (WB == 32) {
+        uint32_t acc = dg[P - 1];
+#pragma unroll
+        for (int k = (int)P - 2; k >= 0; --k) acc = acc * B32 + (uint32_t)dg[k];
+        return acc;
+    } else {
+        uint32_t lo = dg[P - 1], hi = 0;
+#pragma unroll
+        for (int k = (int)P - 2; k >= 0; --k) mad64(lo, hi, B32, (uint32_t)dg[k]);
+        return ((uint64_t)hi << 32) | lo;
+    }
+}
+
+template <typename T, uint32_t WB>
+__device__ __forceinline__ typename WordOf<T, WB>::type
+basic_word(const T *dg, uint32_t p, uint32_t B32, uint64_t K)
+{
+    using Word = typename WordOf<T, WB>::type;
+    Word acc;
+    switch (p) {
+    case 1: acc = horner_k<T, WB, 1>(dg, B32); break;
+    case 2: acc = horner_k<T, WB, 2>(dg, B32); break;
+    case 3: acc = horner_k<T, WB, 3>(dg, B32); break;
+    case 4: acc = horner_k<T, WB, 4>(dg, B32); break;
+    case 5: acc = horner_k<T, WB, 5>(dg, B32); break;
+    case 6: acc = horner_k<T, WB, 6>(dg, B32); break;
+    case 7: acc = horner_k<T, WB, 7>(dg, B32); break;
+    case 8: acc = horner_k<T, WB, 8>(dg, B32); break;
+    case 9: acc = horner_k<T, WB, 9>(dg, B32); break;
+    case 10: acc = horner_k<T, WB, 10>(dg, B32); break;
+    case 11: acc = horner_k<T, WB, 11>(dg, B32); break;
+    case 12: acc = horner_k<T, WB, 12>(dg, B32); break;
+    default:
+        if constexpr (WB == 32) {
+            uint32_t a = dg[p - 1];
+            for (int k = (int)p - 2; k >= 0; --k) a = a * B32 + (uint32_t)dg[k];
+            acc = a;
+        } else {
+            uint32_t lo = dg[p - 1], hi = 0;
+            for (int k = (int)p - 2; k >= 0; --k) mad64(lo, hi, B32, (uint32_t)dg[k]);
+            acc = ((uint64_t)hi << 32) | lo;
+        }
+    }
+    return acc - (Word)K;
+}
+
+// Sec. 3.2, word i of a block:
+//   s_i = r_i + R_i (sum_{k=1}^{p_i} u_{q_i+k} B^{p_i-k} + r'_{i-1} B^{p_i})
+// with the split sample e = u[q_i + p_i], r_i = e mod R_i, and
+// r'_{i-1} = u[q_i - 1] div R_{i-1} (the high part of the previous split).
+template <typename T, uint32_t WB>
+__device__ __forceinline__ typename WordOf<T, WB>::type
+adv_word(const T *u, const uint64_t *sched, uint32_t i, uint32_t B32, uint32_t vmin)
+{
+    const uint64_t e = sched[i];
+    const uint32_t R = (uint32_t)e;
+    const uint32_t p = (uint32_t)(e >> 32) & 0xFFu;
+    const uint32_t q = (uint32_t)(e >> 40);
+    uint32_t top = 0;
+    if (i > 0) {
+        const uint32_t Rprev = (uint32_t)sched[i - 1];
+        top = ((uint32_t)u[q - 1] - vmin) / Rprev;
+    }
+    const uint32_t es = (uint32_t)u[q + p] - vmin;
+    const uint32_t r = es - (es / R) * R;
+    if constexpr (WB == 64 && sizeof(T) == 4) {
+        if (B32 == 0) {  // B = 2^32 (held as 0 in 32 bits): p_i <= 1
+            uint32_t lo = top, hi = 0;
+            if (p == 1) { hi = lo; lo = (uint32_t)u[q] - vmin; }
+            mad64(lo, hi, R, r);
+            return ((uint64_t)hi << 32) | lo;
+        }
+    }
+    if constexpr (WB == 32) {
+        uint32_t acc = top;
+        for (uint32_t k = 0; k < p; ++k) acc = acc * B32 + ((uint32_t)u[q + k] - vmin);
+        return acc * R + r;
+    } else {
+        uint32_t lo = top, hi = 0;
+        for (uint32_t k = 0; k < p; ++k) mad64(lo, hi, B32, (uint32_t)u[q + k] - vmin);
+        mad64(lo, hi, R, r);
+        return ((uint64_t)hi << 32) | lo;
+    }
+}
+
+// Horner over p raw samples starting from acc = top (the advanced word puts
+// its first sample in the highest power); modulo 2^w.
+template <typename T, uint32_t WB, uint32_t P>
+__device__ __forceinline__ uint64_t horner_top_k(uint32_t top, const T *dg, uint32_t B32)
+{
+    if constexpr (WB == 32) {
+        uint32_t acc = top;
+#pragma unroll
+        for (uint32_t k = 0; k < P; ++k) acc = acc * B32 + (uint32_t)dg[k];
+        return acc;
+    } else {
+        uint32_t lo = top, hi = 0;
+#pragma unroll
+        for (uint32_t k = 0; k < P; ++k) mad64(lo, hi, B32, (uint32_t)dg[k]);
+        return ((uint64_t)hi << 32) | lo;
+    }
+}
+
+template <typename T, uint32_t WB>
+__device__ __forceinline__ uint64_t horner_top(uint32_t top, const T *dg, uint32_t p, uint32_t B32)
+{
+    switch (p) {
+    case 0: return top;
+    case 1: return horner_top_k<T, WB, 1>(top, dg, B32);
+    case 2: return horner_top_k<T, WB, 2>(top, dg, B32);
+    case 3: return horner_top_k<T, WB, 3>(top, dg, B32);
+    case 4: return horner_top_k<T, WB, 4>(top, dg, B32);
+    case 5: return horner_top_k<T, WB, 5>(top, dg, B32);
+    case 6: return horner_top_k<T, WB, 6>(top, dg, B32);
+    case 7: return horner_top_k<T, WB, 7>(top, dg, B32);
+    case 8: return horner_top_k<T, WB, 8>(top, dg, B32);
+    case 9: return horner_top_k<T, WB, 9>(top, dg, B32);
+    case 10: return horner_top_k<T, WB, 10>(top, dg, B32);
+    case 11: return horner_top_k<T, WB, 11>(top, dg, B32);
+    case 12: return horner_top_k<T, WB, 12>(top, dg, B32);
+    default:
+        if constexpr (WB == 32) {
+            uint32_t acc = top;
+            for (uint32_t k = 0; k < p; ++k) acc = acc * B32 + (uint32_t)dg[k];
+            return acc;
+        } else {
+            uint32_t lo = top, hi = 0;
+            for (uint32_t k = 0; k < p; ++k) mad64(lo, hi, B32, (uint32_t)dg[k]);
+            return ((uint64_t)hi << 32) | lo;
+        }
+    }
+}
+
+// Sec. 3.2 words of one block from the series table, one warp, lanes over
+// consecutive words; R_{i-1} and its reciprocal come from the lane before
+// (the previous 32 words' last lane for lane 0).  Word i:
+//   r'_{i-1} = u[q_i - 1] div R_{i-1},  r_i = u[q_i + p_i] mod R_i,
+//   s_i = (Horner(r'_{i-1}; u[q_i .. q_i + p_i)) - K_{p_i}) R_i + r_i.
+template <typename T, uint32_t WB>
+__device__ __forceinline__ void adv_words_orbit(const OrbitTable &ot, const OrbitView &v, const T *u,
+                                                uint32_t W, uint32_t B32, uint32_t vmin, uint32_t p1,
+                                                uint64_t Kp1, uint64_t Kp0,
+                                                typename WordOf<T, WB>::type *dst)
+{
+    using Word = typename WordOf<T, WB>::type;
+    const uint32_t lane = threadIdx.x & 31u;
+    uint32_t cR = 1, cm = 0, ca = 0, cs = 0;  // carry: entry of the word before this chunk
+    for (uint32_t j0 = 0; j0 < W; j0 += 32) {
+        const uint32_t i = j0 + lane;
+        const bool valid = i < W;
+        SeriesEntry e;
+        if (valid) e = orbit_entry(ot, v, i);
+        else e = SeriesEntry{1u, 0u, 0u, Magic32{0xFFFFFFFFu, 0xFFFFFFFFu, 0u}};
+        uint32_t Rp = __shfl_up_sync(0xFFFFFFFFu, e.R, 1);
+        Magic32 mp;
+        mp.m = __shfl_up_sync(0xFFFFFFFFu, e.mgR.m, 1);
+        mp.a = __shfl_up_sync(0xFFFFFFFFu, e.mgR.a, 1);
+        mp.s = __shfl_up_sync(0xFFFFFFFFu, e.mgR.s, 1);
+        if (lane == 0) {
+            Rp = cR;
+            mp = Magic32{cm, ca, cs};
+        }
+        cR = __shfl_sync(0xFFFFFFFFu, e.R, 31);
+        cm = __shfl_sync(0xFFFFFFFFu, e.mgR.m, 31);
+        ca = __shfl_sync(0xFFFFFFFFu, e.mgR.a, 31);
+        cs = __shfl_sync(0xFFFFFFFFu, e.mgR.s, 31);
+        if (!valid) continue;
+        const uint32_t top = i > 0 ? magic_div((uint32_t)u[e.q - 1] - vmin, mp) : 0u;
+        const uint32_t es = (uint32_t)u[e.q + e.p] - vmin;
+        const uint32_t r = es - magic_div(es, e.mgR) * e.R;
+        const uint64_t acc = horner_top<T, WB>(top, u + e.q, e.p, B32) - (e.p == p1 ? Kp1 : Kp0);
+        if constexpr (WB == 32) {
+            dst[i] = (Word)((uint32_t)acc * e.R + r);
+        } else {
+            uint32_t lo = (uint32_t)acc, hi = (uint32_t)(acc >> 32);
+            mad64(lo, hi, e.R, r);
+            dst[i] = ((uint64_t)hi << 32) | lo;
+        }
+    }
+}
+
+// Basic words of one block by one warp, four words per lane in lockstep so
+// that their Horner chains are independent for the scheduler.  Lanes past the
+// last word recompute the last word and do not store it.
+template <typename T, uint32_t WB>
+__device__ __forceinline__ void pack_basic_block(const T *u, uint32_t W, uint32_t p, uint32_t B32, uint64_t K,
+                                                 typename WordOf<T, WB>::type *dst)
+{
+    using Word = typename WordOf<T, WB>::type;
+    const uint32_t lane = threadIdx.x & 31u;
+    for (uint32_t j0 = 0; j0 < W; j0 += 128) {
+        const T *g[4];
+#pragma unroll
+        for (uint32_t k = 0; k < 4; ++k) {
+            const uint32_t j = min(j0 + lane + 32 * k, W - 1);
+            g[k] = u + j * p;
+        }
+        Word acc[4];
+        if constexpr (WB == 32) {
+            uint32_t a[4];
+#pragma unroll
+            for (uint32_t k = 0; k < 4; ++k) a[k] = g[k][p - 1];
+            for (int d = (int)p - 2; d >= 0; --d) {
+#pragma unroll
+                for (uint32_t k = 0; k < 4; ++k) a[k] = a[k] * B32 + (uint32_t)g[k][d];
+            }
+#pragma unroll
+            for (uint32_t k = 0; k < 4; ++k) acc[k] = a[k] - (uint32_t)K;
+        } else {
+            uint32_t lo[4], hi[4];
+#pragma unroll
+            for (uint32_t k = 0; k < 4; ++k) {
+                lo[k] = g[k][p - 1];
+                hi[k] = 0;
+            }
+            for (int d = (int)p - 2; d >= 0; --d) {
+#pragma unroll
+                for (uint32_t k = 0; k < 4; ++k) mad64(lo[k], hi[k], B32, (uint32_t)g[k][d]);
+            }
+#pragma unroll
+            for (uint32_t k = 0; k < 4; ++k) acc[k] = (((uint64_t)hi[k] << 32) | lo[k]) - K;
+        }
+#pragma unroll
+        for (uint32_t k = 0; k < 4; ++k) {
+            const uint32_t j = j0 + lane + 32 * k;
+            if (j < W) dst[j] = acc[k];
+        }
+    }
+}
+
+// One stream as the compression kernels see it.
+struct StreamArgs {
+    const void *in;
+    uint64_t n;
+    uint32_t L;
+    uint8_t *out;
+    uint64_t *out_bytes;
+    uint64_t *status;  // look-back words of this stream's tiles
+    uint64_t n_blocks, n_tiles;
+    OrbitTable ot;
+};
+
+// Compress tile `tile` of stream `sa` with the whole CTA: stage its samples,
+// min / max per block (Sec. 3.1), word counts (Eq. 1-2, or the split-base
+// series of Sec. 3.2), scan and publish the tile's aggregate, look back to
+// its payload offset, then write its table entries and packed words; the last
+// tile writes the header, the table padding and the stream size.
+template <typename T, uint32_t WB, uint32_t VAR, bool ORB>
+__device__ void compress_tile(const StreamArgs &sa, uint64_t tile, uint8_t *smem, WsHeader *ws, uint64_t limit_ns)
+{
+    using Word = typename WordOf<T, WB>::type;
+    constexpr uint32_t D = sizeof(T) * 8;
+    const uint32_t L = sa.L;
+    const TileCfg cfg = tile_cfg(kKernelCompress, VAR, D, WB, L, ORB);
+    BlockVars &bv = *reinterpret_cast<BlockVars *>(smem + cfg.off_blk);
+    uint64_t *sched_all = reinterpret_cast<uint64_t *>(smem + cfg.off_sched);
+    const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+    const T *in = static_cast<const T *>(sa.in);
+    const uint64_t n = sa.n, n_blocks = sa.n_blocks, n_tiles = sa.n_tiles;
+    const uint64_t payload_off = PC_HEADER_BYTES + table_bytes(n_blocks, D);
+    const uint64_t blk0 = tile * cfg.tb;
+    const uint32_t nblk = (uint32_t)umin64(cfg.tb, n_blocks - blk0);
+    const uint64_t cnt = umin64(n - blk0 * L, (uint64_t)nblk * L);
+
+    // 1. stage: whole 16-byte blocks put every granule of the tile in flight at once
+    if ((L * sizeof(T)) % 16 == 0) {
+        load_tile_async<T>(in, blk0 * L, cnt, L, smem, cfg.stage_bytes);
+        cp_async_commit();
+        cp_async_wait<0>();
+    } else {
+        load_tile<T>(in, blk0 * L, cnt, L, smem, cfg.stage_bytes);
+    }
+    __syncthreads();
+
+    // 2. min / max per block
+    for (uint32_t b = warp; b < nblk; b += kWarps) {
+        const uint32_t n_b = (uint32_t)umin64(L, cnt - (uint64_t)b * L);
+        block_minmax<T>(reinterpret_cast<T *>(smem + (uint64_t)b * cfg.stage_bytes), n_b, &bv.vmin[b], &bv.B[b]);
+    }
+    __syncthreads();
+
+    // 3-4. word counts, scan, aggregate, look-back
+    if (warp == 0) {
+        uint32_t W = 0;
+        if (lane < nblk) {
+            const uint64_t B = bv.B[lane];
+            const uint32_t n_b = (uint32_t)umin64(L, cnt - (uint64_t)lane * L);
+            if (B > 1) {
+                if constexpr (VAR == PC_VARIANT_BASIC) {
+                    const uint32_t p = basic_p(B, WB);
+                    bv.p[lane] = p;
+                    W = (n_b + p - 1) / p;
+                    uint64_t geo = 0, pw = 1;  // 1 + B + ... + B^(p-1), mod 2^64
+                    for (uint32_t i = 0; i < p; ++i) {
+                        geo += pw;
+                        pw *= B;
+                    }
+                    bv.K[lane] = geo * bv.vmin[lane];
+                } else if (ORB && B <= kOrbitMaxB) {
+                    // the series from the table: O(1) per word
+                    const uint64_t h = orbit_get<WB>(sa.ot, (uint32_t)B, ws, limit_ns);
+                    if (h != ~0ull) {
+                        const OrbitView v = orbit_view(sa.ot, h);
+                        W = orbit_words(sa.ot, v, n_b);
+                        bv.orb_off[lane] = v.off;
+                        bv.orb_Q[lane] = v.Q;
+                        bv.orb_P[lane] = v.P;
+                        bv.orb_SQ[lane] = v.SQ;
+                        bv.orb_G[lane] = v.G;
+                        bv.orb_mgm[lane] = v.mgP.m;
+                        bv.orb_mga[lane] = v.mgP.a;
+                        bv.orb_mgs[lane] = v.mgP.s;
+                        const uint32_t p1 = eq1_p(B, WB);
+                        uint64_t geo = 0, pw = 1, geo0 = 0;  // 1 + B + ... + B^(p-1)
+                        for (uint32_t k = 0; k < p1; ++k) {
+                            geo0 = geo;
+                            geo += pw;
+                            pw *= B;
+                        }
+                        bv.p1[lane] = p1;
+                        bv.K[lane] = geo * bv.vmin[lane];
+                        bv.K2[lane] = geo0 * bv.vmin[lane];
+                    }
+                    bv.mode[lane] = 1;
+                } else {
+                    W = walk_series<WB>(B, n_b, sched_all + (uint64_t)lane * cfg.wcap, cfg.wcap);
+                    if (W == ~0u) {
+                        record_error(ws, PC_ERR_INVALID_ARG);
+                        W = 0;
+                    }
+                    bv.mode[lane] = 0;
+                }
+            }
+            bv.W[lane] = W;
+        }
+        const uint32_t incl = warp_incl_scan_u32(W);
+        if (lane < nblk) bv.woff[lane] = incl - W;
+        const uint32_t agg = __shfl_sync(0xFFFFFFFFu, incl, 31);
+        lookback_publish(sa.status, tile, agg);
+        uint64_t excl = 0;
+        const bool ok = lookback_complete(sa.status, tile, agg, ws, limit_ns, &excl);
+        if (lane == 0) {
+            bv.agg = agg;
+            bv.excl = excl;
+            bv.ok = ok ? 1u : 0u;
+        }
+    }
+    __syncthreads();
+
+    // 5. table entries, packed words, and the stream's closing bytes
+    if (bv.ok) {
+        for (uint32_t b = threadIdx.x; b < nblk; b += kThreads) {
+            const uint64_t gb = blk0 + b;
+            const uint64_t Bm1 = bv.B[b] - 1;
+            if constexpr (D == 16) {
+                reinterpret_cast<uint32_t *>(sa.out + PC_HEADER_BYTES)[gb] = bv.vmin[b] | ((uint32_t)Bm1 << 16);
+            } else {
+                reinterpret_cast<uint64_t *>(sa.out + PC_HEADER_BYTES)[gb] = (uint64_t)bv.vmin[b] | (Bm1 << 32);
+            }
+        }
+        Word *payload = reinterpret_cast<Word *>(sa.out + payload_off);
+        for (uint32_t b = warp; b < nblk; b += kWarps) {
+            const uint32_t W = bv.W[b];
+            if (W == 0) continue;
+            const T *u = reinterpret_cast<const T *>(smem + (uint64_t)b * cfg.stage_bytes);
+            const uint32_t vmin = bv.vmin[b];
+            const uint32_t B32 = (uint32_t)bv.B[b];  // B = 2^32 only with p = 1: never multiplies
+            Word *dst = payload + bv.excl + bv.woff[b];
+            if constexpr (VAR == PC_VARIANT_BASIC) {
+                pack_basic_block<T, WB>(u, W, bv.p[b], B32, bv.K[b], dst);
+            } else {
+                if (ORB && bv.mode[b]) {
+                    const OrbitView v{bv.orb_off[b], bv.orb_Q[b], bv.orb_P[b], bv.orb_SQ[b], bv.orb_G[b],
+                                      Magic32{bv.orb_mgm[b], bv.orb_mga[b], bv.orb_mgs[b]}};
+                    adv_words_orbit<T, WB>(sa.ot, v, u, W, B32, vmin, bv.p1[b], bv.K[b], bv.K2[b], dst);
+                } else {
+                    const uint64_t *sched = sched_all + (uint64_t)b * cfg.wcap;
+                    for (uint32_t j = lane; j < W; j += 32) dst[j] = adv_word<T, WB>(u, sched, j, B32, vmin);
+                }
+            }
+        }
+        if (tile == n_tiles - 1) {
+            const uint64_t payload_words = bv.excl + bv.agg;
+            const uint64_t tend = PC_HEADER_BYTES + n_blocks * 2u * (D / 8);
+            for (uint64_t o = tend + threadIdx.x; o < payload_off; o += kThreads) sa.out[o] = 0;
+            if (threadIdx.x == 0) {
+                uint32_t *h = reinterpret_cast<uint32_t *>(sa.out);
+                h[0] = 0x504D4350u;  // "PCMP"
+                h[1] = 1u | (VAR << 16) | (D << 24);
+                h[2] = WB;
+                h[3] = L;
+                uint64_t *h64 = reinterpret_cast<uint64_t *>(sa.out);
+                h64[2] = n;
+                h64[3] = n_blocks;
+                h64[4] = payload_words;
+                h64[5] = 0;
+                h64[6] = 0;
+                h64[7] = 0;
+                *sa.out_bytes = payload_off + payload_words * (WB / 8);
+            }
+        }
+    }
+    __syncthreads();  // the stage and the per-tile arrays are free again
+}
+
+// Header of an empty stream (no blocks).
+template <uint32_t D, uint32_t WB, uint32_t VAR>
+__device__ void write_empty_stream(const StreamArgs &sa)
+{
+    uint32_t *h = reinterpret_cast<uint32_t *>(sa.out);
+    h[0] = 0x504D4350u;
+    h[1] = 1u | (VAR << 16) | (D << 24);
+    h[2] = WB;
+    h[3] = sa.L;
+    uint64_t *h64 = reinterpret_cast<uint64_t *>(sa.out);
+    for (int i = 2; i < 8; ++i) h64[i] = 0;
+    *sa.out_bytes = PC_HEADER_BYTES;
+}
+
+// Single-stream compression: a persistent grid, tiles taken in order from an
+// atomic ticket (so a tile only waits on tiles owned by running CTAs).
+template <typename T, uint32_t WB, uint32_t VAR, bool ORB>
+__global__ void __launch_bounds__(kThreads)
+k_compress(StreamArgs sa, WsHeader *ws, uint64_t limit_ns)
+{
+    extern __shared__ __align__(16) uint8_t smem[];
+    __shared__ uint32_t s_tile;
+    if (sa.n_tiles == 0) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) write_empty_stream<sizeof(T) * 8, WB, VAR>(sa);
+        return;
+    }
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = atomicAdd(&ws->ticket, 1u);
+        __syncthreads();
+        const uint64_t tile = s_tile;
+        __syncthreads();
+        if (tile >= sa.n_tiles) break;
+        compress_tile<T, WB, VAR, ORB>(sa, tile, smem, ws, limit_ns);
+    }
+}
+
+}  // namespace pcx

@@ -602,7 +602,8 @@ k_decode(const uint8_t *__restrict__ in, uint32_t L, T *__restrict__ out, uint64
 // last word write theirs to `junk`.  Returns true if a word is not the image
 // of valid digits.
 template <typename T, uint32_t WB>
-__device__ __forceinline__ bool decode_basic_block(const typename WordT<T, WB>::type *src, T *u, T *junk,
+__device__ __forceinline__ bool decode_basic_block(const typename WordT<T, WB>::type *src /* shared */, T *u,
+                                                   T *junk,
                                                    uint32_t W, uint32_t p, uint32_t hstar, uint64_t B,
                                                    uint32_t vmin, Magic32 mg, uint64_t Dh, uint64_t MD)
 {
@@ -618,7 +619,7 @@ __device__ __forceinline__ bool decode_basic_block(const typename WordT<T, WB>::
         for (uint32_t k = 0; k < 4; ++k) {
             const uint32_t j = j0 + lane + 32 * k;
             ok[k] = j < W;
-            sv[k] = ok[k] ? __ldcs(src + j) : Word(0);
+            sv[k] = ok[k] ? src[j] : Word(0);  // src is the warp's shared-memory word buffer
             d[k] = ok[k] ? u + j * p : junk;
         }
         uint32_t x[4];
@@ -768,7 +769,7 @@ __device__ __forceinline__ DecBlock shfl_block(const DecBlock &x, int src)
     return d;
 }
 
-constexpr uint32_t kDecWarps = 4;       // warps per CTA of k_decode_w
+constexpr uint32_t kDecWarpsMax = 4;     // warps per CTA of k_decode_w (decw_warps)
 constexpr uint32_t kWarpTileBlocks = 32; // blocks per warp tile (one lane each)
 
 // Warp-granular decoding (basic, and advanced with the series table on 16-bit
@@ -777,7 +778,7 @@ constexpr uint32_t kWarpTileBlocks = 32; // blocks per warp tile (one lane each)
 // then the warp decodes the blocks one by one into its own shared-memory slot
 // and stores each block's samples with 16-byte streaming stores.
 template <typename T, uint32_t WB, uint32_t VAR, bool ORB>
-__global__ void __launch_bounds__(kDecWarps * 32)
+__global__ void __launch_bounds__(kDecWarpsMax * 32)
 k_decode_w(const uint8_t *__restrict__ in, uint32_t L, T *__restrict__ out, uint64_t *__restrict__ n_out,
            WsHeader *ws, const uint64_t *__restrict__ offsets, OrbitTable ot, uint64_t limit_ns)
 {
@@ -785,8 +786,15 @@ k_decode_w(const uint8_t *__restrict__ in, uint32_t L, T *__restrict__ out, uint
     constexpr uint32_t D = sizeof(T) * 8;
     extern __shared__ __align__(16) uint8_t smem[];
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+    // per warp: one block's samples (+ padding, + junk for idle lanes), then
+    // two buffers of packed words: the next block's words stream in while
+    // the current block is decoded
+    const uint32_t wmax = (uint32_t)words_bound(VAR, D, WB, L);
     const uint32_t slot_bytes = (uint32_t)round_up((uint64_t)(L + 2 * kPad) * sizeof(T), 16);
-    T *u = reinterpret_cast<T *>(smem + warp * slot_bytes);  // block, padding, junk for idle lanes
+    const uint32_t warp_bytes = decw_warp_bytes(VAR, D, WB, L);
+    const uint32_t nwarps = blockDim.x >> 5;
+    T *u = reinterpret_cast<T *>(smem + warp * warp_bytes);
+    Word *wbuf = reinterpret_cast<Word *>(smem + warp * warp_bytes + slot_bytes);
 
     if (*reinterpret_cast<volatile uint32_t *>(&ws->status) != PC_OK) return;
     const uint64_t *h64 = reinterpret_cast<const uint64_t *>(in);
@@ -794,7 +802,7 @@ k_decode_w(const uint8_t *__restrict__ in, uint32_t L, T *__restrict__ out, uint
     const uint64_t n_wt = ceil_div(n_blocks, kWarpTileBlocks);
     const uint64_t payload_off = PC_HEADER_BYTES + table_bytes(n_blocks, D);
     const Word *payload = reinterpret_cast<const Word *>(in + payload_off);
-    const uint64_t gw0 = (uint64_t)blockIdx.x * kDecWarps + warp, nw = (uint64_t)gridDim.x * kDecWarps;
+    const uint64_t gw0 = (uint64_t)blockIdx.x * nwarps + warp, nw = (uint64_t)gridDim.x * nwarps;
     bool bad = false;
 
     for (uint64_t wt = gw0; wt < n_wt; wt += nw) {
@@ -809,22 +817,35 @@ k_decode_w(const uint8_t *__restrict__ in, uint32_t L, T *__restrict__ out, uint
         const uint32_t incl = warp_incl_scan_u32(mine.W);
         mine.woff = incl - mine.W;
         const uint64_t base = offsets[wt];
+        auto prefetch = [&](uint32_t b) {  // block b's words into buffer b & 1
+            const uint32_t Wb = __shfl_sync(0xFFFFFFFFu, mine.W, (int)b);
+            const uint32_t ob = __shfl_sync(0xFFFFFFFFu, mine.woff, (int)b);
+            const Word *g = payload + base + ob;
+            Word *dstw = wbuf + (b & 1u) * wmax;
+            for (uint32_t j = lane; j < Wb; j += 32) cp_async_small<sizeof(Word)>(dstw + j, g + j);
+            cp_async_commit();
+        };
+        prefetch(0);
 
         for (uint32_t b = 0; b < nblk; ++b) {
+            if (b + 1 < nblk) prefetch(b + 1);
+            else cp_async_commit();
+            cp_async_wait<1>();
+            __syncwarp();
             const DecBlock k = shfl_block(mine, (int)b);
             const uint64_t gb = blk0 + b;
             const uint32_t vmin = k.vmin, W = k.W, n_b = k.n_b;
+            const Word *wsrc = wbuf + (b & 1u) * wmax;
             if (W == 0) {
                 for (uint32_t i = lane; i < n_b; i += 32) u[i] = (T)vmin;
             } else if constexpr (VAR == PC_VARIANT_BASIC) {
-                const Word *src = payload + base + k.woff;
                 const uint32_t p = k.p;
-                bad |= decode_basic_block<T, WB>(src, u, u + L + kPad, W, p, k.hstar, k.B, vmin, k.mg, k.Dh, k.MD);
+                bad |= decode_basic_block<T, WB>(wsrc, u, u + L + kPad, W, p, k.hstar, k.B, vmin, k.mg, k.Dh, k.MD);
                 __syncwarp();
                 if (lane == 0)
                     for (uint32_t i = n_b; i < W * p; ++i) bad |= (uint32_t)u[i] != vmin;
             } else {
-                const Word *src = payload + base + k.woff;
+                const Word *src = wsrc;
                 const uint32_t hstar = k.hstar, B32 = (uint32_t)k.B;
                 uint32_t cR = 1, cr = 0, qlast = 0, plast = 0;
                 for (uint32_t j0 = 0; j0 < W; j0 += 32) {
@@ -834,7 +855,7 @@ k_decode_w(const uint8_t *__restrict__ in, uint32_t L, T *__restrict__ out, uint
                     uint64_t s = 0;
                     if (valid) {
                         e = orbit_entry(ot, k.ov, i);
-                        s = __ldcs(src + i);
+                        s = src[i];
                     } else {
                         e = SeriesEntry{1u, 0u, 0u, Magic32{0xFFFFFFFFu, 0xFFFFFFFFu, 0u}};
                     }
@@ -906,6 +927,7 @@ k_decode_w(const uint8_t *__restrict__ in, uint32_t L, T *__restrict__ out, uint
         }
         if (wt == n_wt - 1 && lane == 0) *n_out = n;
     }
+    cp_async_wait<0>();
     if (__any_sync(0xFFFFFFFFu, bad) && lane == 0) record_error(ws, PC_ERR_CORRUPT);
 }
 
@@ -940,20 +962,21 @@ static cudaError_t launch_decompress_t(const LaunchArgs &a)
     constexpr bool kWarpPath = VAR == PC_VARIANT_BASIC || (ORB && sizeof(T) == 2);
     if constexpr (kWarpPath) {
         auto kern = k_decode_w<T, WB, VAR, ORB>;
-        const uint32_t smem = kDecWarps * (uint32_t)round_up((uint64_t)(a.L + 2 * kPad) * sizeof(T), 16);
+        const uint32_t nwarps = decw_warps(VAR, sizeof(T) * 8, WB, a.L);
+        if (nwarps < 1) return cudaErrorInvalidConfiguration;
+        const uint32_t smem = nwarps * decw_warp_bytes(VAR, sizeof(T) * 8, WB, a.L);
         if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
             cudaSuccess)
             return e;
         int per_sm = 0;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kDecWarps * 32, smem)) !=
-            cudaSuccess)
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, nwarps * 32, smem)) != cudaSuccess)
             return e;
         if (per_sm < 1) return cudaErrorInvalidConfiguration;
         uint64_t grid = (uint64_t)per_sm * sms;
-        const uint64_t need = ceil_div(a.n_offsets, kDecWarps);  // warp tiles <= offsets - 1
+        const uint64_t need = ceil_div(a.n_offsets, nwarps);  // warp tiles <= offsets - 1
         if (need < grid) grid = need;
         if (grid < 1) grid = 1;
-        kern<<<(unsigned)grid, kDecWarps * 32, smem, a.stream>>>(
+        kern<<<(unsigned)grid, nwarps * 32, smem, a.stream>>>(
             static_cast<const uint8_t *>(a.in), a.L, static_cast<T *>(a.out), a.out_count, a.ws, a.offsets, ot,
             a.limit_ns);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;

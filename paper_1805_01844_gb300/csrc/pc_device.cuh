@@ -11,6 +11,10 @@
 
 #include "pc_common.cuh"
 
+#ifndef PCX_MINMAX_PACKED
+#define PCX_MINMAX_PACKED 0
+#endif
+
 namespace pcx {
 
 __device__ __forceinline__ uint64_t ld_acquire(const uint64_t *p)
@@ -39,6 +43,14 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
 {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+
+// 4- or 8-byte asynchronous copy (a packed word), cached in L1 and L2.
+template <uint32_t BYTES>
+__device__ __forceinline__ void cp_async_small(void *smem, const void *gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(s), "l"(gmem), "n"(BYTES) : "memory");
 }
 
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
@@ -264,6 +276,7 @@ __device__ __forceinline__ void block_minmax(T *blk, uint32_t n_b, uint32_t *vmi
     const uint32_t nvec = n_b / VE;
     const uint4 *v4 = reinterpret_cast<const uint4 *>(blk);
     if (sizeof(T) == 2) {
+#if PCX_MINMAX_PACKED
         uint32_t pmn = 0xFFFFFFFFu, pmx = 0;
         for (uint32_t i = lane; i < nvec; i += 32) {
             uint4 x = v4[i];
@@ -272,6 +285,19 @@ __device__ __forceinline__ void block_minmax(T *blk, uint32_t n_b, uint32_t *vmi
         }
         mn = min(pmn & 0xFFFFu, pmn >> 16);
         mx = max(pmx & 0xFFFFu, pmx >> 16);
+#else
+        // the two halves of each 32-bit word kept apart: plain 32-bit min/max
+        uint32_t lmn = 0xFFFFFFFFu, lmx = 0, hmn = 0xFFFFFFFFu, hmx = 0;
+        for (uint32_t i = lane; i < nvec; i += 32) {
+            const uint4 x = v4[i];
+            lmn = min(min(lmn, min(x.x & 0xFFFFu, x.y & 0xFFFFu)), min(x.z & 0xFFFFu, x.w & 0xFFFFu));
+            lmx = max(max(lmx, max(x.x & 0xFFFFu, x.y & 0xFFFFu)), max(x.z & 0xFFFFu, x.w & 0xFFFFu));
+            hmn = min(min(hmn, min(x.x, x.y)), min(x.z, x.w));  // high halves order the words
+            hmx = max(max(hmx, max(x.x, x.y)), max(x.z, x.w));
+        }
+        mn = min(lmn, hmn >> 16);
+        mx = max(lmx, hmx >> 16);
+#endif
     } else {
         for (uint32_t i = lane; i < nvec; i += 32) {
             uint4 x = v4[i];

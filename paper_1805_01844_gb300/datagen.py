@@ -121,3 +121,56 @@ def white_noise_torch(n, device, mean=300.0, sigma=5.0, seed=0):
     g.manual_seed(seed)
     x = torch.randn(n, generator=g, device=device) * sigma + mean
     return torch.round(x).clamp_(0, 65535).to(torch.int32).to(torch.int16)
+
+
+# ------------------------------------------------------ batches of streams
+
+
+def batched_stream_specs(n_streams=64, min_bytes=4096, max_bytes=64 << 20, seed=0):
+    """Specs of independent streams: byte length log-uniform in
+    [min_bytes, max_bytes], dtype uint16 or uint32 at random, white noise with
+    sigma log-uniform in [1, 2000] around a mean U(100, 10000), and 0.5 %
+    spikes of uniform amplitude up to the dtype maximum."""
+    rng = np.random.default_rng(seed)
+    specs = []
+    for s in range(n_streams):
+        nbytes = float(np.exp(rng.uniform(np.log(min_bytes), np.log(max_bytes))))
+        dtype = np.uint16 if rng.integers(0, 2) == 0 else np.uint32
+        n = max(1, int(nbytes) // np.dtype(dtype).itemsize)
+        sigma = float(np.exp(rng.uniform(0.0, np.log(2000.0))))
+        mean = float(rng.uniform(100.0, 10000.0))
+        specs.append(dict(n=n, dtype=dtype, mean=mean, sigma=sigma, spike_frac=0.005,
+                          seed=int(rng.integers(0, 2 ** 31))))
+    return specs
+
+
+def batched_stream(spec):
+    """Host samples of one stream spec (numpy)."""
+    rng = np.random.default_rng(spec["seed"])
+    hi = np.iinfo(spec["dtype"]).max
+    v = np.rint(rng.normal(spec["mean"], spec["sigma"], spec["n"]))
+    k = int(round(spec["spike_frac"] * spec["n"]))
+    if k:
+        pos = rng.choice(spec["n"], size=k, replace=False)
+        v[pos] = rng.uniform(0, hi, k)
+    return np.clip(np.rint(v), 0, hi).astype(spec["dtype"])
+
+
+def batched_stream_torch(spec, device):
+    """Device samples of one stream spec (torch's generator; int16/int32 bit
+    patterns of the uint16/uint32 values)."""
+    import torch
+
+    g = torch.Generator(device=device)
+    g.manual_seed(spec["seed"])
+    n = spec["n"]
+    hi = float(np.iinfo(spec["dtype"]).max)
+    v = torch.randn(n, generator=g, device=device, dtype=torch.float64) * spec["sigma"] + spec["mean"]
+    k = int(round(spec["spike_frac"] * n))
+    if k:
+        pos = torch.randint(0, n, (k,), generator=g, device=device)
+        v[pos] = torch.rand(k, generator=g, device=device, dtype=torch.float64) * hi
+    v = torch.round(v).clamp_(0, hi)
+    if spec["dtype"] == np.uint16:
+        return v.to(torch.int32).to(torch.int16)
+    return v.to(torch.int64).to(torch.int32)

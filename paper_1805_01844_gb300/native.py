@@ -19,7 +19,10 @@ BASIC, ADVANCED = 0, 1
 
 EXPORTS = ("pc_bound", "pc_workspace_size", "pc_compress", "pc_decompress",
            "pc_parse_header", "pc_last_device_status", "pc_selftest_bounded_wait",
-           "pc_strerror", "pc_compress_noalloc")
+           "pc_strerror", "pc_compress_noalloc", "pc_batch_describe", "pc_batch_plan",
+           "pc_compress_batch", "pc_segment_features", "pc_mlp_forward", "pc_mlp_grad", "pc_mlp_adam")
+SEGMENT_SAMPLES, CHOOSER_FEATURES, CHOOSER_OPTIONS = 4096, 24, 12
+MLP_PARAMS, MLP_WEIGHT_BYTES = 6540, 13360
 NOALLOC_SCRATCH_BYTES = 1 << 20
 
 
@@ -30,6 +33,18 @@ class PcParams(ctypes.Structure):
     def __repr__(self):
         return "PcParams(variant=%d, dtype_bits=%d, word_bits=%d, block_len=%d)" % (
             self.variant, self.dtype_bits, self.word_bits, self.block_len)
+
+
+class PcBatchItem(ctypes.Structure):
+    _fields_ = [("d_in", ctypes.c_void_p), ("n_samples", ctypes.c_uint64), ("params", PcParams),
+                ("d_out", ctypes.c_void_p), ("out_capacity", ctypes.c_uint64),
+                ("d_out_bytes", ctypes.c_void_p)]
+
+
+class PcBatchInfo(ctypes.Structure):
+    _fields_ = [("n_items", ctypes.c_uint32), ("smem_bytes", ctypes.c_uint32),
+                ("total_tiles", ctypes.c_uint64), ("plan_bytes", ctypes.c_uint64),
+                ("workspace_bytes", ctypes.c_uint64)]
 
 
 class PcError(RuntimeError):
@@ -71,6 +86,23 @@ def load(path=LIB_PATH):
     L.pc_selftest_bounded_wait.restype = st
     L.pc_compress_noalloc.argtypes = [vp, u64, pp, vp, u64, vp, vp]
     L.pc_compress_noalloc.restype = st
+    ip = ctypes.POINTER(PcBatchItem)
+    fp = ctypes.POINTER(PcBatchInfo)
+    L.pc_batch_describe.argtypes = [ip, u32, fp]
+    L.pc_batch_describe.restype = st
+    L.pc_batch_plan.argtypes = [ip, u32, fp, vp, vp]
+    L.pc_batch_plan.restype = st
+    L.pc_compress_batch.argtypes = [fp, vp, vp, u64, vp]
+    L.pc_compress_batch.restype = st
+    f32p = ctypes.c_void_p
+    L.pc_segment_features.argtypes = [vp, u64, u32, f32p, vp]
+    L.pc_segment_features.restype = st
+    L.pc_mlp_forward.argtypes = [vp, f32p, u64, f32p, vp, vp]
+    L.pc_mlp_forward.restype = st
+    L.pc_mlp_grad.argtypes = [vp, f32p, vp, u64, f32p, f32p, vp]
+    L.pc_mlp_grad.restype = st
+    L.pc_mlp_adam.argtypes = [f32p, vp, f32p, f32p, f32p, u32, ctypes.c_float, vp]
+    L.pc_mlp_adam.restype = st
     L.pc_strerror.argtypes = [st]
     L.pc_strerror.restype = ctypes.c_char_p
     _lib = L
@@ -138,3 +170,20 @@ def compress_noalloc_raw(d_in, n_samples, p, d_out, out_capacity, d_out_bytes, s
     library's static scratch is used.  Returns the host status."""
     return load().pc_compress_noalloc(d_in or None, int(n_samples), ctypes.byref(p), d_out,
                                       int(out_capacity), d_out_bytes, stream or None)
+
+
+def batch_describe(items):
+    """items: list of PcBatchItem.  Returns (ctypes array, PcBatchInfo)."""
+    arr = (PcBatchItem * len(items))(*items)
+    info = PcBatchInfo()
+    _check(load().pc_batch_describe(arr, len(items), ctypes.byref(info)), "pc_batch_describe")
+    return arr, info
+
+
+def batch_plan(arr, info, d_plan, stream):
+    _check(load().pc_batch_plan(arr, info.n_items, ctypes.byref(info), d_plan, stream or None), "pc_batch_plan")
+
+
+def compress_batch(info, d_plan, d_ws, ws_bytes, stream):
+    """pc_compress_batch; returns the host status."""
+    return load().pc_compress_batch(ctypes.byref(info), d_plan, d_ws, int(ws_bytes), stream or None)

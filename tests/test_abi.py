@@ -116,6 +116,10 @@ int main() {
     TileCfg c = tile_cfg(k, v, d, w, L, orb != 0);
     if (c.smem > 227u * 1024u || c.tb < 1 || c.tb > 32) { printf("bad %u %u %u %u %u\n", k, v, d, w, L); return 1; }
     if (c.slots == 2 && (L * (d / 8)) % 16 != 0) { printf("slots %u\n", L); return 1; }
+    if (k == 1) {
+      unsigned nw = decw_warps(v, d, w, L);
+      if (nw < 1 || nw > 4 || nw * decw_warp_bytes(v, d, w, L) > 227u * 1024u) { printf("decw %u %u %u %u\n", v, d, w, L); return 1; }
+    }
   }
   printf("ok\n");
   return 0;

@@ -263,3 +263,56 @@ def test_paper_simulated_ratios():
     assert abs(blocked - 2.47054) / 2.47054 < 0.03, blocked
     assert abs(unblocked - 2.10361) / 2.10361 < 0.01, unblocked
     assert blocked > 1.15 * unblocked  # "larger than 17 %"
+
+
+# ------------------------------------------- the chooser's MLP oracle (fp64)
+
+
+def test_mlp_oracle_gradient_matches_finite_differences():
+    """oracle.mlp.loss_grad (chain rule written out) against central finite
+    differences of its own loss, coordinate by coordinate on a sample."""
+    from oracle import mlp
+
+    rng = np.random.default_rng(0)
+    P = {k: rng.normal(0, 0.3, mlp.SHAPES[k]) for k in mlp.NAMES}
+    X = rng.uniform(0, 1, (17, 24))
+    y = rng.integers(0, 12, 17)
+    _, G = mlp.loss_grad(P, X, y)
+    flat, g = mlp.flatten(P), mlp.flatten(G)
+    idx = rng.choice(flat.size, 120, replace=False)
+    h = 1e-6
+    for i in idx:
+        a, b = flat.copy(), flat.copy()
+        a[i] += h
+        b[i] -= h
+        num = (mlp.loss_grad(mlp.unflatten(a), X, y)[0] - mlp.loss_grad(mlp.unflatten(b), X, y)[0]) / (2 * h)
+        assert abs(num - g[i]) <= 1e-6 + 1e-5 * abs(num), (i, num, g[i])
+
+
+def test_mlp_oracle_features_of_simple_segments():
+    """Features of hand-checkable segments: a constant segment (range 0, all
+    sub-blocks in class 0), and a ramp 0..4095 of 16-bit samples (every
+    sub-block has range 127 -> class floor(log2 128) = 7)."""
+    from oracle import mlp
+
+    c = np.full(4096, 1000, np.uint16)
+    f = mlp.features(c, 16)[0]
+    assert f[0] == f[1] == 1000 / 65535 and f[2] == 0 and f[3] == 1.0 and f[4:19].sum() == 0
+    assert f[20] == 0 and f[21] == 0 and f[22] == 0.5 and f[23] == 0
+    r = np.arange(4096, dtype=np.uint16)
+    f = mlp.features(r, 16, seg0=65)[0]
+    assert f[3 + 7] == 1.0 and abs(f[2] - 12 / 16) < 1e-12 and f[23] == 1 / 64
+    assert abs(f[19] - 2047.5 / 65535) < 1e-12
+
+
+def test_exhaustive_labels_pick_the_smallest_stream():
+    """The oracle's labels are argmins of its own stream sizes, and on data
+    with one spike the best option is a short block (the paper's observation
+    that outliers make long blocks costly, Sec. 3.3 / 4.2)."""
+    from oracle import mlp
+
+    x = datagen.white_noise(4096 * 3, 300.0, 5.0, seed=4)
+    x[5000] = 60000
+    lab, sizes = mlp.labels(x, 1)
+    assert (sizes[np.arange(3), lab] == sizes.min(axis=1)).all()
+    assert mlp.option_params(int(lab[1]))[0] < 4096
