@@ -50,6 +50,9 @@ def parse():
                     help="events in the oracle's CPU sample (0 = sized to ~15 s)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-events", type=int, default=20000)
     return ap.parse_args()
 
 
@@ -350,6 +353,14 @@ def main():
                "sample": "first %d events (%.1f MB) of the workload, compress + decompress, %.1f s, "
                          "single thread" % (n_ev, n_ev * ev_host[0].size * 2 / 1e6, secs)}
 
+    learned, trained = None, None
+    if not args.no_learned and rank == 0 and world == 1:
+        learned, trained = learned_vs_plain(x, args.events, dev)
+
+    serving = None
+    if not args.no_serve and rank == 0 and world == 1:
+        serving = serve_metrics(dev, args.serve_events, trained)
+
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
@@ -369,10 +380,94 @@ def main():
         "roofline": {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                      "alg_bytes_per_launch": alg_bytes, "traffic": recorded_traffic(key)},
-        "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 2 * args.steps,
+        "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 3 * args.steps,
+        "learned": learned, "serving": serving,
         "clocks": clk, "wall_s_timed": wall,
     }
     print(json.dumps(line), flush=True)
+
+
+def learned_vs_plain(x, n_events, dev, train_events=400, test_events=400):
+    """Compression ratio of the learned per-segment parameters against the
+    plain heuristic (block length 1024, 64-bit words for every segment) and the
+    exhaustive optimum, on held-out events, with the GPU time of each path.
+    Labels are the exhaustive minimum-size options found by compressing every
+    training segment with all 12 options on the GPU (the tests check that
+    search against the CPU oracle's byte for byte)."""
+    import torch
+
+    from paper_1805_01844_gb300 import chooser as ch
+    from paper_1805_01844_gb300 import native
+
+    per = x.numel() // n_events
+    tr = x[: train_events * per]
+    te = x[n_events * per - test_events * per:]
+    t0 = time.perf_counter()
+    sizes_tr = ch.exhaustive_sizes(tr)
+    y = torch.argmin(sizes_tr, dim=1).to(torch.uint8)
+    c = ch.Chooser(dev, seed=0)
+    Xtr = ch.segment_features(tr)
+    c.train(Xtr, y, epochs=40, batch=512, lr=3e-3)
+    train_s = time.perf_counter() - t0
+    sizes_te = ch.exhaustive_sizes(te)
+    raw = te.numel() * 2
+
+    def timed(fn, reps=5):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            out = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return out, e0.elapsed_time(e1) / reps
+
+    nseg = sizes_te.shape[0]
+    plain_opts = [ch.PLAIN_OPTION] * nseg
+
+    def learned_path():
+        pred = c.predict(ch.segment_features(te))
+        return ch.compress_segments(te, pred), pred
+
+    (bl, pred), t_learned = timed(learned_path, reps=3)
+    bp, t_plain = timed(lambda: ch.compress_segments(te, plain_opts), reps=3)
+    learned_bytes = int(bl.nbytes.sum().item())
+    plain_bytes = int(bp.nbytes.sum().item())
+    best = int(sizes_te.min(dim=1).values.sum().item())
+    agree = float((pred.to(torch.int64) == torch.argmin(sizes_te, dim=1)).float().mean().item())
+    return ({"segments": int(nseg), "segment_samples": ch.SEG, "variant": "advanced",
+            "ratio_plain": raw / plain_bytes, "ratio_learned": raw / learned_bytes,
+            "ratio_exhaustive": raw / best, "learned_vs_exhaustive_loss": learned_bytes / best - 1.0,
+            "label_agreement": agree, "gbs_plain": raw / (t_plain / 1e3) / GB,
+            "gbs_learned": raw / (t_learned / 1e3) / GB, "train_s": train_s,
+            "note": "per-segment v1 streams in one batch launch per path; learned path includes features "
+                    "and the MLP; train on the first %d events, test on the last %d" % (train_events, test_events)},
+            c)
+
+
+def serve_metrics(dev, n_events, trained=None):
+    """The serving loop at 20k events/s (Poisson) from four camera
+    geometries, continuous batching under an 8 GB budget, chooser off and on."""
+    import numpy as np
+
+    from paper_1805_01844_gb300 import serve
+    from paper_1805_01844_gb300.chooser import Chooser
+
+    rng = np.random.default_rng(0)
+    pool = [(gi, serve.event_host(serve.GEOMETRIES[gi], 1000 + k))
+            for k, gi in enumerate([k % 4 for k in range(64)])]
+    ev = [pool[int(rng.integers(0, len(pool)))] for _ in range(n_events)]
+    out = {}
+    for name, ch in (("plain", None), ("learned", trained or Chooser(dev, seed=0))):
+        srv = serve.Server(dev, budget=8 << 30, n_streams=3, chooser=ch)
+        srv.run(ev[: min(500, n_events)], rate=20000.0, seed=1)  # warm-up
+        m = srv.run(ev, rate=20000.0, seed=2)
+        m.pop("kept", None)
+        out[name] = {k: m[k] for k in ("events", "rate_per_s", "p50_ms", "p99_ms", "gbs", "ratio", "wall_s",
+                                       "slots_per_stream")}
+    out["note"] = "learned = the chooser trained in the 'learned' section; events cycle a pool of 64"
+    return out
 
 
 def sampled_parity(x, sbuf, stream_bytes, variant, w, L, n_samples=64, seed=0):

@@ -14,7 +14,10 @@ class Batch:
     """Compress `tensors` (CUDA, contiguous, 16/32-bit) with per-stream
     `params` (native.PcParams) in one launch; outputs are v1 streams."""
 
-    def __init__(self, tensors, params, device=None):
+    def __init__(self, tensors, params, device=None, outs=None, workspace=None, stream=None):
+        """outs: optional caller-owned uint8 output tensors (one per item, each
+        at least pc_bound bytes, 16-byte aligned); workspace: optional
+        caller-owned uint8 tensor reused across launches."""
         assert len(tensors) == len(params) and tensors
         self.device = device or tensors[0].device
         self.tensors = tensors
@@ -29,19 +32,24 @@ class Batch:
             caps.append(cap)
             offs.append(total)
             total += (cap + 15) // 16 * 16
-        # every item's output is a 16-byte aligned slice of one buffer
-        self.buffer = torch.empty(max(total, 16), dtype=torch.uint8, device=self.device)
-        self.outs = [self.buffer[o:o + c] for o, c in zip(offs, caps)]
-        base = self.buffer.data_ptr()
+        if outs is None:
+            # every item's output is a 16-byte aligned slice of one buffer
+            self.buffer = torch.empty(max(total, 16), dtype=torch.uint8, device=self.device)
+            self.outs = [self.buffer[o:o + c] for o, c in zip(offs, caps)]
+        else:
+            self.outs = list(outs)
         nb = self.nbytes.data_ptr()
         for i, (x, p) in enumerate(zip(tensors, params)):
             items.append(native.PcBatchItem(x.data_ptr() if x.numel() else None, x.numel(), p,
-                                            base + offs[i], caps[i], nb + 8 * i))
+                                            self.outs[i].data_ptr(), self.outs[i].numel(), nb + 8 * i))
         self._arr, self.info = native.batch_describe(items)
         self.plan = torch.empty((self.info.plan_bytes + 15) // 16 * 16, dtype=torch.uint8, device=self.device)
-        self.ws = torch.empty((self.info.workspace_bytes + 15) // 16 * 16, dtype=torch.uint8, device=self.device)
-        native.batch_plan(self._arr, self.info, self.plan.data_ptr(),
-                          _stream_handle(None, self.device))
+        if workspace is not None and workspace.numel() >= self.info.workspace_bytes:
+            self.ws = workspace
+        else:
+            self.ws = torch.empty((self.info.workspace_bytes + 15) // 16 * 16, dtype=torch.uint8,
+                                  device=self.device)
+        native.batch_plan(self._arr, self.info, self.plan.data_ptr(), _stream_handle(stream, self.device))
 
     def compress(self, stream=None):
         st = native.compress_batch(self.info, self.plan.data_ptr(), self.ws.data_ptr(), self.ws.numel(),
