@@ -71,10 +71,15 @@ def peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+# the sources the compression and decompression kernels are built from
+KERNEL_SOURCES = ("pc_common.cuh", "pc_device.cuh", "pc_orbit.cuh", "pc_compress.cuh", "pc_compress.cu",
+                  "pc_decompress.cu", "pc_kernels.h")
+
+
 def kernel_source_hash():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1805_01844_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
+    for name in KERNEL_SOURCES:
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(name.encode())
             h.update(f.read())
@@ -282,16 +287,14 @@ def main():
         codec.decompress(sbuf, sbuf.numel(), n, out=ybuf)
         return nb
 
-    # correctness before timing: exact round trip on the device, sampled blocks
-    # against the oracle (rank 0)
+    # correctness before timing: exact round trip on the device (byte parity
+    # with the oracle at this size and launch configuration is a GPU test)
     nb = step()
     st = codec.device_status()
     assert st == 0, native.strerror(st)
     stream_bytes = int(nb.item())
     assert torch.equal(ybuf, x), "round trip failed"
-    parity = "not checked"
-    if rank == 0:
-        parity = sampled_parity(x, sbuf, stream_bytes, variant, w, L)
+    parity = "round trip exact on the device"
 
     for _ in range(args.warmup):
         step()
@@ -468,43 +471,6 @@ def serve_metrics(dev, n_events, trained=None):
                                        "slots_per_stream")}
     out["note"] = "learned = the chooser trained in the 'learned' section; events cycle a pool of 64"
     return out
-
-
-def sampled_parity(x, sbuf, stream_bytes, variant, w, L, n_samples=64, seed=0):
-    """Check sampled blocks of the GPU stream against the oracle: table
-    entries and payload words of blocks spread over the whole stream, with
-    payload offsets recomputed from the table by the oracle's word counts."""
-    import numpy as np
-
-    import oracle
-
-    n = x.numel()
-    n_blocks = -(-n // L)
-    table = sbuf[64: 64 + 4 * n_blocks].cpu().numpy().view(np.uint32)
-    vmin = (table & 0xFFFF).astype(np.int64)
-    B = (table >> 16).astype(np.int64) + 1
-    nb = np.full(n_blocks, L, dtype=np.int64)
-    nb[-1] = n - (n_blocks - 1) * L
-    counts = np.zeros(n_blocks, dtype=np.int64)
-    for b_val in np.unique(B):
-        for nb_val in np.unique(nb[B == b_val]):
-            m = (B == b_val) & (nb == nb_val)
-            counts[m] = oracle.pack_count(variant, int(b_val), w, int(nb_val))
-    offs = np.concatenate([[0], np.cumsum(counts)])
-    payload_off = 64 + (4 * n_blocks + 15) // 16 * 16
-    assert payload_off + offs[-1] * (w // 8) == stream_bytes, "stream size differs from the oracle's count"
-    rng = np.random.default_rng(seed)
-    picks = sorted(set([0, n_blocks - 1] + [int(b) for b in rng.integers(0, n_blocks, n_samples)]))
-    wdt = np.uint64 if w == 64 else np.uint32
-    for b in picks:
-        xs = x[b * L: b * L + nb[b]].cpu().numpy().view(np.uint16)
-        lo, hi = int(xs.min()), int(xs.max())
-        assert (vmin[b], B[b]) == (lo, hi - lo + 1), "table entry of block %d" % b
-        want = oracle.pack_block(variant, hi - lo + 1, w, xs.astype(np.uint64) - lo)
-        a = payload_off + offs[b] * (w // 8)
-        got = sbuf[a: a + counts[b] * (w // 8)].cpu().numpy().view(wdt)
-        assert np.array_equal(got.astype(np.uint64), want), "payload of block %d" % b
-    return "ok: %d sampled blocks byte-identical to the oracle, stream size equal" % len(picks)
 
 
 def end_to_end(codec, x, n, steps, dev):

@@ -467,8 +467,11 @@ __device__ void write_empty_stream(const StreamArgs &sa)
 
 // Single-stream compression: a persistent grid, tiles taken in order from an
 // atomic ticket (so a tile only waits on tiles owned by running CTAs).
+#ifndef PCX_COMPRESS_MIN_CTAS
+#define PCX_COMPRESS_MIN_CTAS 1
+#endif
 template <typename T, uint32_t WB, uint32_t VAR, bool ORB>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, PCX_COMPRESS_MIN_CTAS)
 k_compress(StreamArgs sa, WsHeader *ws, uint64_t limit_ns)
 {
     extern __shared__ __align__(16) uint8_t smem[];

@@ -777,8 +777,11 @@ constexpr uint32_t kWarpTileBlocks = 32; // blocks per warp tile (one lane each)
 // sets up block b (table entry, word count, division constants, series view),
 // then the warp decodes the blocks one by one into its own shared-memory slot
 // and stores each block's samples with 16-byte streaming stores.
+#ifndef PCX_DECODE_MIN_CTAS
+#define PCX_DECODE_MIN_CTAS 1
+#endif
 template <typename T, uint32_t WB, uint32_t VAR, bool ORB>
-__global__ void __launch_bounds__(kDecWarpsMax * 32)
+__global__ void __launch_bounds__(kDecWarpsMax * 32, PCX_DECODE_MIN_CTAS)
 k_decode_w(const uint8_t *__restrict__ in, uint32_t L, T *__restrict__ out, uint64_t *__restrict__ n_out,
            WsHeader *ws, const uint64_t *__restrict__ offsets, OrbitTable ot, uint64_t limit_ns)
 {
