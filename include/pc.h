@@ -253,6 +253,73 @@ pc_status pc_mlp_grad(const void *d_weights, const float *d_x, const uint8_t *d_
 pc_status pc_mlp_adam(float *d_master, void *d_weights, float *d_grad, float *d_m, float *d_v, uint32_t step,
                       float lr, pc_stream_t stream);
 
+/* ---- segments: the chooser's whole path on the device --------------------
+ * A list of sources (device sample arrays) is cut into segments of
+ * PC_SEGMENT_SAMPLES samples (the last segment of a source may be shorter; a
+ * source of 0 samples has no segment).  Segments are numbered over all
+ * sources in order.  Segment j of a source is an ordinary version-1 stream
+ * written to its fixed output slot d_out + j * seg_stride, its size to
+ * d_out_bytes[j]; seg_stride holds the stream of a full segment under every
+ * one of the PC_CHOOSER_OPTIONS options.  Features, choices and parameters
+ * stay in device memory, so features -> pc_mlp_forward -> compression runs
+ * without a host round trip:
+ *   pc_segments_describe   host only: sizes and launch facts
+ *   pc_segments_plan       one host-to-device copy of the source table
+ *   pc_segments_features   feature rows of every segment (one kernel)
+ *   pc_compress_segments   every segment with its own option: a memset, a
+ *                          kernel that writes one batch descriptor per
+ *                          segment, the persistent batch kernel, and (if any
+ *                          source has d_totals) a kernel adding to the totals.
+ * Feature 23 uses the segment's index within its source, so a segment's
+ * features, choice and stream do not depend on the other sources.  A source
+ * of 0 samples is skipped entirely (it adds nothing to its totals). */
+typedef struct {
+    const void *d_in;       /* device samples, 16-byte aligned (NULL if n_samples = 0) */
+    uint64_t n_samples;
+    void *d_out;            /* device, 16-byte aligned: slot j at d_out + j * seg_stride */
+    uint64_t out_capacity;  /* >= ceil(n_samples / 4096) * seg_stride, else PC_ERR_CAPACITY */
+    uint64_t *d_out_bytes;  /* device, [ceil(n_samples / 4096)] stream sizes */
+    uint64_t *d_totals;     /* device running totals of the source's stream, or NULL:
+                               [0] += 1 and [1] += the sum of its stream sizes per call */
+} pc_source;
+
+typedef struct {
+    uint32_t n_sources;
+    uint32_t dtype_bits;
+    uint32_t variant;
+    uint32_t smem_bytes;      /* dynamic shared memory of the batch launch */
+    uint32_t has_totals;      /* 1 if some source has d_totals */
+    uint32_t reserved;
+    uint64_t n_segments;      /* over all sources */
+    uint64_t seg_stride;      /* bytes per output slot, a multiple of 16 */
+    uint64_t plan_bytes;      /* device bytes pc_segments_plan writes */
+    uint64_t workspace_bytes; /* device workspace pc_compress_segments needs */
+} pc_segments_info;
+
+/* Validate the sources and fill *info.  Host only.  PC_ERR_UNSUPPORTED if
+ * the segment count reaches 2^31. */
+pc_status pc_segments_describe(const pc_source *src, uint32_t n_sources, uint32_t dtype_bits, uint32_t variant,
+                               pc_segments_info *info);
+
+/* Copy the source table to device memory d_plan (info->plan_bytes bytes,
+ * 16-byte aligned) on `stream`; src is read before the call returns. */
+pc_status pc_segments_plan(const pc_source *src, uint32_t n_sources, const pc_segments_info *info, void *d_plan,
+                           pc_stream_t stream);
+
+/* Feature rows of every segment into d_features[n_segments][24] (the
+ * features of pc_segment_features, segment index counted within its source). */
+pc_status pc_segments_features(const pc_segments_info *info, const void *d_plan, float *d_features,
+                               pc_stream_t stream);
+
+/* Compress every segment with option d_options[k] (device, [n_segments]).
+ * An option >= PC_CHOOSER_OPTIONS is recorded as PC_ERR_INVALID_ARG in the
+ * workspace status (pc_last_device_status) and that segment is compressed
+ * with option 0, so every slot still holds a valid stream of its samples.
+ * d_workspace: info->workspace_bytes, 16-byte aligned.  No-op if there are no
+ * segments.  Bounded waits as for pc_compress. */
+pc_status pc_compress_segments(const pc_segments_info *info, const void *d_plan, const uint8_t *d_options,
+                               void *d_workspace, uint64_t workspace_bytes, pc_stream_t stream);
+
 /* Compression without any device allocation, for callers that cannot
  * allocate device memory once they run: a data-acquisition loop that must not
  * call cudaMalloc mid-readout (it can fail under memory pressure or

@@ -11,7 +11,6 @@ import numpy as np
 import torch
 
 from . import native
-from .batch import Batch
 
 SEG = native.SEGMENT_SAMPLES
 OPTIONS = native.CHOOSER_OPTIONS
@@ -49,29 +48,111 @@ def segments(x):
     return [x[s:s + SEG] for s in range(0, n, SEG)]
 
 
+class Segments:
+    """Sources cut into segments of 4096 samples, each compressed on the
+    device with its own option (pc_segments_* in include/pc.h).  Segment j of
+    source i is a version-1 stream in slot j of outs[i] (slot = seg_stride
+    bytes), its size in nbytes[i][j].  Build once per set of sources; then
+    features() and compress(options) run without a host round trip."""
+
+    def __init__(self, sources, variant=native.ADVANCED, outs=None, nbytes=None, totals=None, workspace=None,
+                 stream=None):
+        """sources: CUDA sample tensors (one dtype); outs / nbytes: optional
+        caller-owned uint8 / int64 tensors per source; totals: optional int64
+        device tensors [2] per source (events, bytes), or None entries."""
+        assert sources
+        self.device = sources[0].device
+        self.sources = [x.reshape(-1) for x in sources]
+        self.dtype_bits = _bits(self.sources[0])
+        self.variant = variant
+        self.stride = native.segment_stride(self.dtype_bits, variant)
+        self.counts = [-(-x.numel() // SEG) for x in self.sources]
+        if outs is None:
+            total = sum(self.counts)
+            self.buffer = torch.empty(max(total, 1) * self.stride, dtype=torch.uint8, device=self.device)
+            self.sizes = torch.zeros(max(total, 1), dtype=torch.int64, device=self.device)
+            outs, nbytes, k = [], [], 0
+            for c in self.counts:
+                outs.append(self.buffer[k * self.stride:(k + c) * self.stride])
+                nbytes.append(self.sizes[k:k + c])
+                k += c
+        self.outs, self.nbytes = list(outs), list(nbytes)
+        totals = totals or [None] * len(self.sources)
+        src = []
+        for x, o, nb, t in zip(self.sources, self.outs, self.nbytes, totals):
+            if _bits(x) != self.dtype_bits:
+                raise TypeError("all sources must have the same sample width")
+            n = x.numel()
+            src.append(native.PcSource(x.data_ptr() if n else None, n, o.data_ptr() if n else None, o.numel(),
+                                       nb.data_ptr() if n else None, t.data_ptr() if t is not None else None))
+        self._arr, self.info = native.segments_describe(src, self.dtype_bits, variant)
+        self.n_segments = int(self.info.n_segments)
+        self.plan = torch.empty(max((self.info.plan_bytes + 15) // 16 * 16, 16), dtype=torch.uint8,
+                                device=self.device)
+        ws = self.info.workspace_bytes
+        if workspace is not None and workspace.numel() >= ws:
+            self.ws = workspace
+        else:
+            self.ws = torch.empty(max((ws + 15) // 16 * 16, 16), dtype=torch.uint8, device=self.device)
+        self._stream = stream
+        native.segments_plan(self._arr, self.info, self.plan.data_ptr(), self._handle())
+
+    def _handle(self):
+        s = self._stream if self._stream is not None else torch.cuda.current_stream(self.device)
+        return s.cuda_stream
+
+    def features(self):
+        """Feature rows [n_segments, 24] (FP32, device)."""
+        out = torch.empty((max(self.n_segments, 1), native.CHOOSER_FEATURES), dtype=torch.float32,
+                          device=self.device)
+        native.segments_features(self.info, self.plan.data_ptr(), out.data_ptr(), self._handle())
+        return out[:self.n_segments]
+
+    def compress(self, options):
+        """Compress every segment with its option (uint8 device tensor)."""
+        options = options.contiguous()
+        assert options.dtype == torch.uint8 and options.numel() >= self.n_segments
+        st = native.compress_segments(self.info, self.plan.data_ptr(), options.data_ptr(), self.ws.data_ptr(),
+                                      self.ws.numel(), self._handle())
+        if st != native.PC_OK:
+            raise native.PcError(st, "pc_compress_segments")
+
+    def device_status(self):
+        return native.last_device_status(self.ws.data_ptr(), self._handle())
+
+    def streams(self, i):
+        """Host bytes of every segment stream of source i (synchronises)."""
+        sizes = self.nbytes[i].cpu().tolist()
+        o = self.outs[i]
+        return [o[j * self.stride:j * self.stride + k].cpu().numpy().tobytes() for j, k in enumerate(sizes)]
+
+    def total_bytes(self):
+        return int(sum(int(nb.sum().item()) for nb in self.nbytes))
+
+
 def compress_segments(x, options, variant=native.ADVANCED):
-    """Compress every segment of x with its option in one batch launch;
-    returns the Batch (streams in .outs, sizes in .nbytes)."""
-    d = _bits(x)
-    segs = segments(x)
-    opts = options.tolist() if hasattr(options, "tolist") else list(options)
-    params = [option_params(int(o), d, variant) for o in opts]
-    b = Batch(segs, params)
-    b.compress()
-    return b
+    """Compress every segment of x with its option (device uint8 tensor or
+    list) in one pass; returns the Segments (streams in .outs[0], sizes in
+    .nbytes[0])."""
+    seg = Segments([x], variant)
+    if not torch.is_tensor(options):
+        options = torch.tensor(list(options), dtype=torch.uint8)
+    seg.compress(options.to(device=x.device, dtype=torch.uint8))
+    return seg
 
 
 def exhaustive_sizes(x, variant=native.ADVANCED):
     """Stream size of every segment under every option: [nseg, 12] int64
-    (12 batch launches, every segment compressed 12 times)."""
-    nseg = -(-x.numel() // SEG)
+    (every segment compressed 12 times on the device)."""
+    seg = Segments([x], variant)
+    nseg = seg.n_segments
     sizes = torch.empty((nseg, OPTIONS), dtype=torch.int64, device=x.device)
     for o in range(OPTIONS):
-        b = compress_segments(x, [o] * nseg, variant)
-        st = b.device_status()
+        seg.compress(torch.full((nseg,), o, dtype=torch.uint8, device=x.device))
+        st = seg.device_status()
         if st != native.PC_OK:
-            raise native.PcError(st, "pc_compress_batch (device)")
-        sizes[:, o] = b.nbytes
+            raise native.PcError(st, "pc_compress_segments (device)")
+        sizes[:, o] = seg.nbytes[0]
     return sizes
 
 

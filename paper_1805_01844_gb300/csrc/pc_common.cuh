@@ -263,6 +263,37 @@ PCX_HD uint64_t table_bytes(uint64_t n_blocks, uint32_t d)
     return round_up(n_blocks * 2u * (d / 8u), 16);
 }
 
+// Segments path (learned chooser): the device copy of a pc_source plus the
+// index of its first segment among all sources' segments.  An empty source
+// owns no segment.
+struct SourceDev {
+    const void *in;
+    uint64_t n;
+    void *out;
+    uint64_t *out_bytes;
+    uint64_t seg_first;
+    uint64_t *totals;
+};
+static_assert(sizeof(SourceDev) == 48, "source descriptors are 48 bytes");
+
+// Option o = 2 i + j of the chooser: block length 128 << i, word size 32 / 64.
+PCX_HD uint32_t option_block_len(uint32_t o) { return 128u << (o >> 1); }
+PCX_HD uint32_t option_word_bits(uint32_t o) { return (o & 1u) ? 64u : 32u; }
+
+// The source owning global segment k: the largest i with seg_first <= k
+// (empty sources share their successor's seg_first and precede it, so they
+// are never picked).
+PCX_HD uint32_t source_of(const SourceDev *src, uint32_t n_src, uint64_t k)
+{
+    uint32_t lo = 0, hi = n_src - 1;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi + 1) >> 1;
+        if (src[mid].seg_first <= k) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
 // Division of a 32-bit x by an invariant d >= 2 without a divide instruction:
 // q = (x * m + a) >> (32 + s).  Power of two d = 2^k: m = 2^(32-k), a = 0,
 // s = 0.  Otherwise s = floor(log2 d) and m = ceil(2^(32+s) / d) when

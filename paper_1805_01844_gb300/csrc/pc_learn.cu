@@ -29,16 +29,17 @@ static_assert(2 * NW + 4 * (NP - NW) == PC_MLP_WEIGHT_BYTES, "weight buffer size
 
 // ------------------------------------------------------------- features
 
-// One warp per segment; lane l summarises sub-block l (128 samples).
+// Features of segment `seg` of a source (in, n), written by one warp to f[24];
+// lane l summarises sub-block l (128 samples).  Sums are exact: integers for
+// 16-bit samples, doubles (integers below 2^53 per lane) for 32-bit ones.
 template <typename T>
-__global__ void k_features(const T *__restrict__ in, uint64_t n, uint32_t d, float *__restrict__ out,
-                           uint64_t n_seg)
+__device__ __forceinline__ void segment_features(const T *__restrict__ in, uint64_t n, uint64_t seg, uint32_t d,
+                                                 float *__restrict__ f)
 {
     const uint32_t lane = threadIdx.x & 31u;
-    const uint64_t seg = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (seg >= n_seg) return;
     const uint64_t s0 = seg * SEG + (uint64_t)lane * 128;
     uint32_t mn = 0xFFFFFFFFu, mx = 0, cnt = 0;
+    uint64_t isum = 0, isq = 0;
     double sum = 0.0, sq = 0.0;
     for (uint32_t i = 0; i < 128; ++i) {
         const uint64_t g = s0 + i;
@@ -46,9 +47,18 @@ __global__ void k_features(const T *__restrict__ in, uint64_t n, uint32_t d, flo
         const uint32_t v = in[g];
         mn = min(mn, v);
         mx = max(mx, v);
-        sum += v;
-        sq += (double)v * v;
+        if constexpr (sizeof(T) == 2) {
+            isum += v;
+            isq += (uint64_t)v * v;
+        } else {
+            sum += v;
+            sq += (double)v * v;
+        }
         ++cnt;
+    }
+    if constexpr (sizeof(T) == 2) {
+        sum = (double)isum;  // < 2^23 and < 2^39 per lane: exact
+        sq = (double)isq;
     }
     const uint32_t vmin = __reduce_min_sync(0xFFFFFFFFu, mn);
     const uint32_t vmax = __reduce_max_sync(0xFFFFFFFFu, mx);
@@ -73,7 +83,6 @@ __global__ void k_features(const T *__restrict__ in, uint64_t n, uint32_t d, flo
     const double dmax = d == 16 ? 65535.0 : 4294967295.0;
     const double mean = sum / tot;
     const double var = fmax(sq / tot - mean * mean, 0.0);
-    float *f = out + seg * F;
     if (lane < 16) f[3 + lane] = hist / 32.0f;
     if (lane == 0) {
         f[0] = (float)(vmin / dmax);
@@ -85,6 +94,27 @@ __global__ void k_features(const T *__restrict__ in, uint64_t n, uint32_t d, flo
         f[22] = d / 32.0f;
         f[23] = (float)(seg & 63u) / 64.0f;
     }
+}
+
+// One warp per segment of one array.
+template <typename T>
+__global__ void k_features(const T *__restrict__ in, uint64_t n, uint32_t d, float *__restrict__ out,
+                           uint64_t n_seg)
+{
+    const uint64_t seg = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (seg >= n_seg) return;
+    segment_features<T>(in, n, seg, d, out + seg * F);
+}
+
+// One warp per segment of a list of sources (segment index within its source).
+template <typename T>
+__global__ void k_features_sources(const SourceDev *__restrict__ src, uint32_t n_src, uint32_t d,
+                                   float *__restrict__ out, uint64_t n_seg)
+{
+    const uint64_t k = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (k >= n_seg) return;
+    const SourceDev s = src[source_of(src, n_src, k)];
+    segment_features<T>(static_cast<const T *>(s.in), s.n, k - s.seg_first, d, out + k * F);
 }
 
 // ------------------------------------------------------------------ MLP
@@ -280,6 +310,22 @@ pc_status pc_segment_features(const void *d_in, uint64_t n_samples, uint32_t dty
         k_features<uint16_t><<<grid, 256, 0, s>>>(static_cast<const uint16_t *>(d_in), n_samples, 16, d_features, n_seg);
     else
         k_features<uint32_t><<<grid, 256, 0, s>>>(static_cast<const uint32_t *>(d_in), n_samples, 32, d_features, n_seg);
+    return cudaGetLastError() == cudaSuccess ? PC_OK : PC_ERR_CUDA;
+}
+
+pc_status pc_segments_features(const pc_segments_info *info, const void *d_plan, float *d_features,
+                               pc_stream_t stream)
+{
+    if (!info || (info->dtype_bits != 16 && info->dtype_bits != 32)) return PC_ERR_INVALID_ARG;
+    if (info->n_segments == 0) return PC_OK;
+    if (!d_plan || !d_features || info->n_sources == 0) return PC_ERR_INVALID_ARG;
+    const SourceDev *src = static_cast<const SourceDev *>(d_plan);
+    const unsigned grid = (unsigned)ceil_div(info->n_segments * 32, 256);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (info->dtype_bits == 16)
+        k_features_sources<uint16_t><<<grid, 256, 0, s>>>(src, info->n_sources, 16, d_features, info->n_segments);
+    else
+        k_features_sources<uint32_t><<<grid, 256, 0, s>>>(src, info->n_sources, 32, d_features, info->n_segments);
     return cudaGetLastError() == cudaSuccess ? PC_OK : PC_ERR_CUDA;
 }
 

@@ -20,7 +20,8 @@ BASIC, ADVANCED = 0, 1
 EXPORTS = ("pc_bound", "pc_workspace_size", "pc_compress", "pc_decompress",
            "pc_parse_header", "pc_last_device_status", "pc_selftest_bounded_wait",
            "pc_strerror", "pc_compress_noalloc", "pc_batch_describe", "pc_batch_plan",
-           "pc_compress_batch", "pc_segment_features", "pc_mlp_forward", "pc_mlp_grad", "pc_mlp_adam")
+           "pc_compress_batch", "pc_segment_features", "pc_mlp_forward", "pc_mlp_grad", "pc_mlp_adam",
+           "pc_segments_describe", "pc_segments_plan", "pc_segments_features", "pc_compress_segments")
 SEGMENT_SAMPLES, CHOOSER_FEATURES, CHOOSER_OPTIONS = 4096, 24, 12
 MLP_PARAMS, MLP_WEIGHT_BYTES = 6540, 13360
 NOALLOC_SCRATCH_BYTES = 1 << 20
@@ -45,6 +46,19 @@ class PcBatchInfo(ctypes.Structure):
     _fields_ = [("n_items", ctypes.c_uint32), ("smem_bytes", ctypes.c_uint32),
                 ("total_tiles", ctypes.c_uint64), ("plan_bytes", ctypes.c_uint64),
                 ("workspace_bytes", ctypes.c_uint64)]
+
+
+class PcSource(ctypes.Structure):
+    _fields_ = [("d_in", ctypes.c_void_p), ("n_samples", ctypes.c_uint64), ("d_out", ctypes.c_void_p),
+                ("out_capacity", ctypes.c_uint64), ("d_out_bytes", ctypes.c_void_p),
+                ("d_totals", ctypes.c_void_p)]
+
+
+class PcSegmentsInfo(ctypes.Structure):
+    _fields_ = [("n_sources", ctypes.c_uint32), ("dtype_bits", ctypes.c_uint32), ("variant", ctypes.c_uint32),
+                ("smem_bytes", ctypes.c_uint32), ("has_totals", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("n_segments", ctypes.c_uint64), ("seg_stride", ctypes.c_uint64),
+                ("plan_bytes", ctypes.c_uint64), ("workspace_bytes", ctypes.c_uint64)]
 
 
 class PcError(RuntimeError):
@@ -103,6 +117,16 @@ def load(path=LIB_PATH):
     L.pc_mlp_grad.restype = st
     L.pc_mlp_adam.argtypes = [f32p, vp, f32p, f32p, f32p, u32, ctypes.c_float, vp]
     L.pc_mlp_adam.restype = st
+    sp = ctypes.POINTER(PcSource)
+    gp = ctypes.POINTER(PcSegmentsInfo)
+    L.pc_segments_describe.argtypes = [sp, u32, u32, u32, gp]
+    L.pc_segments_describe.restype = st
+    L.pc_segments_plan.argtypes = [sp, u32, gp, vp, vp]
+    L.pc_segments_plan.restype = st
+    L.pc_segments_features.argtypes = [gp, vp, f32p, vp]
+    L.pc_segments_features.restype = st
+    L.pc_compress_segments.argtypes = [gp, vp, vp, vp, u64, vp]
+    L.pc_compress_segments.restype = st
     L.pc_strerror.argtypes = [st]
     L.pc_strerror.restype = ctypes.c_char_p
     _lib = L
@@ -187,3 +211,36 @@ def batch_plan(arr, info, d_plan, stream):
 def compress_batch(info, d_plan, d_ws, ws_bytes, stream):
     """pc_compress_batch; returns the host status."""
     return load().pc_compress_batch(ctypes.byref(info), d_plan, d_ws, int(ws_bytes), stream or None)
+
+
+def segments_describe(sources, dtype_bits, variant):
+    """sources: list of PcSource.  Returns (ctypes array, PcSegmentsInfo)."""
+    arr = (PcSource * len(sources))(*sources)
+    info = PcSegmentsInfo()
+    _check(load().pc_segments_describe(arr, len(sources), dtype_bits, variant, ctypes.byref(info)),
+           "pc_segments_describe")
+    return arr, info
+
+
+def segments_plan(arr, info, d_plan, stream):
+    _check(load().pc_segments_plan(arr, info.n_sources, ctypes.byref(info), d_plan, stream or None),
+           "pc_segments_plan")
+
+
+def segments_features(info, d_plan, d_features, stream):
+    _check(load().pc_segments_features(ctypes.byref(info), d_plan, d_features, stream or None),
+           "pc_segments_features")
+
+
+def compress_segments(info, d_plan, d_options, d_ws, ws_bytes, stream):
+    """pc_compress_segments; returns the host status."""
+    return load().pc_compress_segments(ctypes.byref(info), d_plan, d_options, d_ws, int(ws_bytes), stream or None)
+
+
+def segment_stride(dtype_bits, variant):
+    """Output slot bytes per segment (pc_segments_describe of a one-segment
+    probe; needs no device memory: the pointers are never dereferenced)."""
+    src = PcSource(16, 1, 16, 1 << 40, 8, None)
+    _, info = segments_describe([src], dtype_bits, variant)
+    return info.seg_stride
+

@@ -13,9 +13,11 @@ overlap on the GPU while new events keep arriving.  When a batch's completion
 event fires, its slots are freed.  Latency = completion time - arrival time.
 
 With the learned chooser on, each event is cut into segments of 4096 samples
-whose parameters the MLP picks (one batch item per segment, written one after
-the other into the event's output slot); otherwise each event is one item
-with the plain parameters.
+whose parameters the MLP picks; features, choices and the per-segment
+compression of all admitted events run on the device without a host round
+trip (pc_segments_*), each segment's stream in its own slot of the event's
+output area.  Otherwise each event is one batch item with the plain
+parameters.
 """
 import time
 from collections import deque
@@ -25,6 +27,7 @@ import torch
 
 from . import native
 from .batch import Batch
+from .chooser import Segments
 
 GEOMETRIES = ((1855, 40), (2048, 128), (11328, 25), (1296, 64))  # pixels x samples
 
@@ -39,53 +42,28 @@ def event_host(geom, seed):
     return np.clip(x, 0, 65535).astype(np.uint16).reshape(-1)
 
 
-def _event_items(x, out, variant, base_params, chooser):
-    """Batch items of one event (an input slot x, an output slot out)."""
-    if chooser is None:
-        return [x], [base_params], [out]
-    from .chooser import SEG, option_params, segment_features
-
-    opts = chooser.predict(segment_features(x)).cpu().tolist()
-    tensors, params, outs, off = [], [], [], 0
-    for k, o in enumerate(opts):
-        seg = x[k * SEG:(k + 1) * SEG]
-        p = option_params(int(o), 16, variant)
-        cap = (native.bound(p, seg.numel()) + 15) // 16 * 16
-        tensors.append(seg)
-        params.append(p)
-        outs.append(out[off:off + cap])
-        off += cap
-    return tensors, params, outs
-
-
 def event_out_bytes(n, base_params, chooser_on):
-    """Output slot size of an event of n samples (all segment streams fit)."""
+    """Output slot size of an event of n samples: its whole stream, or with
+    the chooser one segment slot per 4096 samples."""
     if not chooser_on:
         return (native.bound(base_params, n) + 15) // 16 * 16
-    from .chooser import SEG
-
-    worst = 0
-    for k in range(0, n, SEG):
-        m = min(SEG, n - k)
-        worst += max((native.bound(native.params(base_params.variant, 16, w, L), m) + 15) // 16 * 16
-                     for L in (128, 256, 512, 1024, 2048, 4096) for w in (32, 64))
-    return worst
+    return -(-n // native.SEGMENT_SAMPLES) * native.segment_stride(16, base_params.variant)
 
 
 class StreamPool:
-    """Per-camera slots in HBM: inputs, output streams, device totals."""
+    """Per-camera slots in HBM: inputs, output streams, segment sizes."""
 
-    def __init__(self, geom, slots, out_bytes, device):
+    def __init__(self, geom, slots, out_bytes, device, totals):
         self.geom = geom
         self.n = geom[0] * geom[1]
         self.inp = torch.empty((slots, self.n), dtype=torch.int16, device=device)
         self.out = torch.empty((slots, out_bytes), dtype=torch.uint8, device=device)
+        self.nbytes = torch.zeros((slots, -(-self.n // native.SEGMENT_SAMPLES)), dtype=torch.int64, device=device)
         self.free = deque(range(slots))
-        self.events = torch.zeros(1, dtype=torch.int64, device=device)
-        self.bytes = torch.zeros(1, dtype=torch.int64, device=device)
+        self.totals = totals  # device int64 [2]: events, compressed bytes
 
-    def nbytes(self):
-        return self.inp.numel() * 2 + self.out.numel()
+    def nbytes_held(self):
+        return self.inp.numel() * 2 + self.out.numel() + self.nbytes.numel() * 8
 
 
 class Server:
@@ -96,14 +74,18 @@ class Server:
         self.chooser = chooser
         self.params = native.params(variant, 16, word_bits, block_len)
         outb = [event_out_bytes(g[0] * g[1], self.params, chooser is not None) for g in GEOMETRIES]
-        per_event = sum(g[0] * g[1] * 2 + o for g, o in zip(GEOMETRIES, outb))
-        ws_reserve = n_streams * (40 << 20)  # batch workspaces (series tables + look-back words)
+        per_event = sum(g[0] * g[1] * 2 + o + 8 * -(-g[0] * g[1] // native.SEGMENT_SAMPLES)
+                        for g, o in zip(GEOMETRIES, outb))
+        ws_reserve = n_streams * (48 << 20)  # launch workspaces (series tables, look-back words, plans)
         slots = int(max(1, min(slot_cap, (budget - ws_reserve) // per_event)))
-        self.pools = [StreamPool(g, slots, o, self.device) for g, o in zip(GEOMETRIES, outb)]
+        # per-stream running totals (events, compressed bytes) stay on the device
+        self.totals = torch.zeros((len(GEOMETRIES), 2), dtype=torch.int64, device=self.device)
+        self.pools = [StreamPool(g, slots, o, self.device, self.totals[i])
+                      for i, (g, o) in enumerate(zip(GEOMETRIES, outb))]
         self.cuda_streams = [torch.cuda.Stream(self.device) for _ in range(n_streams)]
         self.workspaces = [None] * n_streams
         self.budget = budget
-        assert sum(p.nbytes() for p in self.pools) + ws_reserve <= budget
+        assert sum(p.nbytes_held() for p in self.pools) + ws_reserve <= budget
 
     def run(self, events, rate=20000.0, seed=0, keep=()):
         """Serve events = [(geometry index, host uint16 array)] arriving as a
@@ -116,6 +98,7 @@ class Server:
         waiting, admitted, inflight = deque(), [], deque()
         done_time = np.zeros(len(events))
         kept, raw, nxt, finished, rr = {}, 0, 0, 0, 0
+        self.totals.zero_()
         t0 = time.perf_counter()
         while finished < len(events):
             now = time.perf_counter() - t0
@@ -126,12 +109,10 @@ class Server:
             while inflight and inflight[0][0].query():
                 _, members, b = inflight.popleft()
                 tdone = time.perf_counter() - t0
-                if keep & {m[0] for m in members}:
-                    sizes = b.nbytes.cpu().tolist()
-                for e, gi, slot, lo, hi in members:
+                for k, (e, gi, slot) in enumerate(members):
                     done_time[e] = tdone
                     if e in keep:
-                        kept[e] = [b.outs[k][:sizes[k]].cpu().numpy().tobytes() for k in range(lo, hi)]
+                        kept[e] = _streams_of(b, k)
                     self.pools[gi].free.append(slot)
                     finished += 1
             # admit arrived events into free slots of their stream
@@ -150,35 +131,13 @@ class Server:
                 else:
                     still.append(e)
             waiting = still
-            # one batch launch over everything admitted since the last one
+            # one launch sequence over everything admitted since the last one
             if admitted:
                 with torch.cuda.stream(stream):
-                    tensors, params, outs, members = [], [], [], []
-                    for e, gi, slot in admitted:
-                        pool = self.pools[gi]
-                        tt, pp, oo = _event_items(pool.inp[slot], pool.out[slot], self.variant, self.params,
-                                                  self.chooser)
-                        members.append((e, gi, slot, len(tensors), len(tensors) + len(tt)))
-                        tensors += tt
-                        params += pp
-                        outs += oo
-                    b = Batch(tensors, params, device=self.device, outs=outs, workspace=self.workspaces[si],
-                              stream=stream)
-                    self.workspaces[si] = b.ws
-                    b.compress(stream=stream)
-                    # per-stream totals stay on the device
-                    item_stream = torch.tensor([gi for (_, gi, _, lo, hi) in members for _ in range(lo, hi)],
-                                               device=self.device)
-                    per = torch.zeros(len(self.pools), dtype=torch.int64, device=self.device)
-                    per.index_add_(0, item_stream, b.nbytes)
-                    cnt = torch.bincount(torch.tensor([gi for (_, gi, _) in admitted], device=self.device),
-                                         minlength=len(self.pools))
-                    for pi, pool in enumerate(self.pools):
-                        pool.bytes += per[pi]
-                        pool.events += cnt[pi]
+                    b = self._launch(admitted, si, stream)
                     ev = torch.cuda.Event()
                     ev.record(stream)
-                inflight.append((ev, members, b))
+                inflight.append((ev, admitted, b))
                 admitted = []
                 rr += 1
             elif nxt < len(events) and not waiting:
@@ -188,7 +147,9 @@ class Server:
         wall = time.perf_counter() - t0
         torch.cuda.synchronize(self.device)
         lat = (done_time - arrivals) * 1e3
-        comp = int(sum(int(p.bytes.item()) for p in self.pools))
+        tot = self.totals.cpu().numpy()
+        comp = int(tot[:, 1].sum())
+        assert int(tot[:, 0].sum()) == len(events)
         return {"events": len(events), "rate_per_s": rate, "wall_s": wall,
                 "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                 "gbs": raw / wall / 1e9, "raw_bytes": raw, "stream_bytes": comp,
@@ -196,14 +157,50 @@ class Server:
                 "budget_bytes": self.budget, "slots_per_stream": int(self.pools[0].inp.shape[0]),
                 "kept": kept}
 
+    def _launch(self, admitted, si, stream):
+        """Compress the admitted events (e, pool, slot) on `stream`: the plain
+        path is one batch launch with one item per event; with the chooser,
+        features, the MLP and the per-segment compression of all of them."""
+        if self.chooser is not None:
+            pools = [self.pools[gi] for _, gi, _ in admitted]
+            seg = Segments([p.inp[slot] for p, (_, _, slot) in zip(pools, admitted)], self.variant,
+                           outs=[p.out[slot] for p, (_, _, slot) in zip(pools, admitted)],
+                           nbytes=[p.nbytes[slot] for p, (_, _, slot) in zip(pools, admitted)],
+                           totals=[p.totals for p in pools], workspace=self.workspaces[si], stream=stream)
+            self.workspaces[si] = seg.ws
+            seg.compress(self.chooser.predict(seg.features()))
+            return seg
+        tensors = [self.pools[gi].inp[slot] for _, gi, slot in admitted]
+        outs = [self.pools[gi].out[slot] for _, gi, slot in admitted]
+        b = Batch(tensors, [self.params] * len(tensors), device=self.device, outs=outs,
+                  workspace=self.workspaces[si], stream=stream)
+        self.workspaces[si] = b.ws
+        b.compress(stream=stream)
+        idx = torch.tensor([gi for _, gi, _ in admitted], dtype=torch.int64).pin_memory()
+        idx = idx.to(self.device, non_blocking=True)
+        self.totals[:, 1].index_add_(0, idx, b.nbytes)
+        self.totals[:, 0].index_add_(0, idx, torch.ones_like(b.nbytes))
+        b.idx = idx  # kept alive until the launch completes
+        return b
+
+
+def _streams_of(b, k):
+    """Host bytes of the streams of member k of a finished launch."""
+    if isinstance(b, Segments):
+        return b.streams(k)
+    n = int(b.nbytes[k].item())
+    return [b.outs[k][:n].cpu().numpy().tobytes()]
+
 
 def compress_alone(x, variant=native.ADVANCED, block_len=1024, word_bits=64, chooser=None):
-    """The same event compressed on its own (one batch of its items)."""
+    """The same event compressed on its own: its stream, or with the chooser
+    the streams of its segments."""
     x = x.contiguous()
+    if chooser is not None:
+        seg = Segments([x], variant)
+        seg.compress(chooser.predict(seg.features()))
+        return seg.streams(0)
     p = native.params(variant, 16, word_bits, block_len)
-    out = torch.empty(event_out_bytes(x.numel(), p, chooser is not None), dtype=torch.uint8, device=x.device)
-    tt, pp, oo = _event_items(x, out, variant, p, chooser)
-    b = Batch(tt, pp, outs=oo)
+    b = Batch([x], [p])
     b.compress()
-    sizes = b.nbytes.cpu().tolist()
-    return [b.outs[k][:sizes[k]].cpu().numpy().tobytes() for k in range(len(tt))]
+    return _streams_of(b, 0)

@@ -129,3 +129,47 @@ int main() {
     subprocess.check_call(["g++", "-std=c++17", "-O1", "-I" + os.path.join(ROOT, "include"),
                            "-I" + os.path.join(ROOT, "paper_1805_01844_gb300", "csrc"), str(src), "-o", str(exe)])
     assert subprocess.run([str(exe)], capture_output=True, text=True).stdout.strip() == "ok"
+
+
+@pytest.mark.parametrize("d", [16, 32])
+@pytest.mark.parametrize("variant", [0, 1])
+def test_segment_slots_hold_every_option(lib, d, variant):
+    """The segment slot is the largest stream of a full segment over the 12
+    options (the oracle's bound), rounded up to 16 bytes."""
+    want = max(oracle.bound(variant, d, (32, 64)[o % 2], 128 << (o // 2), 4096) for o in range(12))
+    assert native.segment_stride(d, variant) == (want + 15) // 16 * 16
+
+
+def test_segments_describe_checks_on_the_host(lib):
+    fake = 1 << 40
+    stride = native.segment_stride(16, 1)
+
+    def src(n, d_in=fake, d_out=fake, cap=None, nb=fake, tot=None):
+        k = -(-n // 4096)
+        return native.PcSource(d_in, n, d_out, k * stride if cap is None else cap, nb, tot)
+
+    def code(sources, d=16, variant=1):
+        arr = (native.PcSource * len(sources))(*sources)
+        info = native.PcSegmentsInfo()
+        return lib.pc_segments_describe(arr, len(sources), d, variant, ctypes.byref(info)), info
+
+    st, info = code([src(10000), src(0, None, None, 0, None), src(4096, tot=fake + 16)])
+    assert st == native.PC_OK
+    assert (info.n_segments, info.seg_stride, info.has_totals, info.n_sources) == (4, stride, 1, 3)
+    assert info.plan_bytes == 3 * 48 and info.workspace_bytes > 4 * 64
+    assert code([src(10000)], d=8)[0] == native.PC_ERR_INVALID_ARG
+    assert code([src(10000)], variant=2)[0] == native.PC_ERR_INVALID_ARG
+    assert code([src(10000, d_in=fake + 2)])[0] == native.PC_ERR_INVALID_ARG
+    assert code([src(10000, d_out=fake + 8)])[0] == native.PC_ERR_INVALID_ARG
+    assert code([src(10000, nb=fake + 4)])[0] == native.PC_ERR_INVALID_ARG
+    assert code([src(10000, tot=fake + 4)])[0] == native.PC_ERR_INVALID_ARG
+    assert code([src(10000, d_in=None)])[0] == native.PC_ERR_INVALID_ARG
+    assert code([src(10000, cap=3 * stride - 1)])[0] == native.PC_ERR_CAPACITY
+    assert code([src(1 << 43)])[0] == native.PC_ERR_UNSUPPORTED  # 2^31 segments
+    arr = (native.PcSource * 1)(src(10))
+    assert lib.pc_segments_describe(arr, 0, 16, 1, ctypes.byref(native.PcSegmentsInfo())) == \
+        native.PC_ERR_INVALID_ARG
+    # no segments at all: nothing to do, and compressing is a no-op
+    st, info = code([src(0, None, None, 0, None)])
+    assert st == native.PC_OK and info.n_segments == 0
+    assert native.compress_segments(info, None, None, None, 0, None) == native.PC_OK

@@ -96,4 +96,4 @@ def test_trained_chooser_beats_plain_heuristic():
     # the learned options through the GPU batch path give exactly those sizes
     b = ch.compress_segments(to_dev(xte), pred)
     assert b.device_status() == 0
-    assert int(b.nbytes.sum().item()) == learned
+    assert b.total_bytes() == learned

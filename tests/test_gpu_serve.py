@@ -46,3 +46,22 @@ def test_results_identical_alone_and_in_the_mix(use_chooser):
         # every piece is a stream of its segment (or of the whole event)
         y = np.concatenate([oracle.decompress(s) for s in alone])
         assert np.array_equal(y, x)
+
+
+@pytest.mark.parametrize("use_chooser", [False, True])
+def test_device_totals_match_streams(use_chooser):
+    """The per-camera totals kept in device memory add up every event's
+    streams exactly once."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    dev = torch.device("cuda:0")
+    ch = Chooser(dev, seed=2) if use_chooser else None
+    srv = serve.Server(dev, budget=1 << 30, n_streams=2, chooser=ch, slot_cap=8)
+    ev = events(120, seed=7)
+    m = srv.run(ev, rate=50000.0, seed=3, keep=range(120))
+    assert m["stream_bytes"] == sum(len(s) for e in range(120) for s in m["kept"][e])
+    per = srv.totals.cpu().numpy()
+    for gi in range(len(serve.GEOMETRIES)):
+        mine = [e for e in range(120) if ev[e][0] == gi]
+        assert per[gi, 0] == len(mine)
+        assert per[gi, 1] == sum(len(s) for e in mine for s in m["kept"][e])
