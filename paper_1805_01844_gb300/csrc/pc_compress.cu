@@ -12,6 +12,10 @@ static cudaError_t launch_compress_t(const LaunchArgs &a)
     const TileCfg cfg = tile_cfg(kKernelCompress, VAR, sizeof(T) * 8, WB, a.L, ORB);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.smem);
     if (e != cudaSuccess) return e;
+    // all of the unified L1 / shared storage as shared memory, so that the
+    // register-allowed tiles per SM also fit in shared memory
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
     int per_sm = 0, dev = 0, sms = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;

@@ -227,53 +227,67 @@ __device__ __forceinline__ void adv_words_orbit(const OrbitTable &ot, const Orbi
     }
 }
 
-// Basic words of one block by one warp, four words per lane in lockstep so
-// that their Horner chains are independent for the scheduler.  Lanes past the
-// last word recompute the last word and do not store it.
+// Basic words j0 + lane + 32 k (k < NK) of one block by one warp, NK words
+// per lane in lockstep so that their Horner chains are independent for the
+// scheduler.  Lanes past the last word recompute the last word and do not
+// store it.
+template <typename T, uint32_t WB, uint32_t NK>
+__device__ __forceinline__ void pack_basic_group(const T *u, uint32_t j0, uint32_t W, uint32_t p, uint32_t B32,
+                                                 uint64_t K, typename WordOf<T, WB>::type *dst)
+{
+    using Word = typename WordOf<T, WB>::type;
+    const uint32_t lane = threadIdx.x & 31u;
+    const T *g[NK];
+#pragma unroll
+    for (uint32_t k = 0; k < NK; ++k) {
+        const uint32_t j = min(j0 + lane + 32 * k, W - 1);
+        g[k] = u + j * p;
+    }
+    Word acc[NK];
+    if constexpr (WB == 32) {
+        uint32_t a[NK];
+#pragma unroll
+        for (uint32_t k = 0; k < NK; ++k) a[k] = g[k][p - 1];
+        for (int d = (int)p - 2; d >= 0; --d) {
+#pragma unroll
+            for (uint32_t k = 0; k < NK; ++k) a[k] = a[k] * B32 + (uint32_t)g[k][d];
+        }
+#pragma unroll
+        for (uint32_t k = 0; k < NK; ++k) acc[k] = a[k] - (uint32_t)K;
+    } else {
+        uint32_t lo[NK], hi[NK];
+#pragma unroll
+        for (uint32_t k = 0; k < NK; ++k) {
+            lo[k] = g[k][p - 1];
+            hi[k] = 0;
+        }
+        for (int d = (int)p - 2; d >= 0; --d) {
+#pragma unroll
+            for (uint32_t k = 0; k < NK; ++k) mad64(lo[k], hi[k], B32, (uint32_t)g[k][d]);
+        }
+#pragma unroll
+        for (uint32_t k = 0; k < NK; ++k) acc[k] = (((uint64_t)hi[k] << 32) | lo[k]) - K;
+    }
+#pragma unroll
+    for (uint32_t k = 0; k < NK; ++k) {
+        const uint32_t j = j0 + lane + 32 * k;
+        if (j < W) dst[j] = acc[k];
+    }
+}
+
+// Basic words of one block by one warp: groups of 128 words (four per lane),
+// then the last 1..127 words in the fewest lockstep slots per lane.
 template <typename T, uint32_t WB>
 __device__ __forceinline__ void pack_basic_block(const T *u, uint32_t W, uint32_t p, uint32_t B32, uint64_t K,
                                                  typename WordOf<T, WB>::type *dst)
 {
-    using Word = typename WordOf<T, WB>::type;
-    const uint32_t lane = threadIdx.x & 31u;
-    for (uint32_t j0 = 0; j0 < W; j0 += 128) {
-        const T *g[4];
-#pragma unroll
-        for (uint32_t k = 0; k < 4; ++k) {
-            const uint32_t j = min(j0 + lane + 32 * k, W - 1);
-            g[k] = u + j * p;
-        }
-        Word acc[4];
-        if constexpr (WB == 32) {
-            uint32_t a[4];
-#pragma unroll
-            for (uint32_t k = 0; k < 4; ++k) a[k] = g[k][p - 1];
-            for (int d = (int)p - 2; d >= 0; --d) {
-#pragma unroll
-                for (uint32_t k = 0; k < 4; ++k) a[k] = a[k] * B32 + (uint32_t)g[k][d];
-            }
-#pragma unroll
-            for (uint32_t k = 0; k < 4; ++k) acc[k] = a[k] - (uint32_t)K;
-        } else {
-            uint32_t lo[4], hi[4];
-#pragma unroll
-            for (uint32_t k = 0; k < 4; ++k) {
-                lo[k] = g[k][p - 1];
-                hi[k] = 0;
-            }
-            for (int d = (int)p - 2; d >= 0; --d) {
-#pragma unroll
-                for (uint32_t k = 0; k < 4; ++k) mad64(lo[k], hi[k], B32, (uint32_t)g[k][d]);
-            }
-#pragma unroll
-            for (uint32_t k = 0; k < 4; ++k) acc[k] = (((uint64_t)hi[k] << 32) | lo[k]) - K;
-        }
-#pragma unroll
-        for (uint32_t k = 0; k < 4; ++k) {
-            const uint32_t j = j0 + lane + 32 * k;
-            if (j < W) dst[j] = acc[k];
-        }
-    }
+    uint32_t j0 = 0;
+    for (; j0 + 128 <= W; j0 += 128) pack_basic_group<T, WB, 4>(u, j0, W, p, B32, K, dst);
+    const uint32_t rest = W - j0;
+    if (rest > 96) pack_basic_group<T, WB, 4>(u, j0, W, p, B32, K, dst);
+    else if (rest > 64) pack_basic_group<T, WB, 3>(u, j0, W, p, B32, K, dst);
+    else if (rest > 32) pack_basic_group<T, WB, 2>(u, j0, W, p, B32, K, dst);
+    else if (rest > 0) pack_basic_group<T, WB, 1>(u, j0, W, p, B32, K, dst);
 }
 
 // One stream as the compression kernels see it.
@@ -467,11 +481,20 @@ __device__ void write_empty_stream(const StreamArgs &sa)
 
 // Single-stream compression: a persistent grid, tiles taken in order from an
 // atomic ticket (so a tile only waits on tiles owned by running CTAs).
-#ifndef PCX_COMPRESS_MIN_CTAS
-#define PCX_COMPRESS_MIN_CTAS 1
+// CTAs per SM the register allocation must allow: basic tiles (74 KB of
+// shared memory) fit three to an SM once registers are capped at 85; advanced
+// tiles (100 KB) fit two.
+#ifndef PCX_COMPRESS_MIN_CTAS_BASIC
+#define PCX_COMPRESS_MIN_CTAS_BASIC 3
 #endif
+#ifndef PCX_COMPRESS_MIN_CTAS_ADVANCED
+#define PCX_COMPRESS_MIN_CTAS_ADVANCED 2
+#endif
+template <uint32_t VAR>
+constexpr int kCompressMinCtas = VAR == PC_VARIANT_BASIC ? PCX_COMPRESS_MIN_CTAS_BASIC : PCX_COMPRESS_MIN_CTAS_ADVANCED;
+
 template <typename T, uint32_t WB, uint32_t VAR, bool ORB>
-__global__ void __launch_bounds__(kThreads, PCX_COMPRESS_MIN_CTAS)
+__global__ void __launch_bounds__(kThreads, kCompressMinCtas<VAR>)
 k_compress(StreamArgs sa, WsHeader *ws, uint64_t limit_ns)
 {
     extern __shared__ __align__(16) uint8_t smem[];

@@ -597,100 +597,117 @@ k_decode(const uint8_t *__restrict__ in, uint32_t L, T *__restrict__ out, uint64
     }
 }
 
-// Basic words of one block by one warp, four words per lane in lockstep (four
-// independent division chains).  Digits land at u[j p + i]; lanes past the
-// last word write theirs to `junk`.  Returns true if a word is not the image
-// of valid digits.
-template <typename T, uint32_t WB>
-__device__ __forceinline__ bool decode_basic_block(const typename WordT<T, WB>::type *src /* shared */, T *u,
-                                                   T *junk,
-                                                   uint32_t W, uint32_t p, uint32_t hstar, uint64_t B,
-                                                   uint32_t vmin, Magic32 mg, uint64_t Dh, uint64_t MD)
+// Basic words j0 + lane + 32 k (k < NK) of one block, NK words per lane in
+// lockstep (NK independent division chains).  Digits land at u[j p + i];
+// lanes past the last word write theirs to `junk`.  Returns true if a word is
+// not the image of valid digits.
+template <typename T, uint32_t WB, uint32_t NK>
+__device__ __forceinline__ bool decode_basic_group(const typename WordT<T, WB>::type *src /* shared */, T *u,
+                                                   T *junk, uint32_t j0, uint32_t W, uint32_t p, uint32_t hstar,
+                                                   uint64_t B, uint32_t vmin, Magic32 mg, uint64_t Dh, uint64_t MD)
 {
     using Word = typename WordT<T, WB>::type;
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t B32 = (uint32_t)B;
     bool bad = false;
-    for (uint32_t j0 = 0; j0 < W; j0 += 128) {
-        Word sv[4];
-        T *d[4];
-        bool ok[4];
+    {
+        Word sv[NK];
+        T *d[NK];
+        bool ok[NK];
 #pragma unroll
-        for (uint32_t k = 0; k < 4; ++k) {
+        for (uint32_t k = 0; k < NK; ++k) {
             const uint32_t j = j0 + lane + 32 * k;
             ok[k] = j < W;
             sv[k] = ok[k] ? src[j] : Word(0);  // src is the warp's shared-memory word buffer
             d[k] = ok[k] ? u + j * p : junk;
         }
-        uint32_t x[4];
+        uint32_t x[NK];
         uint32_t off = 0, rem = p;
         if (WB == 64 && p > hstar) {
             // split each word into pieces of h* digits (B^h* <= 2^32)
-            uint64_t hv[4];
+            uint64_t hv[NK];
 #pragma unroll
-            for (uint32_t k = 0; k < 4; ++k) {
+            for (uint32_t k = 0; k < NK; ++k) {
                 uint64_t lo;
                 hv[k] = divmod_inv64(sv[k], Dh, MD, lo);
                 x[k] = (uint32_t)lo;
             }
             for (uint32_t i = 0; i + 1 < hstar; ++i) {
 #pragma unroll
-                for (uint32_t k = 0; k < 4; ++k) {
+                for (uint32_t k = 0; k < NK; ++k) {
                     const uint32_t q = magic_div(x[k], mg);
                     d[k][i] = (T)(x[k] - q * B32 + vmin);
                     x[k] = q;
                 }
             }
 #pragma unroll
-            for (uint32_t k = 0; k < 4; ++k) d[k][hstar - 1] = (T)(x[k] + vmin);
+            for (uint32_t k = 0; k < NK; ++k) d[k][hstar - 1] = (T)(x[k] + vmin);
             off = hstar;
             rem = p - hstar;
             if (rem > hstar) {  // p = 2 h* + 1: a middle piece of h* digits
 #pragma unroll
-                for (uint32_t k = 0; k < 4; ++k) {
+                for (uint32_t k = 0; k < NK; ++k) {
                     uint64_t lo;
                     hv[k] = divmod_inv64(hv[k], Dh, MD, lo);
                     x[k] = (uint32_t)lo;
                 }
                 for (uint32_t i = 0; i + 1 < hstar; ++i) {
 #pragma unroll
-                    for (uint32_t k = 0; k < 4; ++k) {
+                    for (uint32_t k = 0; k < NK; ++k) {
                         const uint32_t q = magic_div(x[k], mg);
                         d[k][off + i] = (T)(x[k] - q * B32 + vmin);
                         x[k] = q;
                     }
                 }
 #pragma unroll
-                for (uint32_t k = 0; k < 4; ++k) d[k][off + hstar - 1] = (T)(x[k] + vmin);
+                for (uint32_t k = 0; k < NK; ++k) d[k][off + hstar - 1] = (T)(x[k] + vmin);
                 off += hstar;
                 rem -= hstar;
             }
 #pragma unroll
-            for (uint32_t k = 0; k < 4; ++k) {
+            for (uint32_t k = 0; k < NK; ++k) {
                 bad |= ok[k] && (hv[k] >> 32) != 0;
                 x[k] = (uint32_t)hv[k];
             }
         } else {
 #pragma unroll
-            for (uint32_t k = 0; k < 4; ++k) {
+            for (uint32_t k = 0; k < NK; ++k) {
                 if (WB == 64) bad |= ok[k] && ((uint64_t)sv[k] >> 32) != 0;
                 x[k] = (uint32_t)sv[k];
             }
         }
         for (uint32_t i = 0; i + 1 < rem; ++i) {
 #pragma unroll
-            for (uint32_t k = 0; k < 4; ++k) {
+            for (uint32_t k = 0; k < NK; ++k) {
                 const uint32_t q = magic_div(x[k], mg);
                 d[k][off + i] = (T)(x[k] - q * B32 + vmin);
                 x[k] = q;
             }
         }
 #pragma unroll
-        for (uint32_t k = 0; k < 4; ++k) {
+        for (uint32_t k = 0; k < NK; ++k) {
             d[k][off + rem - 1] = (T)(x[k] + vmin);
             bad |= ok[k] && x[k] >= B;  // the top digit
         }
     }
+    return bad;
+}
+
+// Basic words of one block by one warp: groups of 128 words (four per lane in
+// lockstep), then the last 1..127 words 32 at a time, so a block of W words
+// costs ceil(W / 32) lane slots rather than a multiple of 4.  (Two
+// instantiations only: separate 2- and 3-word tails measured slower.)
+template <typename T, uint32_t WB>
+__device__ __forceinline__ bool decode_basic_block(const typename WordT<T, WB>::type *src /* shared */, T *u,
+                                                   T *junk, uint32_t W, uint32_t p, uint32_t hstar, uint64_t B,
+                                                   uint32_t vmin, Magic32 mg, uint64_t Dh, uint64_t MD)
+{
+    bool bad = false;
+    uint32_t j0 = 0;
+    for (; j0 + 128 <= W; j0 += 128)
+        bad |= decode_basic_group<T, WB, 4>(src, u, junk, j0, W, p, hstar, B, vmin, mg, Dh, MD);
+    for (; j0 < W; j0 += 32)
+        bad |= decode_basic_group<T, WB, 1>(src, u, junk, j0, W, p, hstar, B, vmin, mg, Dh, MD);
     return bad;
 }
 
@@ -777,8 +794,10 @@ constexpr uint32_t kWarpTileBlocks = 32; // blocks per warp tile (one lane each)
 // sets up block b (table entry, word count, division constants, series view),
 // then the warp decodes the blocks one by one into its own shared-memory slot
 // and stores each block's samples with 16-byte streaming stores.
+// 5 CTAs of 4 warps per SM: registers capped at 102 (the unconstrained
+// kernel takes ~127, which allows only 4)
 #ifndef PCX_DECODE_MIN_CTAS
-#define PCX_DECODE_MIN_CTAS 1
+#define PCX_DECODE_MIN_CTAS 5
 #endif
 template <typename T, uint32_t WB, uint32_t VAR, bool ORB>
 __global__ void __launch_bounds__(kDecWarpsMax * 32, PCX_DECODE_MIN_CTAS)
@@ -971,6 +990,7 @@ static cudaError_t launch_decompress_t(const LaunchArgs &a)
         if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
             cudaSuccess)
             return e;
+
         int per_sm = 0;
         if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, nwarps * 32, smem)) != cudaSuccess)
             return e;

@@ -33,12 +33,12 @@ GEOMETRIES = ((1855, 40), (2048, 128), (11328, 25), (1296, 64))  # pixels x samp
 
 
 def event_host(geom, seed):
-    """One event of a camera geometry: per-pixel pedestal U(250, 350) plus
-    white noise of sigma 5, rows = time samples (Sec. 4.3.1 layout), uint16."""
+    """One event of a camera geometry (pixels x time samples, rows = time
+    samples as in Sec. 4.3.1), uint16, with the white-noise model of the
+    65,536-sample workload: Gaussian, mean 300, sigma 5, rounded and clipped."""
     pixels, samples = geom
     rng = np.random.default_rng(seed)
-    ped = rng.uniform(250.0, 350.0, pixels)
-    x = np.rint(rng.normal(0.0, 5.0, (samples, pixels)) + ped)
+    x = np.rint(rng.normal(300.0, 5.0, (samples, pixels)))
     return np.clip(x, 0, 65535).astype(np.uint16).reshape(-1)
 
 
