@@ -156,6 +156,175 @@ __global__ void k_segment_items(const SourceDev *__restrict__ src, uint32_t n_sr
     prefix[k] = k;
 }
 
+// ------------------------------------------------- warp-per-segment path
+//
+// A segment is a whole stream of at most 32 blocks, so it needs neither a
+// look-back nor a CTA: one warp stages it, finds every block's min / max,
+// counts, scans and packs it, and writes its header.  A CTA of 8 warps runs
+// 8 segments at once with no barrier.  Used for 16-bit data (every base is
+// in the series table) and for the basic variant.
+
+// Shared memory of one warp: per-block vmin / B, then the stage (the widest
+// layout over the options: ceil(4096 / L) slots of L + kPad samples).
+constexpr uint32_t kSegVarsBytes = 32 * 4 + 32 * 8;
+
+PCX_HD uint32_t seg_slot_bytes(uint32_t L, uint32_t d) { return (uint32_t)round_up((uint64_t)(L + kPad) * (d / 8), 16); }
+
+PCX_HD uint32_t seg_warp_bytes(uint32_t d)
+{
+    uint32_t m = 0;
+    for (uint32_t i = 0; i < 6; ++i) {
+        const uint32_t L = 128u << i;
+        const uint32_t b = (uint32_t)ceil_div(PC_SEGMENT_SAMPLES, L) * seg_slot_bytes(L, d);
+        if (b > m) m = b;
+    }
+    return kSegVarsBytes + m;
+}
+
+template <typename T, uint32_t WB, uint32_t VAR>
+__device__ void seg_warp(const T *__restrict__ in, uint32_t n, uint32_t L, uint8_t *out, uint64_t *out_bytes,
+                         uint8_t *wsm, const OrbitTable &ot, WsHeader *ws, uint64_t limit_ns)
+{
+    using Word = typename WordOf<T, WB>::type;
+    constexpr uint32_t D = sizeof(T) * 8;
+    constexpr uint32_t VE = 16 / sizeof(T);
+    const uint32_t lane = threadIdx.x & 31u;
+    uint32_t *s_vmin = reinterpret_cast<uint32_t *>(wsm);
+    uint64_t *s_B = reinterpret_cast<uint64_t *>(wsm + 128);
+    uint8_t *stage = wsm + kSegVarsBytes;
+    const uint32_t nblk = (n + L - 1) / L;
+    const uint32_t S = seg_slot_bytes(L, D);
+
+    // 1. stage: 16-byte granules (a block is a whole number of them), the
+    // ragged end element by element
+    const uint32_t vpb = L / VE, nvec = n / VE;
+    for (uint32_t v = lane; v < nvec; v += 32) {
+        const uint32_t b = v / vpb, o = v - b * vpb;
+        cp_async16(stage + b * S + o * 16u, reinterpret_cast<const uint4 *>(in) + v);
+    }
+    cp_async_commit();
+    for (uint32_t i = nvec * VE + lane; i < n; i += 32) {
+        const uint32_t b = i / L;
+        reinterpret_cast<T *>(stage + b * S)[i - b * L] = in[i];
+    }
+    cp_async_wait<0>();
+    __syncwarp();
+
+    // 2. min / max per block (padding set to the minimum)
+    for (uint32_t b = 0; b < nblk; ++b) {
+        const uint32_t n_b = min(L, n - b * L);
+        block_minmax<T>(reinterpret_cast<T *>(stage + b * S), n_b, &s_vmin[b], &s_B[b]);
+    }
+    __syncwarp();
+
+    // 3. lane b: block b's count (Eq. 1-2, or the series table of Sec. 3.2)
+    uint32_t W = 0, p = 0, p1 = 0, vmin = 0;
+    uint64_t B = 1, K = 0, K2 = 0;
+    OrbitView v{};
+    if (lane < nblk) {
+        B = s_B[lane];
+        vmin = s_vmin[lane];
+        const uint32_t n_b = min(L, n - lane * L);
+        if (B > 1) {
+            if constexpr (VAR == PC_VARIANT_BASIC) {
+                p = basic_p(B, WB);
+                W = (n_b + p - 1) / p;
+                uint64_t geo = 0, pw = 1;
+                for (uint32_t i = 0; i < p; ++i) {
+                    geo += pw;
+                    pw *= B;
+                }
+                K = geo * vmin;
+            } else {
+                const uint64_t h = orbit_get<WB>(ot, (uint32_t)B, ws, limit_ns);  // B <= 65536 for 16-bit data
+                if (h != ~0ull) {
+                    v = orbit_view(ot, h);
+                    W = orbit_words(ot, v, n_b);
+                    p1 = eq1_p(B, WB);
+                    uint64_t geo = 0, pw = 1, geo0 = 0;
+                    for (uint32_t k = 0; k < p1; ++k) {
+                        geo0 = geo;
+                        geo += pw;
+                        pw *= B;
+                    }
+                    K = geo * vmin;
+                    K2 = geo0 * vmin;
+                }
+            }
+        }
+    }
+    const uint32_t incl = warp_incl_scan_u32(W);
+    const uint32_t woff = incl - W;
+    const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+
+    // 4. table entries, table padding, header, size
+    if (lane < nblk) {
+        if constexpr (D == 16) reinterpret_cast<uint32_t *>(out + PC_HEADER_BYTES)[lane] = vmin | ((uint32_t)(B - 1) << 16);
+        else reinterpret_cast<uint64_t *>(out + PC_HEADER_BYTES)[lane] = (uint64_t)vmin | ((B - 1) << 32);
+    }
+    const uint64_t payload_off = PC_HEADER_BYTES + table_bytes(nblk, D);
+    for (uint64_t o = PC_HEADER_BYTES + (uint64_t)nblk * 2u * (D / 8) + lane; o < payload_off; o += 32) out[o] = 0;
+    if (lane == 0) {
+        write_header<D, WB, VAR>(out, L, n, nblk, total);
+        *out_bytes = payload_off + (uint64_t)total * (WB / 8);
+    }
+
+    // 5. pack block by block
+    Word *payload = reinterpret_cast<Word *>(out + payload_off);
+    for (uint32_t b = 0; b < nblk; ++b) {
+        const uint32_t Wb = __shfl_sync(0xFFFFFFFFu, W, b);
+        const uint32_t ob = __shfl_sync(0xFFFFFFFFu, woff, b);
+        const uint32_t B32 = (uint32_t)__shfl_sync(0xFFFFFFFFu, B, b);  // B < 2^32 here unless p = 1
+        const uint64_t Kb = __shfl_sync(0xFFFFFFFFu, K, b);
+        const T *u = reinterpret_cast<const T *>(stage + b * S);
+        if (Wb == 0) continue;
+        if constexpr (VAR == PC_VARIANT_BASIC) {
+            pack_basic_block<T, WB>(u, Wb, __shfl_sync(0xFFFFFFFFu, p, b), B32, Kb, payload + ob);
+        } else {
+            OrbitView vb;
+            vb.off = __shfl_sync(0xFFFFFFFFu, v.off, b);
+            vb.Q = __shfl_sync(0xFFFFFFFFu, v.Q, b);
+            vb.P = __shfl_sync(0xFFFFFFFFu, v.P, b);
+            vb.SQ = __shfl_sync(0xFFFFFFFFu, v.SQ, b);
+            vb.G = __shfl_sync(0xFFFFFFFFu, v.G, b);
+            vb.mgP.m = __shfl_sync(0xFFFFFFFFu, v.mgP.m, b);
+            vb.mgP.a = __shfl_sync(0xFFFFFFFFu, v.mgP.a, b);
+            vb.mgP.s = __shfl_sync(0xFFFFFFFFu, v.mgP.s, b);
+            adv_words_orbit<T, WB>(ot, vb, u, Wb, B32, __shfl_sync(0xFFFFFFFFu, vmin, b),
+                                   __shfl_sync(0xFFFFFFFFu, p1, b), Kb, __shfl_sync(0xFFFFFFFFu, K2, b),
+                                   payload + ob);
+        }
+    }
+    __syncwarp();  // the stage is free for the next segment
+}
+
+template <typename T, uint32_t VAR>
+__global__ void __launch_bounds__(kThreads)
+k_compress_segments_w(const SourceDev *__restrict__ src, uint32_t n_src, uint64_t n_seg,
+                      const uint8_t *__restrict__ options, uint64_t seg_stride, uint32_t warp_bytes, WsHeader *ws,
+                      OrbitTable ot32, OrbitTable ot64, uint64_t limit_ns)
+{
+    extern __shared__ __align__(16) uint8_t smem[];
+    const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+    uint8_t *wsm = smem + warp * warp_bytes;
+    const uint64_t nw = (uint64_t)gridDim.x * kWarps;
+    for (uint64_t k = (uint64_t)blockIdx.x * kWarps + warp; k < n_seg; k += nw) {
+        const SourceDev s = src[source_of(src, n_src, k)];
+        const uint64_t j = k - s.seg_first;
+        uint32_t o = options[k];
+        if (o >= PC_CHOOSER_OPTIONS) {
+            if (lane == 0) record_error(ws, PC_ERR_INVALID_ARG);
+            o = 0;
+        }
+        const uint32_t L = option_block_len(o);
+        const T *in = static_cast<const T *>(s.in) + j * PC_SEGMENT_SAMPLES;
+        const uint32_t n = (uint32_t)umin64(PC_SEGMENT_SAMPLES, s.n - j * PC_SEGMENT_SAMPLES);
+        uint8_t *out = static_cast<uint8_t *>(s.out) + j * seg_stride;
+        if (option_word_bits(o) == 64) seg_warp<T, 64, VAR>(in, n, L, out, s.out_bytes + j, wsm, ot64, ws, limit_ns);
+        else seg_warp<T, 32, VAR>(in, n, L, out, s.out_bytes + j, wsm, ot32, ws, limit_ns);
+    }
+}
+
 // Running totals of the sources (segments path): the source's first segment
 // counts the call, every segment adds its stream size.
 __global__ void k_segment_totals(const SourceDev *__restrict__ src, uint32_t n_src, uint64_t n_seg)
@@ -215,6 +384,41 @@ pc_status launch_batch(const BatchItemDev *items, const uint64_t *prefix, uint32
                                                 reinterpret_cast<uint64_t *>(base + lay.off_status), ot32, ot64,
                                                 kWaitLimitNs);
     return cudaGetLastError() == cudaSuccess ? PC_OK : PC_ERR_CUDA;
+}
+
+template <typename T, uint32_t VAR>
+pc_status launch_segments_w_t(const pc_segments_info *info, const SourceDev *src, const uint8_t *options,
+                              uint8_t *base, const BatchLayout &lay, cudaStream_t s)
+{
+    WsHeader *ws = reinterpret_cast<WsHeader *>(base);
+    const OrbitTable ot32 = batch_table(base, lay.off_flags32, lay.off_hdr32, lay.off_slots32, &ws->orbit_cursor);
+    const OrbitTable ot64 = batch_table(base, lay.off_flags64, lay.off_hdr64, lay.off_slots64, &ws->reserved_cursor64);
+    auto kern = k_compress_segments_w<T, VAR>;
+    const uint32_t wb = seg_warp_bytes(sizeof(T) * 8);
+    const uint32_t smem = kWarps * wb;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return PC_ERR_CUDA;
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem) != cudaSuccess)
+        return PC_ERR_CUDA;
+    if (per_sm < 1) return PC_ERR_UNSUPPORTED;
+    uint64_t grid = (uint64_t)per_sm * sms;
+    const uint64_t need = ceil_div(info->n_segments, kWarps);
+    if (need < grid) grid = need;
+    kern<<<(unsigned)grid, kThreads, smem, s>>>(src, info->n_sources, info->n_segments, options, info->seg_stride,
+                                                wb, ws, ot32, ot64, kWaitLimitNs);
+    return cudaGetLastError() == cudaSuccess ? PC_OK : PC_ERR_CUDA;
+}
+
+pc_status launch_segments_w(const pc_segments_info *info, const SourceDev *src, const uint8_t *options,
+                            uint8_t *base, const BatchLayout &lay, cudaStream_t s)
+{
+    if (info->dtype_bits == 16)
+        return info->variant ? launch_segments_w_t<uint16_t, 1>(info, src, options, base, lay, s)
+                             : launch_segments_w_t<uint16_t, 0>(info, src, options, base, lay, s);
+    return launch_segments_w_t<uint32_t, 0>(info, src, options, base, lay, s);
 }
 
 pc_params option_params(uint32_t o, uint32_t d, uint32_t variant)
@@ -409,14 +613,22 @@ pc_status pc_compress_segments(const pc_segments_info *info, const void *d_plan,
     const uint64_t n_seg = info->n_segments;
     const BatchLayout lay = batch_layout(n_seg);
     uint8_t *base = static_cast<uint8_t *>(d_workspace);
-    BatchItemDev *items = reinterpret_cast<BatchItemDev *>(base + round_up(lay.bytes, 16));
-    uint64_t *prefix = reinterpret_cast<uint64_t *>(items + n_seg);
+    const SourceDev *src = static_cast<const SourceDev *>(d_plan);
     if (cudaMemsetAsync(d_workspace, 0, lay.clear_bytes, s) != cudaSuccess) return PC_ERR_CUDA;
-    k_segment_items<<<(unsigned)ceil_div(n_seg, 256), 256, 0, s>>>(
-        static_cast<const SourceDev *>(d_plan), info->n_sources, n_seg, d_options, info->dtype_bits, info->variant,
-        info->seg_stride, items, prefix, reinterpret_cast<WsHeader *>(base));
-    if (cudaGetLastError() != cudaSuccess) return PC_ERR_CUDA;
-    const pc_status st = launch_batch(items, prefix, (uint32_t)n_seg, n_seg, info->smem_bytes, base, s);
+    pc_status st = PC_OK;
+    if (info->dtype_bits == 16 || info->variant == PC_VARIANT_BASIC) {
+        st = launch_segments_w(info, src, d_options, base, lay, s);
+    } else {
+        // 32-bit advanced: bases above 65536 walk the series in shared
+        // memory, so these segments go through the CTA tile routine
+        BatchItemDev *items = reinterpret_cast<BatchItemDev *>(base + round_up(lay.bytes, 16));
+        uint64_t *prefix = reinterpret_cast<uint64_t *>(items + n_seg);
+        k_segment_items<<<(unsigned)ceil_div(n_seg, 256), 256, 0, s>>>(
+            src, info->n_sources, n_seg, d_options, info->dtype_bits, info->variant, info->seg_stride, items, prefix,
+            reinterpret_cast<WsHeader *>(base));
+        if (cudaGetLastError() != cudaSuccess) return PC_ERR_CUDA;
+        st = launch_batch(items, prefix, (uint32_t)n_seg, n_seg, info->smem_bytes, base, s);
+    }
     if (st != PC_OK || !info->has_totals) return st;
     k_segment_totals<<<(unsigned)ceil_div(n_seg, 256), 256, 0, s>>>(static_cast<const SourceDev *>(d_plan),
                                                                   info->n_sources, n_seg);

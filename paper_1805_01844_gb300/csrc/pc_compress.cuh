@@ -290,6 +290,25 @@ __device__ __forceinline__ void pack_basic_block(const T *u, uint32_t W, uint32_
     else if (rest > 0) pack_basic_group<T, WB, 1>(u, j0, W, p, B32, K, dst);
 }
 
+// The 64-byte stream header (format version 1, include/pc.h).
+template <uint32_t D, uint32_t WB, uint32_t VAR>
+__device__ __forceinline__ void write_header(uint8_t *out, uint32_t L, uint64_t n, uint64_t n_blocks,
+                                             uint64_t payload_words)
+{
+    uint32_t *h = reinterpret_cast<uint32_t *>(out);
+    h[0] = 0x504D4350u;  // "PCMP"
+    h[1] = 1u | (VAR << 16) | (D << 24);
+    h[2] = WB;
+    h[3] = L;
+    uint64_t *h64 = reinterpret_cast<uint64_t *>(out);
+    h64[2] = n;
+    h64[3] = n_blocks;
+    h64[4] = payload_words;
+    h64[5] = 0;
+    h64[6] = 0;
+    h64[7] = 0;
+}
+
 // One stream as the compression kernels see it.
 struct StreamArgs {
     const void *in;
@@ -446,18 +465,7 @@ __device__ void compress_tile(const StreamArgs &sa, uint64_t tile, uint8_t *smem
             const uint64_t tend = PC_HEADER_BYTES + n_blocks * 2u * (D / 8);
             for (uint64_t o = tend + threadIdx.x; o < payload_off; o += kThreads) sa.out[o] = 0;
             if (threadIdx.x == 0) {
-                uint32_t *h = reinterpret_cast<uint32_t *>(sa.out);
-                h[0] = 0x504D4350u;  // "PCMP"
-                h[1] = 1u | (VAR << 16) | (D << 24);
-                h[2] = WB;
-                h[3] = L;
-                uint64_t *h64 = reinterpret_cast<uint64_t *>(sa.out);
-                h64[2] = n;
-                h64[3] = n_blocks;
-                h64[4] = payload_words;
-                h64[5] = 0;
-                h64[6] = 0;
-                h64[7] = 0;
+                write_header<D, WB, VAR>(sa.out, L, n, n_blocks, payload_words);
                 *sa.out_bytes = payload_off + payload_words * (WB / 8);
             }
         }
@@ -469,13 +477,7 @@ __device__ void compress_tile(const StreamArgs &sa, uint64_t tile, uint8_t *smem
 template <uint32_t D, uint32_t WB, uint32_t VAR>
 __device__ void write_empty_stream(const StreamArgs &sa)
 {
-    uint32_t *h = reinterpret_cast<uint32_t *>(sa.out);
-    h[0] = 0x504D4350u;
-    h[1] = 1u | (VAR << 16) | (D << 24);
-    h[2] = WB;
-    h[3] = sa.L;
-    uint64_t *h64 = reinterpret_cast<uint64_t *>(sa.out);
-    for (int i = 2; i < 8; ++i) h64[i] = 0;
+    write_header<D, WB, VAR>(sa.out, sa.L, 0, 0, 0);
     *sa.out_bytes = PC_HEADER_BYTES;
 }
 
