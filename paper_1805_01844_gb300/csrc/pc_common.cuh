@@ -336,7 +336,10 @@ PCX_HD Magic32 magic32(uint64_t d)
 
 PCX_HD uint32_t magic_div(uint32_t x, Magic32 mg)
 {
-    return (uint32_t)(((uint64_t)x * mg.m + mg.a) >> (32 + mg.s));
+    // (x m + a) >> (32 + s), taken as the high word shifted by s (s <= 31):
+    // a 32-bit shift instead of a variable 64-bit one
+    const uint64_t t = (uint64_t)x * mg.m + mg.a;
+    return (uint32_t)(t >> 32) >> mg.s;
 }
 
 }  // namespace pcx

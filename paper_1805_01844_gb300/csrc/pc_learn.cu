@@ -41,20 +41,46 @@ __device__ __forceinline__ void segment_features(const T *__restrict__ in, uint6
     uint32_t mn = 0xFFFFFFFFu, mx = 0, cnt = 0;
     uint64_t isum = 0, isq = 0;
     double sum = 0.0, sq = 0.0;
-    for (uint32_t i = 0; i < 128; ++i) {
-        const uint64_t g = s0 + i;
-        if (g >= n) break;
-        const uint32_t v = in[g];
-        mn = min(mn, v);
-        mx = max(mx, v);
-        if constexpr (sizeof(T) == 2) {
-            isum += v;
-            isq += (uint64_t)v * v;
-        } else {
-            sum += v;
-            sq += (double)v * v;
+    if (sizeof(T) == 2 && s0 + 128 <= n && (reinterpret_cast<uintptr_t>(in) & 15u) == 0) {
+        // a whole 16-bit sub-block of an aligned array (the sub-block then
+        // starts 256-byte aligned): sixteen 16-byte loads, both halves of each
+        // 32-bit word at once for min / max
+        const uint4 *v4 = reinterpret_cast<const uint4 *>(in + s0);
+        uint32_t pmn = 0xFFFFFFFFu, pmx = 0, s32 = 0;
+#pragma unroll 4
+        for (uint32_t i = 0; i < 16; ++i) {
+            const uint4 q = v4[i];
+            const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+            for (uint32_t k = 0; k < 4; ++k) {
+                pmn = __vminu2(pmn, w[k]);
+                pmx = __vmaxu2(pmx, w[k]);
+                const uint32_t lo = w[k] & 0xFFFFu, hi = w[k] >> 16;
+                s32 += lo + hi;
+                isq += (uint64_t)lo * lo;
+                isq += (uint64_t)hi * hi;
+            }
         }
-        ++cnt;
+        mn = min(pmn & 0xFFFFu, pmn >> 16);
+        mx = max(pmx & 0xFFFFu, pmx >> 16);
+        isum = s32;  // < 2^24
+        cnt = 128;
+    } else {
+        for (uint32_t i = 0; i < 128; ++i) {
+            const uint64_t g = s0 + i;
+            if (g >= n) break;
+            const uint32_t v = in[g];
+            mn = min(mn, v);
+            mx = max(mx, v);
+            if constexpr (sizeof(T) == 2) {
+                isum += v;
+                isq += (uint64_t)v * v;
+            } else {
+                sum += v;
+                sq += (double)v * v;
+            }
+            ++cnt;
+        }
     }
     if constexpr (sizeof(T) == 2) {
         sum = (double)isum;  // < 2^23 and < 2^39 per lane: exact
@@ -122,14 +148,16 @@ __global__ void k_features_sources(const SourceDev *__restrict__ src, uint32_t n
 constexpr uint32_t NB = 64;        // samples per CTA chunk
 constexpr uint32_t kMlpThreads = 256;
 
+// Rows are padded by one float so that a warp reading one column of 32
+// consecutive rows hits 32 different banks.
 struct MlpSmem {
     float w[NP];                   // FP32 images of the BF16 weights, then the biases
-    float X[NB][F];
-    float H1[NB][H];
-    float H2[NB][H];
-    float Z[NB][O];                // logits, then dZ
-    float D2[NB][H];               // dH2
-    float D1[NB][H];               // dH1
+    float X[NB][F + 1];
+    float H1[NB][H + 1];
+    float H2[NB][H + 1];
+    float Z[NB][O + 1];            // logits, then dZ
+    float D2[NB][H + 1];           // dH2
+    float D1[NB][H + 1];           // dH1
 };
 
 __device__ __forceinline__ void load_weights(const uint8_t *wb, float *w)
@@ -140,25 +168,27 @@ __device__ __forceinline__ void load_weights(const uint8_t *wb, float *w)
 }
 
 // H1 = relu(X W1^T + b1), H2 = relu(H1 W2^T + b2), Z = H2 W3^T + b3 for the
-// chunk's ns samples (FP32 accumulate).
+// chunk's ns samples (FP32 accumulate, each output summed in input order).
+// Consecutive threads take consecutive samples of one output unit, so the
+// weight is a broadcast and the activations a conflict-free column.
 __device__ void mlp_forward_chunk(MlpSmem &S, uint32_t ns)
 {
     for (uint32_t t = threadIdx.x; t < ns * H; t += blockDim.x) {
-        const uint32_t s = t / H, j = t % H;
+        const uint32_t j = t / ns, s = t - j * ns;
         float acc = S.w[ob1 + j];
         for (uint32_t f = 0; f < F; ++f) acc = fmaf(S.w[oW1 + j * F + f], S.X[s][f], acc);
         S.H1[s][j] = fmaxf(acc, 0.0f);
     }
     __syncthreads();
     for (uint32_t t = threadIdx.x; t < ns * H; t += blockDim.x) {
-        const uint32_t s = t / H, j = t % H;
+        const uint32_t j = t / ns, s = t - j * ns;
         float acc = S.w[ob2 + j];
         for (uint32_t k = 0; k < H; ++k) acc = fmaf(S.w[oW2 + j * H + k], S.H1[s][k], acc);
         S.H2[s][j] = fmaxf(acc, 0.0f);
     }
     __syncthreads();
     for (uint32_t t = threadIdx.x; t < ns * O; t += blockDim.x) {
-        const uint32_t s = t / O, o = t % O;
+        const uint32_t o = t / ns, s = t - o * ns;
         float acc = S.w[ob3 + o];
         for (uint32_t k = 0; k < H; ++k) acc = fmaf(S.w[oW3 + o * H + k], S.H2[s][k], acc);
         S.Z[s][o] = acc;

@@ -123,6 +123,30 @@ def white_noise_torch(n, device, mean=300.0, sigma=5.0, seed=0):
     return torch.round(x).clamp_(0, 65535).to(torch.int32).to(torch.int16)
 
 
+def chooser_mix_torch(n_samples, device, seed=0, noise_frac=0.2, chunk_segments=64):
+    """Data for the block-parameter chooser from the two workload generators:
+    camera events (`cherenkov_events_torch`, whole events) for about
+    1 - noise_frac of the samples, then Gaussian white noise around 300 (the
+    65,536-sample workload's generator) in chunks of `chunk_segments` segments
+    of 4096 samples, each chunk with its own sigma, log-uniform in [1, 100].
+    int16 tensor (uint16 bit pattern) of exactly n_samples samples."""
+    import torch
+
+    per_event = 2 * 40 * 1855
+    n_events = int((1.0 - noise_frac) * n_samples) // per_event
+    parts = []
+    if n_events:
+        parts.append(cherenkov_events_torch(n_events, device, seed=seed).reshape(-1))
+    rest = n_samples - n_events * per_event
+    g = np.random.default_rng(seed + 1)
+    step = chunk_segments * 4096
+    for k, c0 in enumerate(range(0, rest, step)):
+        m = min(step, rest - c0)
+        sigma = float(np.exp(g.uniform(0.0, np.log(100.0))))
+        parts.append(white_noise_torch(m, device, mean=300.0, sigma=sigma, seed=seed * 100003 + k))
+    return torch.cat(parts) if len(parts) > 1 else parts[0]
+
+
 # ------------------------------------------------------ batches of streams
 
 

@@ -173,3 +173,53 @@ def test_segments_describe_checks_on_the_host(lib):
     st, info = code([src(0, None, None, 0, None)])
     assert st == native.PC_OK and info.n_segments == 0
     assert native.compress_segments(info, None, None, None, 0, None) == native.PC_OK
+
+
+def test_magic_division_is_exact(tmp_path):
+    """Host-compiled check of the 32-bit magic reciprocals the kernels divide
+    by (pc_common.cuh): for every divisor 2..2^17 and a spread of larger ones
+    up to 2^32, the quotient of dividends at the edges (0, 1, d - 1, d, d + 1,
+    the multiples of d next to 2^32, 2^32 - 1) and pseudo-random ones equals
+    plain integer division."""
+    import shutil
+    import subprocess
+
+    if shutil.which("g++") is None:
+        pytest.skip("no host C++ compiler")
+    src = tmp_path / "md.cpp"
+    src.write_text(r'''
+#include <cstdio>
+#include <cstdint>
+#include "pc_common.cuh"
+using namespace pcx;
+static uint64_t rs = 88172645463325252ull;
+static uint32_t rnd() { rs ^= rs << 13; rs ^= rs >> 7; rs ^= rs << 17; return (uint32_t)rs; }
+static int check(uint64_t d) {
+  const Magic32 mg = magic32(d);
+  uint64_t xs[16];
+  int k = 0;
+  const uint64_t top = 0xFFFFFFFFull, last = top / d * d;
+  xs[k++] = 0; xs[k++] = 1; xs[k++] = d - 1; xs[k++] = d <= top ? d : 0; xs[k++] = d + 1 <= top ? d + 1 : 0;
+  xs[k++] = top; xs[k++] = top - 1; xs[k++] = last; xs[k++] = last ? last - 1 : 0;
+  for (int i = 0; i < 7; ++i) xs[k++] = rnd();
+  for (int i = 0; i < k; ++i) {
+    const uint32_t x = (uint32_t)xs[i];
+    if (magic_div(x, mg) != (uint32_t)(x / d)) { printf("bad d=%llu x=%u\n", (unsigned long long)d, x); return 1; }
+  }
+  return 0;
+}
+int main() {
+  for (uint64_t d = 2; d <= (1u << 17); ++d) if (check(d)) return 1;
+  for (int i = 0; i < 200000; ++i) { uint64_t d = ((uint64_t)rnd() | 2u); if (check(d)) return 1; }
+  for (int e = 17; e <= 32; ++e) {
+    const uint64_t p = 1ull << e;
+    if (check(p) || check(p - 1) || (e < 32 && check(p + 1))) return 1;
+  }
+  printf("ok\n");
+  return 0;
+}
+''')
+    exe = tmp_path / "md"
+    subprocess.check_call(["g++", "-std=c++17", "-O2", "-I" + os.path.join(ROOT, "include"),
+                           "-I" + os.path.join(ROOT, "paper_1805_01844_gb300", "csrc"), str(src), "-o", str(exe)])
+    assert subprocess.run([str(exe)], capture_output=True, text=True).stdout.strip() == "ok"

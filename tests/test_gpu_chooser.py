@@ -47,6 +47,10 @@ def test_features_match_oracle():
         got = ch.segment_features(to_dev(x)).cpu().numpy()
         want = mlp.features(x, d)
         np.testing.assert_allclose(got, want, rtol=2e-6, atol=1e-7)
+        # an array that does not start 16-byte aligned takes the scalar loads
+        shifted = to_dev(np.concatenate([x[:1], x]))[1:]
+        assert shifted.data_ptr() % 16
+        np.testing.assert_array_equal(ch.segment_features(shifted).cpu().numpy(), got)
 
 
 def test_forward_and_gradient_match_oracle():
