@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-sweep", action="store_true")
+    ap.add_argument("--no-cfg1", action="store_true")
     ap.add_argument("--serve-events", type=int, default=20000)
     return ap.parse_args()
 
@@ -210,6 +211,31 @@ def oracle_sample_timing(x_host_events, variant, w, L, target_s=15.0, fixed_even
     return n_ev * per_event / (t2 - t0) / GB, n_ev, t2 - t0, len(s)
 
 
+def oracle_fanout_timing(x_host_events, variant, w, L, threads, events_per_thread):
+    """The oracle as it stands on every host core: the events split into one
+    chunk (an independent stream) per thread, each compressed and
+    decompressed by its own thread (the C oracle runs outside the GIL)."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    import oracle
+
+    per_event = x_host_events[0].size * 2
+    n_ev = min(len(x_host_events), threads * events_per_thread)
+    chunks = [x_host_events[i:n_ev:threads].reshape(-1) for i in range(threads)]
+
+    def work(c):
+        y = oracle.decompress(oracle.compress(c, variant, w, L))
+        return bool((y == c).all())
+
+    work(chunks[0][: 4 * L])  # load the library before timing
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        ok = list(ex.map(work, chunks))
+    dt = time.perf_counter() - t0
+    assert all(ok)
+    return n_ev * per_event / dt / GB, n_ev, dt
+
+
 def run_reference(args):
     """The reference arm: the CPU oracle as it stands, on the host cores, on a
     bounded sample of the same workload (rank 0 only)."""
@@ -346,7 +372,7 @@ def main():
     if not args.no_e2e and rank == 0:
         e2e = end_to_end(codec, x, n, args.e2e_steps, dev)
 
-    cpu = None
+    cpu = cpu_all = None
     if not args.no_cpu_baseline and rank == 0 and world == 1:
         ev_host = x.view(args.events, -1)[: max(args.cpu_events, min(args.events, 2000))]
         ev_host = ev_host.cpu().numpy().view(np.uint16)
@@ -356,10 +382,20 @@ def main():
         cpu = {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle",
                "sample": "first %d events (%.1f MB) of the workload, compress + decompress, %.1f s, "
                          "single thread" % (n_ev, n_ev * ev_host[0].size * 2 / 1e6, secs)}
+        threads = os.cpu_count() or 1
+        gbs_all, n_all, secs_all = oracle_fanout_timing(ev_host, variant, w, L, threads,
+                                                        max(1, len(ev_host) // threads))
+        cpu_all = {"value": gbs_all, "unit": "GB/s", "cores": threads, "kind": "oracle",
+                   "sample": "first %d events (%.1f MB), one chunk per thread, compress + decompress, %.1f s"
+                             % (n_all, n_all * ev_host[0].size * 2 / 1e6, secs_all)}
 
     sweep = None
     if not args.no_sweep and rank == 0 and world == 1:
         sweep = sweep_params(x, n, dev)
+
+    cfg1 = None
+    if not args.no_cfg1 and rank == 0 and world == 1:
+        cfg1 = white_noise_2e30(dev, peak)
 
     learned, trained = None, None
     if not args.no_learned and rank == 0 and world == 1:
@@ -388,11 +424,54 @@ def main():
         "roofline": {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                      "alg_bytes_per_launch": alg_bytes, "traffic": recorded_traffic(key)},
-        "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 3 * args.steps,
-        "sweep": sweep, "learned": learned, "serving": serving,
+        "cpu_baseline": cpu, "cpu_baseline_all_cores": cpu_all, "e2e": e2e, "gpu_launches": 3 * args.steps,
+        "white_noise_2e30": cfg1, "sweep": sweep, "learned": learned, "serving": serving,
         "clocks": clk, "wall_s_timed": wall,
     }
     print(json.dumps(line), flush=True)
+
+
+def white_noise_2e30(dev, peak, steps=20):
+    """The 65,536-sample white-noise workload scaled to 2^30 samples (2 GiB;
+    N(300, 5), rounded, clipped; drawn on the GPU), basic, L = 1024, w = 64:
+    compress and decompress GB/s of uncompressed data (median of `steps`
+    CUDA-event timed calls after 3 warm-ups) against the HBM peak, and the
+    roofline fraction of each direction (read + write bytes / time / peak)."""
+    import torch
+
+    import paper_1805_01844_gb300 as pc
+    from paper_1805_01844_gb300 import datagen
+
+    n = 1 << 30
+    x = datagen.white_noise_torch(n, dev, mean=300.0, sigma=5.0, seed=0)
+    codec = pc.Codec(pc.BASIC, 16, 64, 1024, max_samples=n, device=dev)
+    sbuf = torch.empty(codec.bound(n), dtype=torch.uint8, device=dev)
+    ybuf = torch.empty(n, dtype=torch.int16, device=dev)
+    tc, td = [], []
+    for k in range(steps + 3):
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record()
+        _, nb = codec.compress(x, out=sbuf)
+        e[1].record()
+        codec.decompress(sbuf, sbuf.numel(), n, out=ybuf)
+        e[2].record()
+        torch.cuda.synchronize()
+        if k >= 3:
+            tc.append(e[0].elapsed_time(e[1]))
+            td.append(e[1].elapsed_time(e[2]))
+    assert codec.device_status() == 0 and torch.equal(ybuf, x)
+    size = int(nb.item())
+    raw = 2 * n
+    mc, md = sorted(tc)[len(tc) // 2], sorted(td)[len(td) // 2]
+    out = {"workload": "white_noise_N300_5_2^30_u16", "variant": "basic", "block_len": 1024, "word_bits": 64,
+           "ratio": raw / size, "compress_gbs": raw / (mc / 1e3) / GB, "decompress_gbs": raw / (md / 1e3) / GB,
+           "compress_roofline_frac": (raw + size) / (mc / 1e3) / GB / peak,
+           "decompress_roofline_frac": (raw + size) / (md / 1e3) / GB / peak}
+    out["compress_pct_hbm"] = 100 * out["compress_gbs"] / peak
+    out["decompress_pct_hbm"] = 100 * out["decompress_gbs"] / peak
+    del x, sbuf, ybuf, codec
+    torch.cuda.empty_cache()
+    return out
 
 
 def sweep_params(x, n, dev, steps=5):

@@ -236,10 +236,10 @@ __device__ void seg_warp(const T *__restrict__ in, uint32_t n, uint32_t L, uint8
                 }
                 K = geo * vmin;
             } else {
-                const uint64_t h = orbit_get<WB>(ot, (uint32_t)B, ws, limit_ns);  // B <= 65536 for 16-bit data
+                const uint64_t h = orbit_get<WB>(ot, (uint32_t)B, L, ws, limit_ns);  // B <= 65536 for 16-bit data
                 if (h != ~0ull) {
                     v = orbit_view(ot, h);
-                    W = orbit_words(ot, v, n_b);
+                    W = orbit_words_cached(ot, v, n_b, L);
                     p1 = eq1_p(B, WB);
                     uint64_t geo = 0, pw = 1, geo0 = 0;
                     for (uint32_t k = 0; k < p1; ++k) {

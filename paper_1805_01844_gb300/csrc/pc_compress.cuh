@@ -379,10 +379,10 @@ __device__ void compress_tile(const StreamArgs &sa, uint64_t tile, uint8_t *smem
                     bv.K[lane] = geo * bv.vmin[lane];
                 } else if (ORB && B <= kOrbitMaxB) {
                     // the series from the table: O(1) per word
-                    const uint64_t h = orbit_get<WB>(sa.ot, (uint32_t)B, ws, limit_ns);
+                    const uint64_t h = orbit_get<WB>(sa.ot, (uint32_t)B, L, ws, limit_ns);
                     if (h != ~0ull) {
                         const OrbitView v = orbit_view(sa.ot, h);
-                        W = orbit_words(sa.ot, v, n_b);
+                        W = orbit_words_cached(sa.ot, v, n_b, L);
                         bv.orb_off[lane] = v.off;
                         bv.orb_Q[lane] = v.Q;
                         bv.orb_P[lane] = v.P;

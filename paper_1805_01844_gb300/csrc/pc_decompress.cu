@@ -184,8 +184,8 @@ __device__ uint32_t check_header(const uint8_t *in, uint64_t in_bytes, uint32_t 
 // Word count of a block from its table entry (basic: Eq. 1-2; advanced: the
 // length of the split-base series of Sec. 3.2).
 template <uint32_t WB, uint32_t VAR, bool ORB>
-__device__ __forceinline__ uint32_t block_words(uint64_t B, uint32_t n_b, const OrbitTable &ot, WsHeader *ws,
-                                                uint64_t limit_ns)
+__device__ __forceinline__ uint32_t block_words(uint64_t B, uint32_t n_b, uint32_t L, const OrbitTable &ot,
+                                                WsHeader *ws, uint64_t limit_ns)
 {
     if (B <= 1) return 0;
     if constexpr (VAR == PC_VARIANT_BASIC) {
@@ -193,9 +193,9 @@ __device__ __forceinline__ uint32_t block_words(uint64_t B, uint32_t n_b, const 
         return (n_b + p - 1) / p;
     } else {
         if (ORB && B <= kOrbitMaxB) {
-            const uint64_t h = orbit_get<WB>(ot, (uint32_t)B, ws, limit_ns);
+            const uint64_t h = orbit_get<WB>(ot, (uint32_t)B, L, ws, limit_ns);
             if (h == ~0ull) return 0;
-            return orbit_words(ot, orbit_view(ot, h), n_b);
+            return orbit_words_cached(ot, orbit_view(ot, h), n_b, L);
         }
         return walk_series<WB>(B, n_b, nullptr, 0);
     }
@@ -269,7 +269,7 @@ k_offsets(const uint8_t *__restrict__ in, uint64_t in_bytes, uint32_t L, uint64_
                 Bm1 = 0;
             }
             const uint32_t n_b = (uint32_t)umin64(L, n - b * L);
-            W = block_words<WB, VAR, ORB>(Bm1 + 1, n_b, ot, ws, limit_ns);
+            W = block_words<WB, VAR, ORB>(Bm1 + 1, n_b, L, ot, ws, limit_ns);
         }
         // block-wide exclusive scan of W
         const uint32_t incl = warp_incl_scan_u32(W);
@@ -372,10 +372,10 @@ k_decode(const uint8_t *__restrict__ in, uint32_t L, T *__restrict__ out, uint64
                         bv.p[lane] = p;
                         W = (n_b + p - 1) / p;
                     } else if (ORB && B <= kOrbitMaxB) {
-                        const uint64_t h = orbit_get<WB>(ot, (uint32_t)B, ws, limit_ns);
+                        const uint64_t h = orbit_get<WB>(ot, (uint32_t)B, L, ws, limit_ns);
                         if (h != ~0ull) {
                             const OrbitView v = orbit_view(ot, h);
-                            W = orbit_words(ot, v, n_b);
+                            W = orbit_words_cached(ot, v, n_b, L);
                             bv.orb_off[lane] = v.off;
                             bv.orb_Q[lane] = v.Q;
                             bv.orb_P[lane] = v.P;
@@ -720,7 +720,8 @@ struct DecBlock {
 };
 
 template <uint32_t WB, uint32_t VAR, bool ORB>
-__device__ __forceinline__ DecBlock dec_setup(const uint8_t *in, uint64_t gb, uint32_t n_b, const OrbitTable &ot,
+__device__ __forceinline__ DecBlock dec_setup(const uint8_t *in, uint64_t gb, uint32_t n_b, uint32_t L,
+                                              const OrbitTable &ot,
                                               WsHeader *ws, uint64_t limit_ns, uint32_t D)
 {
     DecBlock d{};
@@ -750,10 +751,10 @@ __device__ __forceinline__ DecBlock dec_setup(const uint8_t *in, uint64_t gb, ui
         d.p = basic_p(d.B, WB);
         d.W = (n_b + d.p - 1) / d.p;
     } else {
-        const uint64_t h = orbit_get<WB>(ot, (uint32_t)d.B, ws, limit_ns);  // B <= 65536 here
+        const uint64_t h = orbit_get<WB>(ot, (uint32_t)d.B, L, ws, limit_ns);  // B <= 65536 here
         if (h != ~0ull) {
             d.ov = orbit_view(ot, h);
-            d.W = orbit_words(ot, d.ov, n_b);
+            d.W = orbit_words_cached(ot, d.ov, n_b, L);
         }
     }
     return d;
@@ -834,7 +835,7 @@ k_decode_w(const uint8_t *__restrict__ in, uint32_t L, T *__restrict__ out, uint
         if (lane < nblk) {
             const uint64_t gb = blk0 + lane;
             const uint32_t n_b = (uint32_t)umin64(L, n - gb * L);
-            mine = dec_setup<WB, VAR, ORB>(in, gb, n_b, ot, ws, limit_ns, D);
+            mine = dec_setup<WB, VAR, ORB>(in, gb, n_b, L, ot, ws, limit_ns, D);
         }
         const uint32_t incl = warp_incl_scan_u32(mine.W);
         mine.woff = incl - mine.W;

@@ -76,9 +76,48 @@ __device__ __forceinline__ void st_release32(uint32_t *p, uint32_t v)
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// Walk the series of B, find its pre-period Q and period P, reserve Q + P + 1
-// slots and fill them; publish the header.  ~0 on failure (recorded).
-__device__ __noinline__ static uint64_t orbit_build(const OrbitTable &ot, const SeriesConst &c, WsHeader *ws)
+// Per-block view of an orbit.
+struct OrbitView {
+    uint32_t off, Q, P, SQ, G;
+    Magic32 mgP;
+};
+
+__device__ __forceinline__ uint32_t orbit_S(const OrbitTable &ot, uint32_t slot)
+{
+    return (uint32_t)(__ldcg(&ot.ent[slot].x) >> 24) & 0xFFFFFFu;
+}
+
+// Words of a block of n_b samples: the smallest m >= 1 with q_m >= n_b + 1
+// (q_m = samples consumed by m words), from the orbit's prefix sums.
+__device__ __forceinline__ uint32_t orbit_words(const OrbitTable &ot, const OrbitView &v, uint32_t n_b)
+{
+    const uint32_t T = n_b + 1;
+    uint32_t lo, hi, add = 0, base = 0;  // search m in [lo, hi] over S(base + m) + add
+    if (T <= v.SQ + v.G) {
+        lo = 1;
+        hi = v.Q + v.P;
+    } else {
+        const uint32_t c = (T - v.SQ - 1) / v.G;
+        add = c * v.G;
+        base = c * v.P;  // m = Q + c P + r, r in [1, P]
+        lo = v.Q + 1;
+        hi = v.Q + v.P;
+    }
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (orbit_S(ot, v.off + mid) + add >= T) hi = mid;
+        else lo = mid + 1;
+    }
+    return base + lo;
+}
+
+// Walk the series of B, find its pre-period Q and period P, reserve Q + P + 3
+// slots and fill them: the Q + P steps, the total S_{Q+P}, the block view
+// (S_Q, G and the magic reciprocal of P) and the word count of a full block
+// of the requesting call's length L; publish the header.  ~0 on failure
+// (recorded).
+__device__ __noinline__ static uint64_t orbit_build(const OrbitTable &ot, const SeriesConst &c, uint32_t L,
+                                                   WsHeader *ws)
 {
     uint32_t p, R, steps = 1;
     // Brent: the cycle length P
@@ -105,11 +144,12 @@ __device__ __noinline__ static uint64_t orbit_build(const OrbitTable &ot, const 
             ++mu;
             if (++steps > kOrbitStepLimit) goto fail;
         }
-        const uint32_t Q = mu, P = lam, n = Q + P + 1;
+        const uint32_t Q = mu, P = lam, n = Q + P + 3;
         const uint32_t off = atomicAdd(ot.cursor, n);
         if ((uint64_t)off + n > kOrbitCap) goto fail;
-        uint32_t x = 1, S = 0;
+        uint32_t x = 1, S = 0, SQ = 0;
         for (uint32_t k = 0; k < Q + P; ++k) {
+            if (k == Q) SQ = S;
             const uint32_t xn = series_step(c, x, p, R);
             const Magic32 mg = magic32(R);
             ulonglong2 e;
@@ -124,6 +164,20 @@ __device__ __noinline__ static uint64_t orbit_build(const OrbitTable &ot, const 
         last.x = (uint64_t)S << 24;
         last.y = 0;
         ot.ent[off + Q + P] = last;
+        const Magic32 mgP = magic32(P);
+        ulonglong2 view;
+        view.x = (uint64_t)SQ | ((uint64_t)(S - SQ) << 24) | ((uint64_t)mgP.s << 48) | ((uint64_t)(mgP.a != 0) << 53);
+        view.y = mgP.m;
+        ot.ent[off + Q + P + 1] = view;
+        // the cache: words of a full block of the requesting call's length
+        OrbitView v;
+        v.off = off;
+        v.Q = Q;
+        v.P = P;
+        v.SQ = SQ;
+        v.G = S - SQ;
+        v.mgP = mgP;
+        ot.ent[off + Q + P + 2] = ulonglong2{((unsigned long long)L << 32) | orbit_words(ot, v, L), 0ull};
         const uint64_t h = (uint64_t)off | ((uint64_t)Q << 32) | ((uint64_t)P << 48);
         ot.hdr[c.B] = h;
         st_release32(&ot.flags[c.B], 2u);  // orders the slots and the header before it
@@ -138,11 +192,11 @@ fail:
 // Header of the orbit of B (2 <= B <= 65536): built by the first lane that
 // asks, waited for (bounded) by the others.  ~0 on failure (recorded).
 template <uint32_t WB>
-__device__ uint64_t orbit_get(const OrbitTable &ot, uint32_t B, WsHeader *ws, uint64_t limit_ns)
+__device__ uint64_t orbit_get(const OrbitTable &ot, uint32_t B, uint32_t L, WsHeader *ws, uint64_t limit_ns)
 {
     uint32_t f = ld_acquire32(&ot.flags[B]);
     if (f == 2u) return __ldcg(&ot.hdr[B]);
-    if (f == 0u && atomicCAS(&ot.flags[B], 0u, 1u) == 0u) return orbit_build(ot, series_const<WB>(B), ws);
+    if (f == 0u && atomicCAS(&ot.flags[B], 0u, 1u) == 0u) return orbit_build(ot, series_const<WB>(B), L, ws);
     const uint64_t t0 = globaltimer();
     uint32_t spins = 0;
     while ((f = ld_acquire32(&ot.flags[B])) == 1u || f == 0u) {
@@ -157,51 +211,34 @@ __device__ uint64_t orbit_get(const OrbitTable &ot, uint32_t B, WsHeader *ws, ui
     return __ldcg(&ot.hdr[B]);
 }
 
-// Per-block view of an orbit.
-struct OrbitView {
-    uint32_t off, Q, P, SQ, G;
-    Magic32 mgP;
-};
-
-__device__ __forceinline__ uint32_t orbit_S(const OrbitTable &ot, uint32_t slot)
-{
-    return (uint32_t)(__ldcg(&ot.ent[slot].x) >> 24) & 0xFFFFFFu;
-}
-
+// The view of a block: one 16-byte load of the slot after the orbit's steps.
 __device__ __forceinline__ OrbitView orbit_view(const OrbitTable &ot, uint64_t h)
 {
     OrbitView v;
     v.off = (uint32_t)h;
     v.Q = (uint32_t)(h >> 32) & 0xFFFFu;
     v.P = (uint32_t)(h >> 48);
-    v.SQ = orbit_S(ot, v.off + v.Q);
-    v.G = orbit_S(ot, v.off + v.Q + v.P) - v.SQ;
-    v.mgP = magic32(v.P);
+    const ulonglong2 e = __ldcg(&ot.ent[v.off + v.Q + v.P + 1]);
+    v.SQ = (uint32_t)e.x & 0xFFFFFFu;
+    v.G = (uint32_t)(e.x >> 24) & 0xFFFFFFu;
+    v.mgP.m = (uint32_t)e.y;
+    v.mgP.s = (uint32_t)(e.x >> 48) & 31u;
+    v.mgP.a = ((e.x >> 53) & 1u) ? v.mgP.m : 0u;
     return v;
 }
 
-// Words of a block of n_b samples: the smallest m >= 1 with q_m >= n_b + 1
-// (q_m = samples consumed by m words), from the orbit's prefix sums.
-__device__ __forceinline__ uint32_t orbit_words(const OrbitTable &ot, const OrbitView &v, uint32_t n_b)
+// Words of a block of n_b samples in a stream of block length L: a full
+// block (n_b = L) reads the orbit's cache, which the builder filled with
+// L' << 32 | words of a full block of the block length L' of the call that
+// built it; otherwise, or for another length, the prefix search.
+__device__ __forceinline__ uint32_t orbit_words_cached(const OrbitTable &ot, const OrbitView &v, uint32_t n_b,
+                                                       uint32_t L)
 {
-    const uint32_t T = n_b + 1;
-    uint32_t lo, hi, add = 0, base = 0;  // search m in [lo, hi] over S(base + m) + add
-    if (T <= v.SQ + v.G) {
-        lo = 1;
-        hi = v.Q + v.P;
-    } else {
-        const uint32_t c = (T - v.SQ - 1) / v.G;
-        add = c * v.G;
-        base = c * v.P;  // m = Q + c P + r, r in [1, P]
-        lo = v.Q + 1;
-        hi = v.Q + v.P;
+    if (n_b == L) {
+        const unsigned long long c = __ldcg(&ot.ent[v.off + v.Q + v.P + 2].x);
+        if ((uint32_t)(c >> 32) == L) return (uint32_t)c;
     }
-    while (lo < hi) {
-        const uint32_t mid = (lo + hi) >> 1;
-        if (orbit_S(ot, v.off + mid) + add >= T) hi = mid;
-        else lo = mid + 1;
-    }
-    return base + lo;
+    return orbit_words(ot, v, n_b);
 }
 
 // Series entry of word i: R_i, p_i, q_i and the magic reciprocal of R_i.
