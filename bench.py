@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-cfg1", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--serve-events", type=int, default=20000)
     return ap.parse_args()
 
@@ -397,6 +398,10 @@ def main():
     if not args.no_cfg1 and rank == 0 and world == 1:
         cfg1 = white_noise_2e30(dev, peak)
 
+    batch = None
+    if not args.no_batch and rank == 0 and world == 1:
+        batch = batch_metrics(dev)
+
     learned, trained = None, None
     if not args.no_learned and rank == 0 and world == 1:
         learned, trained = learned_vs_plain(dev)
@@ -425,7 +430,7 @@ def main():
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                      "alg_bytes_per_launch": alg_bytes, "traffic": recorded_traffic(key)},
         "cpu_baseline": cpu, "cpu_baseline_all_cores": cpu_all, "e2e": e2e, "gpu_launches": 3 * args.steps,
-        "white_noise_2e30": cfg1, "sweep": sweep, "learned": learned, "serving": serving,
+        "white_noise_2e30": cfg1, "batch": batch, "sweep": sweep, "learned": learned, "serving": serving,
         "clocks": clk, "wall_s_timed": wall,
     }
     print(json.dumps(line), flush=True)
@@ -472,6 +477,64 @@ def white_noise_2e30(dev, peak, steps=20):
     del x, sbuf, ybuf, codec
     torch.cuda.empty_cache()
     return out
+
+
+def batch_metrics(dev, n_streams=64, reps=20):
+    """64 uneven streams (4 KB - 64 MB, uint16 / uint32, varied noise and
+    spikes): block length and word size autotuned per stream, then all of
+    them compressed by one persistent launch captured in a CUDA graph; the
+    same streams one pc_compress call each, for comparison.  GB/s of input
+    (median replay), ratio, and a byte check of every stream's batch output
+    against its own single-stream compression."""
+    import torch
+
+    import paper_1805_01844_gb300 as pc
+    from paper_1805_01844_gb300 import batch as pcb
+    from paper_1805_01844_gb300 import datagen
+
+    specs = datagen.batched_stream_specs(n_streams, seed=0)
+    xs = [datagen.batched_stream_torch(sp, dev) for sp in specs]
+    raw = sum(x.numel() * x.element_size() for x in xs)
+    t0 = time.perf_counter()
+    params = [pcb.autotune(x, variant=pc.BASIC) for x in xs]
+    nt, nt_ms = pcb.autotune_threads(xs, params)
+    tune_s = time.perf_counter() - t0
+    b = pcb.Batch(xs, params, cta_threads=nt)
+    g = b.capture()
+
+    def med(fn):
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return sorted(ts)[len(ts) // 2]
+
+    g.replay()
+    torch.cuda.synchronize()
+    t_batch = med(g.replay)
+    assert b.device_status() == 0
+    sizes = b.nbytes.cpu().tolist()
+    codecs = [pc.Codec(p.variant, p.dtype_bits, p.word_bits, p.block_len, max_samples=x.numel(), device=dev)
+              for x, p in zip(xs, params)]
+    outs = [torch.empty(c.bound(x.numel()), dtype=torch.uint8, device=dev) for c, x in zip(codecs, xs)]
+
+    def one_by_one():
+        for c, x, o in zip(codecs, xs, outs):
+            c.compress(x, out=o)
+
+    one_by_one()
+    torch.cuda.synchronize()
+    t_each = med(one_by_one)
+    same = all(torch.equal(b.outs[k][:sizes[k]], outs[k][:sizes[k]]) for k in range(len(xs)))
+    return {"streams": len(xs), "input_bytes": raw, "ratio": raw / sum(sizes),
+            "gbs_one_graph_launch": raw / (t_batch / 1e3) / GB, "gbs_one_call_per_stream": raw / (t_each / 1e3) / GB,
+            "autotune_s": tune_s, "identical_to_single_stream": same, "cta_threads": nt,
+            "ms_by_cta_threads": nt_ms,
+            "params": sorted(set("L%d_w%d" % (p.block_len, p.word_bits) for p in params))}
 
 
 def sweep_params(x, n, dev, steps=5):

@@ -190,9 +190,14 @@ typedef struct {
     uint64_t total_tiles;     /* tiles over all items (an empty item counts 1) */
     uint64_t plan_bytes;      /* device bytes pc_batch_plan writes */
     uint64_t workspace_bytes; /* device workspace pc_compress_batch needs */
+    uint32_t cta_threads;     /* in: 128 or 256 threads per CTA (anything else: 256); out: the value used */
+    uint32_t reserved;
 } pc_batch_info;
 
-/* Validate items (same rules as pc_compress) and fill *info.  Host only. */
+/* Validate items (same rules as pc_compress) and fill *info.  Host only.
+ * info->cta_threads is read first: 128-thread CTAs take half-size tiles and
+ * run twice as many per SM (faster for short blocks); the plan and the
+ * launch follow the value describe settles on. */
 pc_status pc_batch_describe(const pc_batch_item *items, uint32_t n_items, pc_batch_info *info);
 
 /* Copy the descriptors and the tile prefix of items to device memory d_plan
@@ -266,10 +271,11 @@ pc_status pc_mlp_adam(float *d_master, void *d_weights, float *d_grad, float *d_
  *   pc_segments_describe   host only: sizes and launch facts
  *   pc_segments_plan       one host-to-device copy of the source table
  *   pc_segments_features   feature rows of every segment (one kernel)
- *   pc_compress_segments   every segment with its own option: a memset, a
- *                          kernel that writes one batch descriptor per
- *                          segment, the persistent batch kernel, and (if any
- *                          source has d_totals) a kernel adding to the totals.
+ *   pc_compress_segments   every segment with its own option: a memset, one
+ *                          kernel (a warp per segment; for 32-bit advanced
+ *                          data a descriptor kernel and the batch kernel), and
+ *                          (if any source has d_totals) a kernel adding to the
+ *                          totals.
  * Feature 23 uses the segment's index within its source, so a segment's
  * features, choice and stream do not depend on the other sources.  A source
  * of 0 samples is skipped entirely (it adds nothing to its totals). */

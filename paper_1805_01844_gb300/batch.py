@@ -14,10 +14,11 @@ class Batch:
     """Compress `tensors` (CUDA, contiguous, 16/32-bit) with per-stream
     `params` (native.PcParams) in one launch; outputs are v1 streams."""
 
-    def __init__(self, tensors, params, device=None, outs=None, workspace=None, stream=None):
+    def __init__(self, tensors, params, device=None, outs=None, workspace=None, stream=None, cta_threads=256):
         """outs: optional caller-owned uint8 output tensors (one per item, each
         at least pc_bound bytes, 16-byte aligned); workspace: optional
-        caller-owned uint8 tensor reused across launches."""
+        caller-owned uint8 tensor reused across launches; cta_threads: 128 or
+        256 threads per CTA of the launch (see autotune_threads)."""
         assert len(tensors) == len(params) and tensors
         self.device = device or tensors[0].device
         self.tensors = tensors
@@ -42,7 +43,7 @@ class Batch:
         for i, (x, p) in enumerate(zip(tensors, params)):
             items.append(native.PcBatchItem(x.data_ptr() if x.numel() else None, x.numel(), p,
                                             self.outs[i].data_ptr(), self.outs[i].numel(), nb + 8 * i))
-        self._arr, self.info = native.batch_describe(items)
+        self._arr, self.info = native.batch_describe(items, cta_threads)
         self.plan = torch.empty((self.info.plan_bytes + 15) // 16 * 16, dtype=torch.uint8, device=self.device)
         if workspace is not None and workspace.numel() >= self.info.workspace_bytes:
             self.ws = workspace
@@ -97,3 +98,25 @@ def autotune(x, variant=native.BASIC, sample=1 << 18, lengths=LENGTHS, words=WOR
             if best is None or key < best[0]:
                 best = (key, native.params(variant, d, w, L))
     return best[1]
+
+
+def autotune_threads(tensors, params, candidates=(128, 256), reps=5):
+    """Threads per CTA for a batch: each candidate compresses the whole batch
+    `reps` times after a warm-up, timed with CUDA events; the fastest wins.
+    Returns (threads, {threads: ms per launch})."""
+    times = {}
+    for nt in candidates:
+        b = Batch(tensors, params, cta_threads=nt)
+        b.compress()
+        torch.cuda.synchronize(b.device)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            b.compress()
+        e1.record()
+        torch.cuda.synchronize(b.device)
+        times[nt] = e0.elapsed_time(e1) / reps
+        del b
+    best = min(times, key=lambda k: (times[k], k))
+    return best, times
+

@@ -99,8 +99,9 @@ pc_status pc_compress(const void *d_in, uint64_t n_samples, const pc_params *par
     WsLayout lay;
     const bool fits = pick_layout(params, n_samples, workspace_bytes, lay);
     const uint64_t n_blocks = ceil_div(n_samples, params->block_len);
+    const uint32_t nt = compress_threads(params->variant, params->dtype_bits, params->word_bits, params->block_len);
     const TileCfg cfg = tile_cfg(kKernelCompress, params->variant, params->dtype_bits, params->word_bits,
-                                 params->block_len, lay.orbit);
+                                 params->block_len, lay.orbit, nt);
     const uint64_t n_tiles = ceil_div(n_blocks, cfg.tb);
     if (n_tiles >> 31) return PC_ERR_UNSUPPORTED;  // tile tickets are 32-bit
     uint64_t need = 0;
@@ -120,6 +121,7 @@ pc_status pc_compress(const void *d_in, uint64_t n_samples, const pc_params *par
     fill_workspace(a, d_workspace, lay);
     a.n_blocks = n_blocks;
     a.n_tiles = n_tiles;
+    a.nt = nt;
     a.limit_ns = kWaitLimitNs;
     a.stream = static_cast<cudaStream_t>(stream);
     if (cudaMemsetAsync(d_workspace, 0, lay.clear_bytes, a.stream) != cudaSuccess) return PC_ERR_CUDA;

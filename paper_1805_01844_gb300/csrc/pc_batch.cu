@@ -58,7 +58,8 @@ __device__ __forceinline__ void empty_item(const StreamArgs &sa)
     if (threadIdx.x == 0) write_empty_stream<D, WB, VAR>(sa);
 }
 
-__global__ void __launch_bounds__(kThreads)
+template <uint32_t NT>
+__global__ void __launch_bounds__(NT)
 k_compress_batch(const BatchItemDev *__restrict__ items, const uint64_t *__restrict__ prefix, uint32_t n_items,
                  uint64_t total_tiles, WsHeader *ws, uint64_t *status, OrbitTable ot32, OrbitTable ot64,
                  uint64_t limit_ns)
@@ -111,14 +112,14 @@ k_compress_batch(const BatchItemDev *__restrict__ items, const uint64_t *__restr
             continue;
         }
         switch (it.key) {
-        case 0: compress_tile<uint16_t, 32, 0, false>(sa, tile, smem, ws, limit_ns); break;
-        case 1: compress_tile<uint16_t, 32, 1, true>(sa, tile, smem, ws, limit_ns); break;
-        case 2: compress_tile<uint16_t, 64, 0, false>(sa, tile, smem, ws, limit_ns); break;
-        case 3: compress_tile<uint16_t, 64, 1, true>(sa, tile, smem, ws, limit_ns); break;
-        case 4: compress_tile<uint32_t, 32, 0, false>(sa, tile, smem, ws, limit_ns); break;
-        case 5: compress_tile<uint32_t, 32, 1, true>(sa, tile, smem, ws, limit_ns); break;
-        case 6: compress_tile<uint32_t, 64, 0, false>(sa, tile, smem, ws, limit_ns); break;
-        default: compress_tile<uint32_t, 64, 1, true>(sa, tile, smem, ws, limit_ns); break;
+        case 0: compress_tile<uint16_t, 32, 0, false, NT>(sa, tile, smem, ws, limit_ns); break;
+        case 1: compress_tile<uint16_t, 32, 1, true, NT>(sa, tile, smem, ws, limit_ns); break;
+        case 2: compress_tile<uint16_t, 64, 0, false, NT>(sa, tile, smem, ws, limit_ns); break;
+        case 3: compress_tile<uint16_t, 64, 1, true, NT>(sa, tile, smem, ws, limit_ns); break;
+        case 4: compress_tile<uint32_t, 32, 0, false, NT>(sa, tile, smem, ws, limit_ns); break;
+        case 5: compress_tile<uint32_t, 32, 1, true, NT>(sa, tile, smem, ws, limit_ns); break;
+        case 6: compress_tile<uint32_t, 64, 0, false, NT>(sa, tile, smem, ws, limit_ns); break;
+        default: compress_tile<uint32_t, 64, 1, true, NT>(sa, tile, smem, ws, limit_ns); break;
         }
     }
 }
@@ -346,10 +347,10 @@ namespace {
 
 bool a16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
-uint64_t item_tiles(const pc_batch_item &it)
+uint64_t item_tiles(const pc_batch_item &it, uint32_t nt)
 {
     const pc_params &p = it.params;
-    const TileCfg cfg = tile_cfg(kKernelCompress, p.variant, p.dtype_bits, p.word_bits, p.block_len, true);
+    const TileCfg cfg = tile_cfg(kKernelCompress, p.variant, p.dtype_bits, p.word_bits, p.block_len, true, nt);
     return ceil_div(ceil_div(it.n_samples, p.block_len), cfg.tb);
 }
 
@@ -362,28 +363,36 @@ OrbitTable batch_table(uint8_t *base, uint64_t off_flags, uint64_t off_hdr, uint
 // The persistent batch kernel over a plan (items, prefix) with workspace
 // `base` laid out by batch_layout(total_tiles); the workspace is cleared by
 // the caller.
-pc_status launch_batch(const BatchItemDev *items, const uint64_t *prefix, uint32_t n_items, uint64_t total_tiles,
-                       uint32_t smem, uint8_t *base, cudaStream_t s)
+template <uint32_t NT>
+pc_status launch_batch_t(const BatchItemDev *items, const uint64_t *prefix, uint32_t n_items, uint64_t total_tiles,
+                         uint32_t smem, uint8_t *base, cudaStream_t s)
 {
     const BatchLayout lay = batch_layout(total_tiles);
     WsHeader *ws = reinterpret_cast<WsHeader *>(base);
     const OrbitTable ot32 = batch_table(base, lay.off_flags32, lay.off_hdr32, lay.off_slots32, &ws->orbit_cursor);
     const OrbitTable ot64 = batch_table(base, lay.off_flags64, lay.off_hdr64, lay.off_slots64, &ws->reserved_cursor64);
-    auto kern = k_compress_batch;
+    auto kern = k_compress_batch<NT>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return PC_ERR_CUDA;
     int dev = 0, sms = 0, per_sm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem) != cudaSuccess)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem) != cudaSuccess)
         return PC_ERR_CUDA;
     if (per_sm < 1) return PC_ERR_UNSUPPORTED;
     uint64_t grid = (uint64_t)per_sm * sms;
     if (total_tiles < grid) grid = total_tiles;
-    kern<<<(unsigned)grid, kThreads, smem, s>>>(items, prefix, n_items, total_tiles, ws,
+    kern<<<(unsigned)grid, NT, smem, s>>>(items, prefix, n_items, total_tiles, ws,
                                                 reinterpret_cast<uint64_t *>(base + lay.off_status), ot32, ot64,
                                                 kWaitLimitNs);
     return cudaGetLastError() == cudaSuccess ? PC_OK : PC_ERR_CUDA;
+}
+
+pc_status launch_batch(const BatchItemDev *items, const uint64_t *prefix, uint32_t n_items, uint64_t total_tiles,
+                       uint32_t smem, uint32_t nt, uint8_t *base, cudaStream_t s)
+{
+    return nt == 128 ? launch_batch_t<128>(items, prefix, n_items, total_tiles, smem, base, s)
+                     : launch_batch_t<256>(items, prefix, n_items, total_tiles, smem, base, s);
 }
 
 template <typename T, uint32_t VAR>
@@ -457,6 +466,7 @@ extern "C" {
 pc_status pc_batch_describe(const pc_batch_item *items, uint32_t n_items, pc_batch_info *info)
 {
     if (!items || !info || n_items == 0) return PC_ERR_INVALID_ARG;
+    const uint32_t nt = info->cta_threads == 128 ? 128u : 256u;
     uint64_t total = 0;
     uint32_t smem = 0;
     for (uint32_t i = 0; i < n_items; ++i) {
@@ -472,13 +482,15 @@ pc_status pc_batch_describe(const pc_batch_item *items, uint32_t n_items, pc_bat
         uint64_t need = 0;
         pc_bound(&p, it.n_samples, &need);
         if (it.out_capacity < need) return PC_ERR_CAPACITY;
-        const uint64_t t = item_tiles(it);
+        const uint64_t t = item_tiles(it, nt);
         total += t ? t : 1;
-        const TileCfg cfg = tile_cfg(kKernelCompress, p.variant, p.dtype_bits, p.word_bits, p.block_len, true);
+        const TileCfg cfg = tile_cfg(kKernelCompress, p.variant, p.dtype_bits, p.word_bits, p.block_len, true, nt);
         if (cfg.smem > smem) smem = cfg.smem;
     }
     if (total >> 31) return PC_ERR_UNSUPPORTED;  // tickets are 32-bit
     info->n_items = n_items;
+    info->cta_threads = nt;
+    info->reserved = 0;
     info->smem_bytes = smem;
     info->total_tiles = total;
     info->plan_bytes = sizeof(BatchItemDev) * (uint64_t)n_items + 8 * ((uint64_t)n_items + 1);
@@ -504,7 +516,7 @@ pc_status pc_batch_plan(const pc_batch_item *items, uint32_t n_items, const pc_b
         d.out = it.d_out;
         d.out_bytes = it.d_out_bytes;
         d.n_blocks = ceil_div(it.n_samples, p.block_len);
-        d.n_tiles = item_tiles(it);
+        d.n_tiles = item_tiles(it, info->cta_threads);
         d.L = p.block_len;
         d.key = (p.dtype_bits == 32 ? 4u : 0u) | (p.word_bits == 64 ? 2u : 0u) | (p.variant ? 1u : 0u);
         dv[i] = d;
@@ -530,7 +542,7 @@ pc_status pc_compress_batch(const pc_batch_info *info, const void *d_plan, void 
     const BatchItemDev *items = static_cast<const BatchItemDev *>(d_plan);
     const uint64_t *prefix = reinterpret_cast<const uint64_t *>(static_cast<const uint8_t *>(d_plan) +
                                                                 sizeof(BatchItemDev) * (uint64_t)info->n_items);
-    return launch_batch(items, prefix, info->n_items, info->total_tiles, info->smem_bytes,
+    return launch_batch(items, prefix, info->n_items, info->total_tiles, info->smem_bytes, info->cta_threads,
                         static_cast<uint8_t *>(d_workspace), s);
 }
 
@@ -627,7 +639,7 @@ pc_status pc_compress_segments(const pc_segments_info *info, const void *d_plan,
             src, info->n_sources, n_seg, d_options, info->dtype_bits, info->variant, info->seg_stride, items, prefix,
             reinterpret_cast<WsHeader *>(base));
         if (cudaGetLastError() != cudaSuccess) return PC_ERR_CUDA;
-        st = launch_batch(items, prefix, (uint32_t)n_seg, n_seg, info->smem_bytes, base, s);
+        st = launch_batch(items, prefix, (uint32_t)n_seg, n_seg, info->smem_bytes, kThreads, base, s);
     }
     if (st != PC_OK || !info->has_totals) return st;
     k_segment_totals<<<(unsigned)ceil_div(n_seg, 256), 256, 0, s>>>(static_cast<const SourceDev *>(d_plan),

@@ -21,7 +21,10 @@
 
 namespace pcx {
 
-constexpr uint32_t kThreads = 256;
+#ifndef PCX_THREADS
+#define PCX_THREADS 256
+#endif
+constexpr uint32_t kThreads = PCX_THREADS;
 constexpr uint32_t kWarps = kThreads / 32;
 constexpr uint32_t kPad = 64;           // > largest digit count per word (63, B = 2, w = 64)
 constexpr uint32_t kMaxTileBlocks = 32;  // one look-back / chain-walk lane per block
@@ -169,7 +172,8 @@ enum : uint32_t { kKernelCompress = 0, kKernelDecode = 1 };
 // Compression keeps two tiles in flight per CTA when a block is a whole
 // number of 16-byte vectors (asynchronous copies need 16-byte granules) and
 // two blocks' slots fit the budget.
-PCX_HD TileCfg tile_cfg(uint32_t kind, uint32_t variant, uint32_t d, uint32_t w, uint32_t L, bool orbit)
+PCX_HD TileCfg tile_cfg(uint32_t kind, uint32_t variant, uint32_t d, uint32_t w, uint32_t L, bool orbit,
+                        uint32_t nt = kThreads)
 {
     TileCfg c;
     c.S = L + kPad;
@@ -178,7 +182,9 @@ PCX_HD TileCfg tile_cfg(uint32_t kind, uint32_t variant, uint32_t d, uint32_t w,
     // table, 16-bit data never walks (every base is <= 65536)
     const bool walk = variant == PC_VARIANT_ADVANCED && !(orbit && d == 16);
     c.wcap = walk ? (uint32_t)words_bound(variant, d, w, L) : 0u;
-    const uint32_t budget = variant == PC_VARIANT_ADVANCED ? kTileBudgetAdvanced : kTileBudgetBasic;
+    // a 128-thread CTA gets about half the shared memory of a 256-thread one
+    const uint32_t budget = (variant == PC_VARIANT_ADVANCED ? kTileBudgetAdvanced : kTileBudgetBasic) /
+                            (nt <= 128 ? 2u : 1u);
     const uint32_t one = c.stage_bytes + c.wcap * 12u;
     c.slots = (PCX_COMPRESS_SLOTS == 2 && kind == kKernelCompress && (L * (d / 8)) % 16 == 0 &&
                2u * one <= budget) ? 2u : 1u;
@@ -199,6 +205,16 @@ PCX_HD TileCfg tile_cfg(uint32_t kind, uint32_t variant, uint32_t d, uint32_t w,
     c.slot_bytes = (uint32_t)round_up(off, 16);
     c.smem = c.slots * c.slot_bytes;
     return c;
+}
+
+// Threads per CTA of the single-stream compression kernel: 128-thread CTAs
+// (half-size tiles, more CTAs per SM) for short basic blocks, where the per-
+// tile work is small; 256 otherwise (measured on the camera workload).
+PCX_HD uint32_t compress_threads(uint32_t variant, uint32_t d, uint32_t w, uint32_t L)
+{
+    (void)d;
+    (void)w;
+    return variant == PC_VARIANT_BASIC && L <= 512 ? 128u : 256u;
 }
 
 // Blocks per tile of the decompression offsets kernel (one thread per block).
@@ -226,7 +242,8 @@ PCX_HD WsLayout ws_layout(uint32_t variant, uint32_t d, uint32_t w, uint32_t L, 
     const uint64_t n_blocks = ceil_div(n, L);
     WsLayout lay;
     lay.orbit = orbit && variant == PC_VARIANT_ADVANCED;
-    const uint64_t ctiles = ceil_div(n_blocks, tile_cfg(kKernelCompress, variant, d, w, L, lay.orbit).tb);
+    const uint64_t ctiles = ceil_div(
+        n_blocks, tile_cfg(kKernelCompress, variant, d, w, L, lay.orbit, compress_threads(variant, d, w, L)).tb);
     const uint64_t otiles = ceil_div(n_blocks, kOffsetTileBlocks);
     const uint64_t dtiles = ceil_div(n_blocks, tile_cfg(kKernelDecode, variant, d, w, L, lay.orbit).tb);
     lay.n_status = (ctiles > otiles ? ctiles : otiles) + 1;  // + 1: the self-test uses two words
@@ -244,10 +261,25 @@ PCX_HD WsLayout ws_layout(uint32_t variant, uint32_t d, uint32_t w, uint32_t L, 
 // Warp-granular decoding: shared memory of one warp (one block's samples
 // with padding and a junk area, two buffers of packed words) and the warps
 // per CTA that fit a 200 KB budget (1 to 4).
+constexpr uint32_t kDecChunk = 256;  // packed words staged at a time per warp (a multiple of 128)
+
+// Long blocks (two word buffers of a whole block above 8 KB) are decoded in
+// chunks of kDecChunk words, so that a warp's shared memory stays small and
+// enough warps share an SM; shorter ones stage a whole block's words.
+PCX_HD bool dec_chunked(uint32_t variant, uint32_t d, uint32_t w, uint32_t L)
+{
+    return 2 * words_bound(variant, d, w, L) * (w / 8) > 8192;
+}
+
+PCX_HD uint32_t dec_chunk_words(uint32_t variant, uint32_t d, uint32_t w, uint32_t L)
+{
+    return dec_chunked(variant, d, w, L) ? kDecChunk : (uint32_t)words_bound(variant, d, w, L);
+}
+
 PCX_HD uint32_t decw_warp_bytes(uint32_t variant, uint32_t d, uint32_t w, uint32_t L)
 {
     const uint64_t slot = round_up((uint64_t)(L + 2 * kPad) * (d / 8), 16);
-    const uint64_t words = round_up(2 * words_bound(variant, d, w, L) * (w / 8), 16);
+    const uint64_t words = round_up(2 * (uint64_t)dec_chunk_words(variant, d, w, L) * (w / 8), 16);
     return (uint32_t)(slot + words);
 }
 

@@ -5,11 +5,11 @@
 
 namespace pcx {
 
-template <typename T, uint32_t WB, uint32_t VAR, bool ORB>
+template <typename T, uint32_t WB, uint32_t VAR, bool ORB, uint32_t NT>
 static cudaError_t launch_compress_t(const LaunchArgs &a)
 {
-    auto kern = k_compress<T, WB, VAR, ORB>;
-    const TileCfg cfg = tile_cfg(kKernelCompress, VAR, sizeof(T) * 8, WB, a.L, ORB);
+    auto kern = k_compress<T, WB, VAR, ORB, NT>;
+    const TileCfg cfg = tile_cfg(kKernelCompress, VAR, sizeof(T) * 8, WB, a.L, ORB, NT);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.smem);
     if (e != cudaSuccess) return e;
     // all of the unified L1 / shared storage as shared memory, so that the
@@ -19,8 +19,7 @@ static cudaError_t launch_compress_t(const LaunchArgs &a)
     int per_sm = 0, dev = 0, sms = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, cfg.smem)) != cudaSuccess)
-        return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, cfg.smem)) != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     uint64_t grid = (uint64_t)per_sm * sms;
     if (a.n_tiles < grid) grid = a.n_tiles;
@@ -35,22 +34,28 @@ static cudaError_t launch_compress_t(const LaunchArgs &a)
     sa.n_blocks = a.n_blocks;
     sa.n_tiles = a.n_tiles;
     sa.ot = OrbitTable{a.orb_flags, a.orb_hdr, static_cast<ulonglong2 *>(a.orb_slots), &a.ws->orbit_cursor};
-    kern<<<(unsigned)grid, kThreads, cfg.smem, a.stream>>>(sa, a.ws, a.limit_ns);
+    kern<<<(unsigned)grid, NT, cfg.smem, a.stream>>>(sa, a.ws, a.limit_ns);
     return cudaGetLastError();
+}
+
+template <typename T, uint32_t WB, uint32_t VAR, bool ORB>
+static cudaError_t launch_compress_nt(const LaunchArgs &a)
+{
+    return a.nt == 128 ? launch_compress_t<T, WB, VAR, ORB, 128>(a) : launch_compress_t<T, WB, VAR, ORB, 256>(a);
 }
 
 cudaError_t launch_compress(const LaunchArgs &a)
 {
     const uint32_t key = (a.d == 32 ? 4u : 0u) | (a.w == 64 ? 2u : 0u) | (a.variant ? 1u : 0u);
     switch (key) {
-    case 0: return launch_compress_t<uint16_t, 32, 0, false>(a);
-    case 1: return a.orbit ? launch_compress_t<uint16_t, 32, 1, true>(a) : launch_compress_t<uint16_t, 32, 1, false>(a);
-    case 2: return launch_compress_t<uint16_t, 64, 0, false>(a);
-    case 3: return a.orbit ? launch_compress_t<uint16_t, 64, 1, true>(a) : launch_compress_t<uint16_t, 64, 1, false>(a);
-    case 4: return launch_compress_t<uint32_t, 32, 0, false>(a);
-    case 5: return a.orbit ? launch_compress_t<uint32_t, 32, 1, true>(a) : launch_compress_t<uint32_t, 32, 1, false>(a);
-    case 6: return launch_compress_t<uint32_t, 64, 0, false>(a);
-    default: return a.orbit ? launch_compress_t<uint32_t, 64, 1, true>(a) : launch_compress_t<uint32_t, 64, 1, false>(a);
+    case 0: return launch_compress_nt<uint16_t, 32, 0, false>(a);
+    case 1: return a.orbit ? launch_compress_nt<uint16_t, 32, 1, true>(a) : launch_compress_nt<uint16_t, 32, 1, false>(a);
+    case 2: return launch_compress_nt<uint16_t, 64, 0, false>(a);
+    case 3: return a.orbit ? launch_compress_nt<uint16_t, 64, 1, true>(a) : launch_compress_nt<uint16_t, 64, 1, false>(a);
+    case 4: return launch_compress_nt<uint32_t, 32, 0, false>(a);
+    case 5: return a.orbit ? launch_compress_nt<uint32_t, 32, 1, true>(a) : launch_compress_nt<uint32_t, 32, 1, false>(a);
+    case 6: return launch_compress_nt<uint32_t, 64, 0, false>(a);
+    default: return a.orbit ? launch_compress_nt<uint32_t, 64, 1, true>(a) : launch_compress_nt<uint32_t, 64, 1, false>(a);
     }
 }
 

@@ -326,13 +326,13 @@ struct StreamArgs {
 // series of Sec. 3.2), scan and publish the tile's aggregate, look back to
 // its payload offset, then write its table entries and packed words; the last
 // tile writes the header, the table padding and the stream size.
-template <typename T, uint32_t WB, uint32_t VAR, bool ORB>
+template <typename T, uint32_t WB, uint32_t VAR, bool ORB, uint32_t NT = kThreads>
 __device__ void compress_tile(const StreamArgs &sa, uint64_t tile, uint8_t *smem, WsHeader *ws, uint64_t limit_ns)
 {
     using Word = typename WordOf<T, WB>::type;
     constexpr uint32_t D = sizeof(T) * 8;
     const uint32_t L = sa.L;
-    const TileCfg cfg = tile_cfg(kKernelCompress, VAR, D, WB, L, ORB);
+    const TileCfg cfg = tile_cfg(kKernelCompress, VAR, D, WB, L, ORB, NT);
     BlockVars &bv = *reinterpret_cast<BlockVars *>(smem + cfg.off_blk);
     uint64_t *sched_all = reinterpret_cast<uint64_t *>(smem + cfg.off_sched);
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
@@ -343,22 +343,38 @@ __device__ void compress_tile(const StreamArgs &sa, uint64_t tile, uint8_t *smem
     const uint32_t nblk = (uint32_t)umin64(cfg.tb, n_blocks - blk0);
     const uint64_t cnt = umin64(n - blk0 * L, (uint64_t)nblk * L);
 
-    // 1. stage: whole 16-byte blocks put every granule of the tile in flight at once
     if ((L * sizeof(T)) % 16 == 0) {
-        load_tile_async<T>(in, blk0 * L, cnt, L, smem, cfg.stage_bytes);
+        // 1-2. each warp stages its own blocks (all granules in flight at
+        // once) and finds their min / max as soon as its copies land
+        constexpr uint32_t VE = 16 / sizeof(T);
+        for (uint32_t b = warp; b < nblk; b += (NT / 32)) {
+            const uint32_t n_b = (uint32_t)umin64(L, cnt - (uint64_t)b * L);
+            const uint4 *src = reinterpret_cast<const uint4 *>(in + (blk0 + b) * L);
+            uint8_t *dst = smem + (uint64_t)b * cfg.stage_bytes;
+            const uint32_t nv = n_b / VE;
+            for (uint32_t v = lane; v < nv; v += 32) cp_async16(dst + v * 16u, src + v);
+            for (uint32_t e = nv * VE + lane; e < n_b; e += 32)
+                reinterpret_cast<T *>(dst)[e] = in[(blk0 + b) * L + e];
+        }
         cp_async_commit();
         cp_async_wait<0>();
+        __syncwarp();
+        for (uint32_t b = warp; b < nblk; b += (NT / 32)) {
+            const uint32_t n_b = (uint32_t)umin64(L, cnt - (uint64_t)b * L);
+            block_minmax<T>(reinterpret_cast<T *>(smem + (uint64_t)b * cfg.stage_bytes), n_b, &bv.vmin[b], &bv.B[b]);
+        }
+        __syncthreads();
     } else {
-        load_tile<T>(in, blk0 * L, cnt, L, smem, cfg.stage_bytes);
+        // 1. stage
+        load_tile<T, NT>(in, blk0 * L, cnt, L, smem, cfg.stage_bytes);
+        __syncthreads();
+        // 2. min / max per block
+        for (uint32_t b = warp; b < nblk; b += (NT / 32)) {
+            const uint32_t n_b = (uint32_t)umin64(L, cnt - (uint64_t)b * L);
+            block_minmax<T>(reinterpret_cast<T *>(smem + (uint64_t)b * cfg.stage_bytes), n_b, &bv.vmin[b], &bv.B[b]);
+        }
+        __syncthreads();
     }
-    __syncthreads();
-
-    // 2. min / max per block
-    for (uint32_t b = warp; b < nblk; b += kWarps) {
-        const uint32_t n_b = (uint32_t)umin64(L, cnt - (uint64_t)b * L);
-        block_minmax<T>(reinterpret_cast<T *>(smem + (uint64_t)b * cfg.stage_bytes), n_b, &bv.vmin[b], &bv.B[b]);
-    }
-    __syncthreads();
 
     // 3-4. word counts, scan, aggregate, look-back
     if (warp == 0) {
@@ -430,7 +446,7 @@ __device__ void compress_tile(const StreamArgs &sa, uint64_t tile, uint8_t *smem
 
     // 5. table entries, packed words, and the stream's closing bytes
     if (bv.ok) {
-        for (uint32_t b = threadIdx.x; b < nblk; b += kThreads) {
+        for (uint32_t b = threadIdx.x; b < nblk; b += NT) {
             const uint64_t gb = blk0 + b;
             const uint64_t Bm1 = bv.B[b] - 1;
             if constexpr (D == 16) {
@@ -440,7 +456,7 @@ __device__ void compress_tile(const StreamArgs &sa, uint64_t tile, uint8_t *smem
             }
         }
         Word *payload = reinterpret_cast<Word *>(sa.out + payload_off);
-        for (uint32_t b = warp; b < nblk; b += kWarps) {
+        for (uint32_t b = warp; b < nblk; b += (NT / 32)) {
             const uint32_t W = bv.W[b];
             if (W == 0) continue;
             const T *u = reinterpret_cast<const T *>(smem + (uint64_t)b * cfg.stage_bytes);
@@ -463,7 +479,7 @@ __device__ void compress_tile(const StreamArgs &sa, uint64_t tile, uint8_t *smem
         if (tile == n_tiles - 1) {
             const uint64_t payload_words = bv.excl + bv.agg;
             const uint64_t tend = PC_HEADER_BYTES + n_blocks * 2u * (D / 8);
-            for (uint64_t o = tend + threadIdx.x; o < payload_off; o += kThreads) sa.out[o] = 0;
+            for (uint64_t o = tend + threadIdx.x; o < payload_off; o += NT) sa.out[o] = 0;
             if (threadIdx.x == 0) {
                 write_header<D, WB, VAR>(sa.out, L, n, n_blocks, payload_words);
                 *sa.out_bytes = payload_off + payload_words * (WB / 8);
@@ -492,11 +508,13 @@ __device__ void write_empty_stream(const StreamArgs &sa)
 #ifndef PCX_COMPRESS_MIN_CTAS_ADVANCED
 #define PCX_COMPRESS_MIN_CTAS_ADVANCED 2
 #endif
-template <uint32_t VAR>
-constexpr int kCompressMinCtas = VAR == PC_VARIANT_BASIC ? PCX_COMPRESS_MIN_CTAS_BASIC : PCX_COMPRESS_MIN_CTAS_ADVANCED;
+// 128-thread CTAs (half-size tiles): twice as many per SM.
+template <uint32_t VAR, uint32_t NT>
+constexpr int kCompressMinCtas =
+    (VAR == PC_VARIANT_BASIC ? PCX_COMPRESS_MIN_CTAS_BASIC : PCX_COMPRESS_MIN_CTAS_ADVANCED) * (NT <= 128 ? 2 : 1);
 
-template <typename T, uint32_t WB, uint32_t VAR, bool ORB>
-__global__ void __launch_bounds__(kThreads, kCompressMinCtas<VAR>)
+template <typename T, uint32_t WB, uint32_t VAR, bool ORB, uint32_t NT>
+__global__ void __launch_bounds__(NT, kCompressMinCtas<VAR, NT>)
 k_compress(StreamArgs sa, WsHeader *ws, uint64_t limit_ns)
 {
     extern __shared__ __align__(16) uint8_t smem[];
@@ -511,7 +529,7 @@ k_compress(StreamArgs sa, WsHeader *ws, uint64_t limit_ns)
         const uint64_t tile = s_tile;
         __syncthreads();
         if (tile >= sa.n_tiles) break;
-        compress_tile<T, WB, VAR, ORB>(sa, tile, smem, ws, limit_ns);
+        compress_tile<T, WB, VAR, ORB, NT>(sa, tile, smem, ws, limit_ns);
     }
 }
 

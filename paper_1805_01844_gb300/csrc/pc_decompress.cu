@@ -602,9 +602,10 @@ k_decode(const uint8_t *__restrict__ in, uint32_t L, T *__restrict__ out, uint64
 // lanes past the last word write theirs to `junk`.  Returns true if a word is
 // not the image of valid digits.
 template <typename T, uint32_t WB, uint32_t NK>
-__device__ __forceinline__ bool decode_basic_group(const typename WordT<T, WB>::type *src /* shared */, T *u,
-                                                   T *junk, uint32_t j0, uint32_t W, uint32_t p, uint32_t hstar,
-                                                   uint64_t B, uint32_t vmin, Magic32 mg, uint64_t Dh, uint64_t MD)
+__device__ __forceinline__ bool decode_basic_group(const typename WordT<T, WB>::type *src /* shared */,
+                                                   uint32_t src0, T *u, T *junk, uint32_t j0, uint32_t W, uint32_t p,
+                                                   uint32_t hstar, uint64_t B, uint32_t vmin, Magic32 mg, uint64_t Dh,
+                                                   uint64_t MD)
 {
     using Word = typename WordT<T, WB>::type;
     const uint32_t lane = threadIdx.x & 31u;
@@ -618,7 +619,7 @@ __device__ __forceinline__ bool decode_basic_group(const typename WordT<T, WB>::
         for (uint32_t k = 0; k < NK; ++k) {
             const uint32_t j = j0 + lane + 32 * k;
             ok[k] = j < W;
-            sv[k] = ok[k] ? src[j] : Word(0);  // src is the warp's shared-memory word buffer
+            sv[k] = ok[k] ? src[j - src0] : Word(0);  // src: the staged words from word src0 on
             d[k] = ok[k] ? u + j * p : junk;
         }
         uint32_t x[NK];
@@ -693,22 +694,41 @@ __device__ __forceinline__ bool decode_basic_group(const typename WordT<T, WB>::
     return bad;
 }
 
-// Basic words of one block by one warp: groups of 128 words (four per lane in
-// lockstep), then the last 1..127 words 32 at a time, so a block of W words
-// costs ceil(W / 32) lane slots rather than a multiple of 4.  (Two
-// instantiations only: separate 2- and 3-word tails measured slower.)
+// Basic words [jb, je) of one block by one warp (src holds them from word jb
+// on): groups of 128 words (four per lane in lockstep), then the rest 32 at
+// a time, so W words cost ceil(W / 32) lane slots rather than a multiple of 4.
+// (Two instantiations only: separate 2- and 3-word tails, and versions
+// specialised on h*, measured slower.)
 template <typename T, uint32_t WB>
 __device__ __forceinline__ bool decode_basic_block(const typename WordT<T, WB>::type *src /* shared */, T *u,
-                                                   T *junk, uint32_t W, uint32_t p, uint32_t hstar, uint64_t B,
-                                                   uint32_t vmin, Magic32 mg, uint64_t Dh, uint64_t MD)
+                                                   T *junk, uint32_t jb, uint32_t je, uint32_t p, uint32_t hstar,
+                                                   uint64_t B, uint32_t vmin, Magic32 mg, uint64_t Dh, uint64_t MD)
 {
     bool bad = false;
-    uint32_t j0 = 0;
-    for (; j0 + 128 <= W; j0 += 128)
-        bad |= decode_basic_group<T, WB, 4>(src, u, junk, j0, W, p, hstar, B, vmin, mg, Dh, MD);
-    for (; j0 < W; j0 += 32)
-        bad |= decode_basic_group<T, WB, 1>(src, u, junk, j0, W, p, hstar, B, vmin, mg, Dh, MD);
+    uint32_t j0 = jb;
+    for (; j0 + 128 <= je; j0 += 128)
+        bad |= decode_basic_group<T, WB, 4>(src, jb, u, junk, j0, je, p, hstar, B, vmin, mg, Dh, MD);
+    for (; j0 < je; j0 += 32)
+        bad |= decode_basic_group<T, WB, 1>(src, jb, u, junk, j0, je, p, hstar, B, vmin, mg, Dh, MD);
     return bad;
+}
+
+// A decoded block's samples from a warp's shared slot to global memory:
+// 16-byte streaming stores when blocks are whole 16-byte vectors.
+template <typename T>
+__device__ __forceinline__ void copy_block_out(T *dstg, const T *u, uint32_t n_b, uint32_t L)
+{
+    const uint32_t lane = threadIdx.x & 31u;
+    if ((L * sizeof(T)) % 16 == 0) {
+        constexpr uint32_t VE = 16 / sizeof(T);
+        const uint32_t nv = n_b / VE;
+        const uint4 *sv4 = reinterpret_cast<const uint4 *>(u);
+        uint4 *dv4 = reinterpret_cast<uint4 *>(dstg);
+        for (uint32_t v = lane; v < nv; v += 32) __stcs(dv4 + v, sv4[v]);
+        for (uint32_t i = nv * VE + lane; i < n_b; i += 32) dstg[i] = u[i];
+    } else {
+        for (uint32_t i = lane; i < n_b; i += 32) dstg[i] = u[i];
+    }
 }
 
 // Per-block decoding parameters, held by one lane each in k_decode_w.
@@ -800,7 +820,7 @@ constexpr uint32_t kWarpTileBlocks = 32; // blocks per warp tile (one lane each)
 #ifndef PCX_DECODE_MIN_CTAS
 #define PCX_DECODE_MIN_CTAS 5
 #endif
-template <typename T, uint32_t WB, uint32_t VAR, bool ORB>
+template <typename T, uint32_t WB, uint32_t VAR, bool ORB, bool CHUNKED>
 __global__ void __launch_bounds__(kDecWarpsMax * 32, PCX_DECODE_MIN_CTAS)
 k_decode_w(const uint8_t *__restrict__ in, uint32_t L, T *__restrict__ out, uint64_t *__restrict__ n_out,
            WsHeader *ws, const uint64_t *__restrict__ offsets, OrbitTable ot, uint64_t limit_ns)
@@ -810,9 +830,10 @@ k_decode_w(const uint8_t *__restrict__ in, uint32_t L, T *__restrict__ out, uint
     extern __shared__ __align__(16) uint8_t smem[];
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
     // per warp: one block's samples (+ padding, + junk for idle lanes), then
-    // two buffers of packed words: the next block's words stream in while
-    // the current block is decoded
-    const uint32_t wmax = (uint32_t)words_bound(VAR, D, WB, L);
+    // two buffers of packed words: a whole block's (the next block streams in
+    // while the current one is decoded), or, for long blocks, kDecChunk words
+    // (the next chunk, of this block or the next, streams in)
+    const uint32_t cw = dec_chunk_words(VAR, D, WB, L);
     const uint32_t slot_bytes = (uint32_t)round_up((uint64_t)(L + 2 * kPad) * sizeof(T), 16);
     const uint32_t warp_bytes = decw_warp_bytes(VAR, D, WB, L);
     const uint32_t nwarps = blockDim.x >> 5;
@@ -839,114 +860,226 @@ k_decode_w(const uint8_t *__restrict__ in, uint32_t L, T *__restrict__ out, uint
         }
         const uint32_t incl = warp_incl_scan_u32(mine.W);
         mine.woff = incl - mine.W;
-        const uint64_t base = offsets[wt];
-        auto prefetch = [&](uint32_t b) {  // block b's words into buffer b & 1
-            const uint32_t Wb = __shfl_sync(0xFFFFFFFFu, mine.W, (int)b);
-            const uint32_t ob = __shfl_sync(0xFFFFFFFFu, mine.woff, (int)b);
-            const Word *g = payload + base + ob;
-            Word *dstw = wbuf + (b & 1u) * wmax;
-            for (uint32_t j = lane; j < Wb; j += 32) cp_async_small<sizeof(Word)>(dstw + j, g + j);
-            cp_async_commit();
-        };
-        prefetch(0);
+        if constexpr (!CHUNKED) {
+            const uint64_t base = offsets[wt];
+            auto prefetch = [&](uint32_t b) {  // block b's words into buffer b & 1
+                const uint32_t Wb = __shfl_sync(0xFFFFFFFFu, mine.W, (int)b);
+                const uint32_t ob = __shfl_sync(0xFFFFFFFFu, mine.woff, (int)b);
+                const Word *g = payload + base + ob;
+                Word *dstw = wbuf + (b & 1u) * cw;
+                for (uint32_t j = lane; j < Wb; j += 32) cp_async_small<sizeof(Word)>(dstw + j, g + j);
+                cp_async_commit();
+            };
+            prefetch(0);
 
-        for (uint32_t b = 0; b < nblk; ++b) {
-            if (b + 1 < nblk) prefetch(b + 1);
-            else cp_async_commit();
-            cp_async_wait<1>();
-            __syncwarp();
-            const DecBlock k = shfl_block(mine, (int)b);
-            const uint64_t gb = blk0 + b;
-            const uint32_t vmin = k.vmin, W = k.W, n_b = k.n_b;
-            const Word *wsrc = wbuf + (b & 1u) * wmax;
-            if (W == 0) {
-                for (uint32_t i = lane; i < n_b; i += 32) u[i] = (T)vmin;
-            } else if constexpr (VAR == PC_VARIANT_BASIC) {
-                const uint32_t p = k.p;
-                bad |= decode_basic_block<T, WB>(wsrc, u, u + L + kPad, W, p, k.hstar, k.B, vmin, k.mg, k.Dh, k.MD);
+            for (uint32_t b = 0; b < nblk; ++b) {
+                if (b + 1 < nblk) prefetch(b + 1);
+                else cp_async_commit();
+                cp_async_wait<1>();
                 __syncwarp();
-                if (lane == 0)
-                    for (uint32_t i = n_b; i < W * p; ++i) bad |= (uint32_t)u[i] != vmin;
-            } else {
-                const Word *src = wsrc;
-                const uint32_t hstar = k.hstar, B32 = (uint32_t)k.B;
-                uint32_t cR = 1, cr = 0, qlast = 0, plast = 0;
-                for (uint32_t j0 = 0; j0 < W; j0 += 32) {
-                    const uint32_t i = j0 + lane;
-                    const bool valid = i < W;
-                    SeriesEntry e;
-                    uint64_t s = 0;
-                    if (valid) {
-                        e = orbit_entry(ot, k.ov, i);
-                        s = src[i];
-                    } else {
-                        e = SeriesEntry{1u, 0u, 0u, Magic32{0xFFFFFFFFu, 0xFFFFFFFFu, 0u}};
-                    }
-                    uint32_t r = 0;
-                    uint64_t body = 0;
-                    if (valid) {
-                        if constexpr (WB == 32) {
-                            const uint32_t q32 = magic_div((uint32_t)s, e.mgR);
-                            r = (uint32_t)s - q32 * e.R;
-                            body = q32;
+                const DecBlock k = shfl_block(mine, (int)b);
+                const uint64_t gb = blk0 + b;
+                const uint32_t vmin = k.vmin, W = k.W, n_b = k.n_b;
+                const Word *wsrc = wbuf + (b & 1u) * cw;
+                if (W == 0) {
+                    for (uint32_t i = lane; i < n_b; i += 32) u[i] = (T)vmin;
+                } else if constexpr (VAR == PC_VARIANT_BASIC) {
+                    const uint32_t p = k.p;
+                    bad |= decode_basic_block<T, WB>(wsrc, u, u + L + kPad, 0, W, p, k.hstar, k.B, vmin, k.mg, k.Dh, k.MD);
+                    __syncwarp();
+                    if (lane == 0)
+                        for (uint32_t i = n_b; i < W * p; ++i) bad |= (uint32_t)u[i] != vmin;
+                } else {
+                    const Word *src = wsrc;
+                    const uint32_t hstar = k.hstar, B32 = (uint32_t)k.B;
+                    uint32_t cR = 1, cr = 0, qlast = 0, plast = 0;
+                    for (uint32_t j0 = 0; j0 < W; j0 += 32) {
+                        const uint32_t i = j0 + lane;
+                        const bool valid = i < W;
+                        SeriesEntry e;
+                        uint64_t s = 0;
+                        if (valid) {
+                            e = orbit_entry(ot, k.ov, i);
+                            s = src[i];
                         } else {
-                            body = divmod_small64(s, e.R, e.mgR, r);
+                            e = SeriesEntry{1u, 0u, 0u, Magic32{0xFFFFFFFFu, 0xFFFFFFFFu, 0u}};
+                        }
+                        uint32_t r = 0;
+                        uint64_t body = 0;
+                        if (valid) {
+                            if constexpr (WB == 32) {
+                                const uint32_t q32 = magic_div((uint32_t)s, e.mgR);
+                                r = (uint32_t)s - q32 * e.R;
+                                body = q32;
+                            } else {
+                                body = divmod_small64(s, e.R, e.mgR, r);
+                            }
+                        }
+                        uint32_t Rp = __shfl_up_sync(0xFFFFFFFFu, e.R, 1);
+                        uint32_t rp = __shfl_up_sync(0xFFFFFFFFu, r, 1);
+                        if (lane == 0) {
+                            Rp = cR;
+                            rp = cr;
+                        }
+                        cR = __shfl_sync(0xFFFFFFFFu, e.R, 31);
+                        cr = __shfl_sync(0xFFFFFFFFu, r, 31);
+                        if (!valid) continue;
+                        T *last = u + e.q + e.p - 1;
+                        uint32_t rem = e.p;
+                        while (rem >= hstar && (body >> 32) != 0) {
+                            uint64_t lo;
+                            body = divmod_inv64(body, k.Dh, k.MD, lo);
+                            rev_exact<T>(last, (uint32_t)lo, hstar, B32, k.mg, vmin);
+                            last -= hstar;
+                            rem -= hstar;
+                        }
+                        bad |= (body >> 32) != 0;
+                        const uint32_t top = rev_quot<T>(last, (uint32_t)body, rem, B32, k.mg, vmin);
+                        if (i == 0) {
+                            bad |= top != 0;
+                        } else {
+                            const uint64_t val = (uint64_t)top * Rp + rp;
+                            bad |= val >= k.B;
+                            u[e.q - 1] = (T)(val + vmin);
+                        }
+                        if (e.q + e.p >= n_b) bad |= r != 0;
+                        if (i == W - 1) {
+                            qlast = e.q;
+                            plast = e.p;
                         }
                     }
-                    uint32_t Rp = __shfl_up_sync(0xFFFFFFFFu, e.R, 1);
-                    uint32_t rp = __shfl_up_sync(0xFFFFFFFFu, r, 1);
-                    if (lane == 0) {
-                        Rp = cR;
-                        rp = cr;
-                    }
-                    cR = __shfl_sync(0xFFFFFFFFu, e.R, 31);
-                    cr = __shfl_sync(0xFFFFFFFFu, r, 31);
-                    if (!valid) continue;
-                    T *last = u + e.q + e.p - 1;
-                    uint32_t rem = e.p;
-                    while (rem >= hstar && (body >> 32) != 0) {
-                        uint64_t lo;
-                        body = divmod_inv64(body, k.Dh, k.MD, lo);
-                        rev_exact<T>(last, (uint32_t)lo, hstar, B32, k.mg, vmin);
-                        last -= hstar;
-                        rem -= hstar;
-                    }
-                    bad |= (body >> 32) != 0;
-                    const uint32_t top = rev_quot<T>(last, (uint32_t)body, rem, B32, k.mg, vmin);
-                    if (i == 0) {
-                        bad |= top != 0;
-                    } else {
-                        const uint64_t val = (uint64_t)top * Rp + rp;
-                        bad |= val >= k.B;
-                        u[e.q - 1] = (T)(val + vmin);
-                    }
-                    if (e.q + e.p >= n_b) bad |= r != 0;
-                    if (i == W - 1) {
-                        qlast = e.q;
-                        plast = e.p;
-                    }
+                    __syncwarp();
+                    const uint32_t src_lane = (W - 1) & 31u;
+                    qlast = __shfl_sync(0xFFFFFFFFu, qlast, src_lane);
+                    plast = __shfl_sync(0xFFFFFFFFu, plast, src_lane);
+                    if (lane == 0)
+                        for (uint32_t i = n_b; i < qlast + plast; ++i) bad |= (uint32_t)u[i] != vmin;
                 }
                 __syncwarp();
-                const uint32_t src_lane = (W - 1) & 31u;
-                qlast = __shfl_sync(0xFFFFFFFFu, qlast, src_lane);
-                plast = __shfl_sync(0xFFFFFFFFu, plast, src_lane);
-                if (lane == 0)
-                    for (uint32_t i = n_b; i < qlast + plast; ++i) bad |= (uint32_t)u[i] != vmin;
+                // this block's samples out
+                T *dstg = out + gb * L;
+                copy_block_out<T>(dstg, u, n_b, L);
+                __syncwarp();
             }
-            __syncwarp();
-            // this block's samples out
-            T *dstg = out + gb * L;
-            if ((L * sizeof(T)) % 16 == 0) {
-                constexpr uint32_t VE = 16 / sizeof(T);
-                const uint32_t nv = n_b / VE;
-                const uint4 *sv4 = reinterpret_cast<const uint4 *>(u);
-                uint4 *dv4 = reinterpret_cast<uint4 *>(dstg);
-                for (uint32_t v = lane; v < nv; v += 32) __stcs(dv4 + v, sv4[v]);
-                for (uint32_t i = nv * VE + lane; i < n_b; i += 32) dstg[i] = u[i];
-            } else {
-                for (uint32_t i = lane; i < n_b; i += 32) dstg[i] = u[i];
+        } else {
+            const uint64_t base = offsets[wt];
+            const uint32_t nz = __ballot_sync(0xFFFFFFFFu, lane < nblk && mine.W > 0);  // blocks with words
+            auto prefetch = [&](uint32_t b, uint32_t c, uint32_t slot) {  // chunk c of block b into a buffer
+                const uint32_t Wb = __shfl_sync(0xFFFFFFFFu, mine.W, (int)b);
+                const uint32_t ob = __shfl_sync(0xFFFFFFFFu, mine.woff, (int)b);
+                const uint32_t j0 = c * cw, cnt = min(cw, Wb - j0);
+                const Word *g = payload + base + ob + j0;
+                Word *dstw = wbuf + slot * cw;
+                for (uint32_t j = lane; j < cnt; j += 32) cp_async_small<sizeof(Word)>(dstw + j, g + j);
+                cp_async_commit();
+            };
+            uint32_t slot = 0;
+            if (nz) prefetch((uint32_t)__ffs(nz) - 1u, 0, 0);
+
+            for (uint32_t b = 0; b < nblk; ++b) {
+                const DecBlock k = shfl_block(mine, (int)b);
+                const uint64_t gb = blk0 + b;
+                const uint32_t vmin = k.vmin, W = k.W, n_b = k.n_b;
+                if (W == 0) {
+                    for (uint32_t i = lane; i < n_b; i += 32) u[i] = (T)vmin;
+                } else {
+                    const uint32_t nch = (W + cw - 1) / cw;
+                    uint32_t cR = 1, cr = 0, qlast = 0, plast = 0;  // advanced: carries across words
+                    for (uint32_t c = 0; c < nch; ++c) {
+                        // the next chunk: this block's next, else the next block with words
+                        if (c + 1 < nch) {
+                            prefetch(b, c + 1, slot ^ 1u);
+                        } else {
+                            const uint32_t later = nz & ~((2u << b) - 1u);
+                            if (later) prefetch((uint32_t)__ffs(later) - 1u, 0, slot ^ 1u);
+                            else cp_async_commit();
+                        }
+                        cp_async_wait<1>();
+                        __syncwarp();
+                        const Word *wsrc = wbuf + slot * cw;
+                        const uint32_t jb = c * cw, je = min(W, jb + cw);
+                        if constexpr (VAR == PC_VARIANT_BASIC) {
+                            bad |= decode_basic_block<T, WB>(wsrc, u, u + L + kPad, jb, je, k.p, k.hstar, k.B, vmin, k.mg,
+                                                             k.Dh, k.MD);
+                        } else {
+                            const uint32_t hstar = k.hstar, B32 = (uint32_t)k.B;
+                            for (uint32_t j0 = jb; j0 < je; j0 += 32) {
+                                const uint32_t i = j0 + lane;
+                                const bool valid = i < je;
+                                SeriesEntry e;
+                                uint64_t s = 0;
+                                if (valid) {
+                                    e = orbit_entry(ot, k.ov, i);
+                                    s = wsrc[i - jb];
+                                } else {
+                                    e = SeriesEntry{1u, 0u, 0u, Magic32{0xFFFFFFFFu, 0xFFFFFFFFu, 0u}};
+                                }
+                                uint32_t r = 0;
+                                uint64_t body = 0;
+                                if (valid) {
+                                    if constexpr (WB == 32) {
+                                        const uint32_t q32 = magic_div((uint32_t)s, e.mgR);
+                                        r = (uint32_t)s - q32 * e.R;
+                                        body = q32;
+                                    } else {
+                                        body = divmod_small64(s, e.R, e.mgR, r);
+                                    }
+                                }
+                                uint32_t Rp = __shfl_up_sync(0xFFFFFFFFu, e.R, 1);
+                                uint32_t rp = __shfl_up_sync(0xFFFFFFFFu, r, 1);
+                                if (lane == 0) {
+                                    Rp = cR;
+                                    rp = cr;
+                                }
+                                cR = __shfl_sync(0xFFFFFFFFu, e.R, 31);
+                                cr = __shfl_sync(0xFFFFFFFFu, r, 31);
+                                if (!valid) continue;
+                                T *last = u + e.q + e.p - 1;
+                                uint32_t rem = e.p;
+                                while (rem >= hstar && (body >> 32) != 0) {
+                                    uint64_t lo;
+                                    body = divmod_inv64(body, k.Dh, k.MD, lo);
+                                    rev_exact<T>(last, (uint32_t)lo, hstar, B32, k.mg, vmin);
+                                    last -= hstar;
+                                    rem -= hstar;
+                                }
+                                bad |= (body >> 32) != 0;
+                                const uint32_t top = rev_quot<T>(last, (uint32_t)body, rem, B32, k.mg, vmin);
+                                if (i == 0) {
+                                    bad |= top != 0;
+                                } else {
+                                    const uint64_t val = (uint64_t)top * Rp + rp;
+                                    bad |= val >= k.B;
+                                    u[e.q - 1] = (T)(val + vmin);
+                                }
+                                if (e.q + e.p >= n_b) bad |= r != 0;
+                                if (i == W - 1) {
+                                    qlast = e.q;
+                                    plast = e.p;
+                                }
+                            }
+                        }
+                        __syncwarp();  // the buffer is free for the chunk after next
+                        slot ^= 1u;
+                    }
+                    // digits past the block's end must be padding (offset 0)
+                    uint32_t end;
+                    if constexpr (VAR == PC_VARIANT_BASIC) {
+                        end = W * k.p;
+                    } else {
+                        const uint32_t src_lane = (W - 1) & 31u;
+                        qlast = __shfl_sync(0xFFFFFFFFu, qlast, src_lane);
+                        plast = __shfl_sync(0xFFFFFFFFu, plast, src_lane);
+                        end = qlast + plast;
+                    }
+                    for (uint32_t i = n_b + lane; i < end; i += 32) bad |= (uint32_t)u[i] != vmin;
+                }
+                __syncwarp();
+                // this block's samples out
+                T *dstg = out + gb * L;
+                copy_block_out<T>(dstg, u, n_b, L);
+                __syncwarp();
             }
-            __syncwarp();
         }
         if (wt == n_wt - 1 && lane == 0) *n_out = n;
     }
@@ -984,7 +1117,8 @@ static cudaError_t launch_decompress_t(const LaunchArgs &a)
     // 2. decode: warp tiles where no serial walk is needed, CTA tiles otherwise
     constexpr bool kWarpPath = VAR == PC_VARIANT_BASIC || (ORB && sizeof(T) == 2);
     if constexpr (kWarpPath) {
-        auto kern = k_decode_w<T, WB, VAR, ORB>;
+        auto kern = dec_chunked(VAR, sizeof(T) * 8, WB, a.L) ? k_decode_w<T, WB, VAR, ORB, true>
+                                                             : k_decode_w<T, WB, VAR, ORB, false>;
         const uint32_t nwarps = decw_warps(VAR, sizeof(T) * 8, WB, a.L);
         if (nwarps < 1) return cudaErrorInvalidConfiguration;
         const uint32_t smem = nwarps * decw_warp_bytes(VAR, sizeof(T) * 8, WB, a.L);

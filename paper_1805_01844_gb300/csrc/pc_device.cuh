@@ -159,7 +159,7 @@ __device__ __forceinline__ bool lookback_warp(uint64_t *status, uint64_t tile, u
 // element e goes to slot (e / L) at offset (e % L).  16-byte vector copies
 // when a block's bytes are a multiple of 16 (then every block starts 16-byte
 // aligned in both spaces), element copies otherwise.
-template <typename T>
+template <typename T, uint32_t NT = kThreads>
 __device__ __forceinline__ void load_tile(const T *__restrict__ in, uint64_t g0, uint64_t cnt,
                                           uint32_t L, uint8_t *stage, uint32_t stage_bytes)
 {
@@ -169,15 +169,15 @@ __device__ __forceinline__ void load_tile(const T *__restrict__ in, uint64_t g0,
         const uint64_t nvec = cnt / VE;
         const uint4 *src = reinterpret_cast<const uint4 *>(in + g0);
         uint32_t b = threadIdx.x / vpb, o = threadIdx.x - b * vpb;
-        const uint32_t sb = kThreads / vpb, so = kThreads - sb * vpb;
+        const uint32_t sb = NT / vpb, so = NT - sb * vpb;
         uint64_t v = threadIdx.x;
         // four loads in flight per thread before their shared-memory stores
-        for (; v + 3 * kThreads < nvec; v += 4 * kThreads) {
+        for (; v + 3 * NT < nvec; v += 4 * NT) {
             uint4 x[4];
             uint32_t bb[4], oo[4];
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                x[k] = __ldcs(src + v + k * kThreads);
+                x[k] = __ldcs(src + v + k * NT);
                 bb[k] = b;
                 oo[k] = o;
                 o += so;
@@ -188,19 +188,19 @@ __device__ __forceinline__ void load_tile(const T *__restrict__ in, uint64_t g0,
             for (int k = 0; k < 4; ++k)
                 *reinterpret_cast<uint4 *>(stage + (uint64_t)bb[k] * stage_bytes + oo[k] * 16u) = x[k];
         }
-        for (; v < nvec; v += kThreads) {
+        for (; v < nvec; v += NT) {
             uint4 x = __ldcs(src + v);
             *reinterpret_cast<uint4 *>(stage + (uint64_t)b * stage_bytes + o * 16u) = x;
             o += so;
             b += sb;
             if (o >= vpb) { o -= vpb; ++b; }
         }
-        for (uint64_t e = nvec * VE + threadIdx.x; e < cnt; e += kThreads) {
+        for (uint64_t e = nvec * VE + threadIdx.x; e < cnt; e += NT) {
             uint32_t bi = (uint32_t)(e / L), oi = (uint32_t)(e - (uint64_t)bi * L);
             reinterpret_cast<T *>(stage + (uint64_t)bi * stage_bytes)[oi] = in[g0 + e];
         }
     } else {
-        for (uint64_t e = threadIdx.x; e < cnt; e += kThreads) {
+        for (uint64_t e = threadIdx.x; e < cnt; e += NT) {
             uint32_t bi = (uint32_t)(e / L), oi = (uint32_t)(e - (uint64_t)bi * L);
             reinterpret_cast<T *>(stage + (uint64_t)bi * stage_bytes)[oi] = in[g0 + e];
         }
@@ -210,7 +210,7 @@ __device__ __forceinline__ void load_tile(const T *__restrict__ in, uint64_t g0,
 // load_tile with asynchronous copies for the 16-byte granules (blocks must be
 // a whole number of granules); the ragged tail of the stream, if any, is
 // copied synchronously.  The caller commits the group and waits for it.
-template <typename T>
+template <typename T, uint32_t NT = kThreads>
 __device__ __forceinline__ void load_tile_async(const T *__restrict__ in, uint64_t g0, uint64_t cnt,
                                                 uint32_t L, uint8_t *stage, uint32_t stage_bytes)
 {
@@ -219,14 +219,14 @@ __device__ __forceinline__ void load_tile_async(const T *__restrict__ in, uint64
     const uint64_t nvec = cnt / VE;
     const uint4 *src = reinterpret_cast<const uint4 *>(in + g0);
     uint32_t b = threadIdx.x / vpb, o = threadIdx.x - b * vpb;
-    const uint32_t sb = kThreads / vpb, so = kThreads - sb * vpb;
-    for (uint64_t v = threadIdx.x; v < nvec; v += kThreads) {
+    const uint32_t sb = NT / vpb, so = NT - sb * vpb;
+    for (uint64_t v = threadIdx.x; v < nvec; v += NT) {
         cp_async16(stage + (uint64_t)b * stage_bytes + o * 16u, src + v);
         o += so;
         b += sb;
         if (o >= vpb) { o -= vpb; ++b; }
     }
-    for (uint64_t e = nvec * VE + threadIdx.x; e < cnt; e += kThreads) {
+    for (uint64_t e = nvec * VE + threadIdx.x; e < cnt; e += NT) {
         uint32_t bi = (uint32_t)(e / L), oi = (uint32_t)(e - (uint64_t)bi * L);
         reinterpret_cast<T *>(stage + (uint64_t)bi * stage_bytes)[oi] = in[g0 + e];
     }

@@ -45,7 +45,8 @@ class PcBatchItem(ctypes.Structure):
 class PcBatchInfo(ctypes.Structure):
     _fields_ = [("n_items", ctypes.c_uint32), ("smem_bytes", ctypes.c_uint32),
                 ("total_tiles", ctypes.c_uint64), ("plan_bytes", ctypes.c_uint64),
-                ("workspace_bytes", ctypes.c_uint64)]
+                ("workspace_bytes", ctypes.c_uint64), ("cta_threads", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32)]
 
 
 class PcSource(ctypes.Structure):
@@ -196,10 +197,11 @@ def compress_noalloc_raw(d_in, n_samples, p, d_out, out_capacity, d_out_bytes, s
                                       int(out_capacity), d_out_bytes, stream or None)
 
 
-def batch_describe(items):
+def batch_describe(items, cta_threads=256):
     """items: list of PcBatchItem.  Returns (ctypes array, PcBatchInfo)."""
     arr = (PcBatchItem * len(items))(*items)
     info = PcBatchInfo()
+    info.cta_threads = cta_threads
     _check(load().pc_batch_describe(arr, len(items), ctypes.byref(info)), "pc_batch_describe")
     return arr, info
 

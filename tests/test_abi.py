@@ -112,8 +112,8 @@ using namespace pcx;
 int main() {
   for (unsigned k = 0; k < 2; ++k) for (unsigned v = 0; v < 2; ++v)
   for (unsigned d = 16; d <= 32; d += 16) for (unsigned w = 32; w <= 64; w += 32)
-  for (unsigned L = 1; L <= 8192; ++L) for (int orb = 0; orb < 2; ++orb) {
-    TileCfg c = tile_cfg(k, v, d, w, L, orb != 0);
+  for (unsigned L = 1; L <= 8192; ++L) for (int orb = 0; orb < 2; ++orb) for (unsigned nt = 128; nt <= 256; nt *= 2) {
+    TileCfg c = tile_cfg(k, v, d, w, L, orb != 0, nt);
     if (c.smem > 227u * 1024u || c.tb < 1 || c.tb > 32) { printf("bad %u %u %u %u %u\n", k, v, d, w, L); return 1; }
     if (c.slots == 2 && (L * (d / 8)) % 16 != 0) { printf("slots %u\n", L); return 1; }
     if (k == 1) {

@@ -12,7 +12,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 import paper_1805_01844_gb300 as pc  # noqa: E402
-from paper_1805_01844_gb300.batch import Batch, autotune  # noqa: E402
+from paper_1805_01844_gb300.batch import Batch, autotune, autotune_threads  # noqa: E402
 
 
 def dev():
@@ -30,7 +30,8 @@ def small_specs(n_streams, seed):
     return datagen.batched_stream_specs(n_streams, min_bytes=64, max_bytes=2 << 20, seed=seed)
 
 
-def test_batch_matches_oracle_per_item():
+@pytest.mark.parametrize("cta_threads", [256, 128])
+def test_batch_matches_oracle_per_item(cta_threads):
     rng = np.random.default_rng(3)
     specs = small_specs(40, seed=1)
     hosts, tensors, params = [], [], []
@@ -48,7 +49,8 @@ def test_batch_matches_oracle_per_item():
         hosts.append(x)
         tensors.append(to_dev(x))
         params.append(native.params(1, 16, 64, 1024))
-    b = Batch(tensors, params)
+    b = Batch(tensors, params, cta_threads=cta_threads)
+    assert b.info.cta_threads == cta_threads
     b.compress()
     assert b.device_status() == 0
     got = b.streams()
@@ -83,3 +85,12 @@ def test_autotune_picks_the_smallest_candidate():
     sizes = {(L, w): len(oracle.compress(head, 0, w, L)) for L in (128, 256, 512, 1024, 2048, 4096)
              for w in (32, 64)}
     assert len(oracle.compress(head, 0, p.word_bits, p.block_len)) == min(sizes.values())
+
+
+def test_autotune_threads_returns_a_candidate():
+    specs = small_specs(8, seed=4)
+    tensors = [to_dev(datagen.batched_stream(sp)) for sp in specs]
+    params = [native.params(0, t.element_size() * 8, 64, 256) for t in tensors]
+    nt, times = autotune_threads(tensors, params, reps=2)
+    assert nt in (128, 256) and set(times) == {128, 256} and times[nt] == min(times.values())
+
