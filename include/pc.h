@@ -90,10 +90,14 @@ pc_status pc_bound(const pc_params *params, uint64_t n_samples, uint64_t *max_by
  * at most n_samples samples with *params: a 64-byte header, 8 bytes per tile
  * of blocks (look-back words, decoding offsets) and, for the advanced variant,
  * a table of the split-base series of every base B <= 65536 the stream meets
- * (about 17 MB, filled lazily by the kernels).  The advanced variant also
- * runs with a smaller workspace that only has room for the look-back words
- * and offsets; each block then walks its series serially (same bytes,
- * slower).  Host only.  Errors as for pc_bound. */
+ * (about 17 MB, filled lazily by the kernels).  The table depends on the base
+ * and the word size only, so it is kept across calls that reuse the
+ * workspace (a tag in the workspace header records the word size it was
+ * built for; any other content, including a fresh allocation, is cleared by
+ * the first call).  Calls that share a workspace must not overlap on the
+ * GPU.  The advanced variant also runs with a smaller workspace that only
+ * has room for the look-back words and offsets; each block then walks its
+ * series serially (same bytes, slower).  Host only.  Errors as for pc_bound. */
 pc_status pc_workspace_size(const pc_params *params, uint64_t n_samples, uint64_t *bytes);
 
 /* Compress n_samples samples (uint16 or uint32 per params->dtype_bits) from

@@ -42,6 +42,21 @@ bool pick_layout(const pc_params *p, uint64_t n, uint64_t workspace_bytes, WsLay
     return workspace_bytes >= lay.bytes;
 }
 
+// Per call: the header's ticket, status and timeout count, and the look-back
+// words, cleared; the series table kept if its tag names this word size
+// (without a table the cursors and the tag are cleared too).
+cudaError_t clear_workspace(void *d_workspace, const WsLayout &lay, uint32_t w, cudaStream_t s)
+{
+    uint8_t *base = static_cast<uint8_t *>(d_workspace);
+    WsHeader *ws = reinterpret_cast<WsHeader *>(base);
+    cudaError_t e = cudaMemsetAsync(base, 0, lay.orbit ? 12 : 32, s);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(base + lay.off_status, 0, 8 * lay.n_status, s)) != cudaSuccess) return e;
+    if (!lay.orbit) return cudaSuccess;
+    return launch_orbit_prepare(ws, reinterpret_cast<uint32_t *>(base + lay.off_flags), kOrbitFlagsBytes,
+                                &ws->orbit_cursor, nullptr, kOrbitTagOne | w, s);
+}
+
 void fill_workspace(LaunchArgs &a, void *d_workspace, const WsLayout &lay)
 {
     uint8_t *base = static_cast<uint8_t *>(d_workspace);
@@ -124,7 +139,7 @@ pc_status pc_compress(const void *d_in, uint64_t n_samples, const pc_params *par
     a.nt = nt;
     a.limit_ns = kWaitLimitNs;
     a.stream = static_cast<cudaStream_t>(stream);
-    if (cudaMemsetAsync(d_workspace, 0, lay.clear_bytes, a.stream) != cudaSuccess) return PC_ERR_CUDA;
+    if (clear_workspace(d_workspace, lay, a.w, a.stream) != cudaSuccess) return PC_ERR_CUDA;
     if (launch_compress(a) != cudaSuccess) return PC_ERR_CUDA;
     return PC_OK;
 }
@@ -157,8 +172,9 @@ pc_status pc_decompress(const void *d_in, uint64_t in_bytes, const pc_params *pa
     fill_workspace(a, d_workspace, lay);
     a.limit_ns = kWaitLimitNs;
     a.stream = static_cast<cudaStream_t>(stream);
-    // header, table flags, look-back words: cleared; offsets are written before they are read
-    if (cudaMemsetAsync(d_workspace, 0, lay.clear_bytes, a.stream) != cudaSuccess) return PC_ERR_CUDA;
+    // header words and look-back words cleared, the series table kept or
+    // cleared; offsets are written before they are read
+    if (clear_workspace(d_workspace, lay, a.w, a.stream) != cudaSuccess) return PC_ERR_CUDA;
     if (launch_decompress(a) != cudaSuccess) return PC_ERR_CUDA;
     return PC_OK;
 }

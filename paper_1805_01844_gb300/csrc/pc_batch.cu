@@ -30,10 +30,11 @@ struct BatchItemDev {
 };
 static_assert(sizeof(BatchItemDev) % 16 == 0, "descriptors stay 16-byte aligned");
 
-// Batch workspace: header, two series-table flag arrays (w = 32, 64), the
-// look-back words (one per tile of every item), then the two tables.
+// Batch workspace: header, the two series tables (w = 32, 64: flags, flags,
+// headers, slots, headers, slots; kept across calls, see ws_layout), then the
+// look-back words (one per tile of every item).
 struct BatchLayout {
-    uint64_t off_flags32, off_flags64, off_status, clear_bytes, off_hdr32, off_slots32, off_hdr64, off_slots64,
+    uint64_t off_flags32, off_flags64, off_hdr32, off_slots32, off_hdr64, off_slots64, off_status, n_status,
         bytes;
 };
 
@@ -42,13 +43,13 @@ PCX_HD BatchLayout batch_layout(uint64_t total_tiles)
     BatchLayout b;
     b.off_flags32 = sizeof(WsHeader);
     b.off_flags64 = b.off_flags32 + kOrbitFlagsBytes;
-    b.off_status = b.off_flags64 + kOrbitFlagsBytes;
-    b.clear_bytes = b.off_status + 8 * (total_tiles + 1);
-    b.off_hdr32 = round_up(b.clear_bytes, 16);
+    b.off_hdr32 = b.off_flags64 + kOrbitFlagsBytes;
     b.off_slots32 = b.off_hdr32 + kOrbitHdrBytes;
     b.off_hdr64 = b.off_slots32 + kOrbitSlotBytes;
     b.off_slots64 = b.off_hdr64 + kOrbitHdrBytes;
-    b.bytes = b.off_slots64 + kOrbitSlotBytes;
+    b.off_status = b.off_slots64 + kOrbitSlotBytes;
+    b.n_status = total_tiles + 1;
+    b.bytes = b.off_status + 8 * b.n_status;
     return b;
 }
 
@@ -354,6 +355,18 @@ uint64_t item_tiles(const pc_batch_item &it, uint32_t nt)
     return ceil_div(ceil_div(it.n_samples, p.block_len), cfg.tb);
 }
 
+// Per call: header words and look-back words cleared, the tables kept or
+// cleared (tag check on the device).
+cudaError_t clear_batch_workspace(uint8_t *base, const BatchLayout &lay, cudaStream_t s)
+{
+    WsHeader *ws = reinterpret_cast<WsHeader *>(base);
+    cudaError_t e = cudaMemsetAsync(base, 0, 12, s);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(base + lay.off_status, 0, 8 * lay.n_status, s)) != cudaSuccess) return e;
+    return launch_orbit_prepare(ws, reinterpret_cast<uint32_t *>(base + lay.off_flags32), 2 * kOrbitFlagsBytes,
+                                &ws->orbit_cursor, &ws->reserved_cursor64, kOrbitTagBatch, s);
+}
+
 OrbitTable batch_table(uint8_t *base, uint64_t off_flags, uint64_t off_hdr, uint64_t off_slots, uint32_t *cursor)
 {
     return OrbitTable{reinterpret_cast<uint32_t *>(base + off_flags), reinterpret_cast<uint64_t *>(base + off_hdr),
@@ -538,7 +551,7 @@ pc_status pc_compress_batch(const pc_batch_info *info, const void *d_plan, void 
     if (workspace_bytes < info->workspace_bytes || info->n_items == 0) return PC_ERR_INVALID_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const BatchLayout lay = batch_layout(info->total_tiles);
-    if (cudaMemsetAsync(d_workspace, 0, lay.clear_bytes, s) != cudaSuccess) return PC_ERR_CUDA;
+    if (clear_batch_workspace(static_cast<uint8_t *>(d_workspace), lay, s) != cudaSuccess) return PC_ERR_CUDA;
     const BatchItemDev *items = static_cast<const BatchItemDev *>(d_plan);
     const uint64_t *prefix = reinterpret_cast<const uint64_t *>(static_cast<const uint8_t *>(d_plan) +
                                                                 sizeof(BatchItemDev) * (uint64_t)info->n_items);
@@ -626,7 +639,7 @@ pc_status pc_compress_segments(const pc_segments_info *info, const void *d_plan,
     const BatchLayout lay = batch_layout(n_seg);
     uint8_t *base = static_cast<uint8_t *>(d_workspace);
     const SourceDev *src = static_cast<const SourceDev *>(d_plan);
-    if (cudaMemsetAsync(d_workspace, 0, lay.clear_bytes, s) != cudaSuccess) return PC_ERR_CUDA;
+    if (clear_batch_workspace(static_cast<uint8_t *>(d_workspace), lay, s) != cudaSuccess) return PC_ERR_CUDA;
     pc_status st = PC_OK;
     if (info->dtype_bits == 16 || info->variant == PC_VARIANT_BASIC) {
         st = launch_segments_w(info, src, d_options, base, lay, s);

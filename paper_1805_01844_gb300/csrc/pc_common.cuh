@@ -35,9 +35,6 @@ constexpr uint64_t kWaitLimitNs = 1000000000ull;  // bounded device waits: 1 s
 #ifndef PCX_TILE_BUDGET_ADVANCED
 #define PCX_TILE_BUDGET_ADVANCED (100u * 1024u)
 #endif
-#ifndef PCX_COMPRESS_SLOTS
-#define PCX_COMPRESS_SLOTS 1
-#endif
 // shared memory a tile may use; sets the blocks per tile
 constexpr uint32_t kTileBudgetBasic = PCX_TILE_BUDGET_BASIC;
 constexpr uint32_t kTileBudgetAdvanced = PCX_TILE_BUDGET_ADVANCED;
@@ -52,7 +49,8 @@ struct WsHeader {
     uint32_t orbit_cursor;  // next free slot of the series table (advanced)
     uint32_t reserved_cursor64;  // same, second table of a batch (64-bit words)
     uint32_t reserved1;
-    uint64_t reserved[5];
+    uint64_t orbit_tag;  // series tables valid for this layout and word size (see ws_layout)
+    uint64_t reserved[4];
 };
 static_assert(sizeof(WsHeader) == 64, "workspace header is 64 bytes");
 
@@ -121,9 +119,8 @@ struct TileCfg {
     uint32_t tb;          // blocks per tile
     uint32_t S;           // staged samples per block (block_len + kPad)
     uint32_t stage_bytes; // bytes per staged block (multiple of 16)
-    uint32_t slots;       // tiles in flight per CTA (2: one loads while the other is packed)
     uint32_t wcap;        // schedule entries per block (advanced), else 0
-    uint32_t slot_bytes;  // bytes of one slot
+    uint32_t slot_bytes;  // bytes of the tile's shared memory
     uint32_t off_sched;   // within a slot: u64 [tb][wcap]: R | p << 32 | q << 40
     uint32_t off_tops;    // within a slot: u32 [tb][wcap]: decoded high parts r'_{i-1}
     uint32_t off_blk;     // within a slot: per-block scalars, see BlockVars
@@ -169,9 +166,6 @@ struct BlockVars {        // per-tile arrays in shared memory
 enum : uint32_t { kKernelCompress = 0, kKernelDecode = 1 };
 
 // Tile of the compression kernel (kind 0) or of the decoding kernel (kind 1).
-// Compression keeps two tiles in flight per CTA when a block is a whole
-// number of 16-byte vectors (asynchronous copies need 16-byte granules) and
-// two blocks' slots fit the budget.
 PCX_HD TileCfg tile_cfg(uint32_t kind, uint32_t variant, uint32_t d, uint32_t w, uint32_t L, bool orbit,
                         uint32_t nt = kThreads)
 {
@@ -185,10 +179,7 @@ PCX_HD TileCfg tile_cfg(uint32_t kind, uint32_t variant, uint32_t d, uint32_t w,
     // a 128-thread CTA gets about half the shared memory of a 256-thread one
     const uint32_t budget = (variant == PC_VARIANT_ADVANCED ? kTileBudgetAdvanced : kTileBudgetBasic) /
                             (nt <= 128 ? 2u : 1u);
-    const uint32_t one = c.stage_bytes + c.wcap * 12u;
-    c.slots = (PCX_COMPRESS_SLOTS == 2 && kind == kKernelCompress && (L * (d / 8)) % 16 == 0 &&
-               2u * one <= budget) ? 2u : 1u;
-    const uint32_t per_block = c.slots * one;
+    const uint32_t per_block = c.stage_bytes + c.wcap * 12u;
     uint32_t tb = budget / per_block;
     if (tb < 1) tb = 1;
     if (tb > kMaxTileBlocks) tb = kMaxTileBlocks;
@@ -203,7 +194,7 @@ PCX_HD TileCfg tile_cfg(uint32_t kind, uint32_t variant, uint32_t d, uint32_t w,
     c.off_blk = off;
     off += (uint32_t)sizeof(BlockVars);
     c.slot_bytes = (uint32_t)round_up(off, 16);
-    c.smem = c.slots * c.slot_bytes;
+    c.smem = c.slot_bytes;
     return c;
 }
 
@@ -220,20 +211,25 @@ PCX_HD uint32_t compress_threads(uint32_t variant, uint32_t d, uint32_t w, uint3
 // Blocks per tile of the decompression offsets kernel (one thread per block).
 constexpr uint32_t kOffsetTileBlocks = kThreads;
 
-// Workspace layout: the header; the flags of the series table (advanced with
-// the table); the look-back words; the decoding-tile offsets plus the total
-// (decompression); the headers and slots of the series table.  The header,
-// the flags and the look-back words are cleared by every call.
+// Workspace layout: the header; the series table (advanced with the table:
+// flags, headers, slots) at fixed offsets; the look-back words; the
+// decoding-tile offsets plus the total (decompression).  The table depends on
+// (B, w) only, so it is kept across calls that reuse the workspace: a call
+// clears the header's first words and its look-back words, and a one-CTA
+// kernel clears the table's flags only when the header's tag does not name
+// this layout and word size (a fresh workspace, another word size, or a call
+// of another layout in between, which rewrites or clears the tag).
 constexpr uint64_t kOrbitFlagsBytes = 262160;     // (65536 + 1) u32, padded to 16
 constexpr uint64_t kOrbitHdrBytes = 524304;       // (65536 + 1) u64, padded to 16
 constexpr uint64_t kOrbitSlotBytes = 16ull << 20; // 2^20 slots of 16 bytes
+constexpr uint64_t kOrbitTagOne = 0x4F52424954310000ull;    // | w: one table, single stream
+constexpr uint64_t kOrbitTagBatch = 0x4F52424954320000ull;  // two tables (w = 32, 64): batches
 
 struct WsLayout {
     uint64_t n_status;     // look-back words
     uint64_t n_offsets;    // decoding-tile offsets
     bool orbit;            // series table present
-    uint64_t off_flags, off_status, off_offsets, off_hdr, off_slots;
-    uint64_t clear_bytes;  // bytes cleared per call, from offset 0
+    uint64_t off_flags, off_hdr, off_slots, off_status, off_offsets;
     uint64_t bytes;
 };
 
@@ -249,12 +245,11 @@ PCX_HD WsLayout ws_layout(uint32_t variant, uint32_t d, uint32_t w, uint32_t L, 
     lay.n_status = (ctiles > otiles ? ctiles : otiles) + 1;  // + 1: the self-test uses two words
     lay.n_offsets = dtiles + 1;
     lay.off_flags = sizeof(WsHeader);
-    lay.off_status = lay.off_flags + (lay.orbit ? kOrbitFlagsBytes : 0);
-    lay.clear_bytes = lay.off_status + 8 * lay.n_status;
-    lay.off_offsets = lay.clear_bytes;
-    lay.off_hdr = round_up(lay.off_offsets + 8 * lay.n_offsets, 16);
+    lay.off_hdr = lay.off_flags + (lay.orbit ? kOrbitFlagsBytes : 0);
     lay.off_slots = lay.off_hdr + (lay.orbit ? kOrbitHdrBytes : 0);
-    lay.bytes = lay.off_slots + (lay.orbit ? kOrbitSlotBytes : 0);
+    lay.off_status = lay.off_slots + (lay.orbit ? kOrbitSlotBytes : 0);
+    lay.off_offsets = lay.off_status + 8 * lay.n_status;
+    lay.bytes = round_up(lay.off_offsets + 8 * lay.n_offsets, 16);
     return lay;
 }
 

@@ -44,6 +44,32 @@ static cudaError_t launch_compress_nt(const LaunchArgs &a)
     return a.nt == 128 ? launch_compress_t<T, WB, VAR, ORB, 128>(a) : launch_compress_t<T, WB, VAR, ORB, 256>(a);
 }
 
+// One CTA: clear the series tables' flags and cursors unless the header's tag
+// says they were built for this layout and word size, then set the tag.
+__global__ void k_orbit_prepare(WsHeader *ws, uint32_t *flags, uint64_t flag_bytes, uint32_t *cursor0,
+                                uint32_t *cursor1, uint64_t tag)
+{
+    __shared__ uint32_t stale;
+    if (threadIdx.x == 0) stale = ws->orbit_tag != tag;
+    __syncthreads();
+    if (!stale) return;
+    uint4 *f = reinterpret_cast<uint4 *>(flags);
+    for (uint64_t i = threadIdx.x; i < flag_bytes / 16; i += blockDim.x) f[i] = make_uint4(0u, 0u, 0u, 0u);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        *cursor0 = 0;
+        if (cursor1) *cursor1 = 0;
+        ws->orbit_tag = tag;
+    }
+}
+
+cudaError_t launch_orbit_prepare(WsHeader *ws, uint32_t *flags, uint64_t flag_bytes, uint32_t *cursor0,
+                                 uint32_t *cursor1, uint64_t tag, cudaStream_t stream)
+{
+    k_orbit_prepare<<<1, 1024, 0, stream>>>(ws, flags, flag_bytes, cursor0, cursor1, tag);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_compress(const LaunchArgs &a)
 {
     const uint32_t key = (a.d == 32 ? 4u : 0u) | (a.w == 64 ? 2u : 0u) | (a.variant ? 1u : 0u);

@@ -34,6 +34,9 @@ struct LaunchArgs {
 };
 
 cudaError_t launch_compress(const LaunchArgs &a);
+// Keep or clear the series tables of a workspace (see ws_layout).
+cudaError_t launch_orbit_prepare(WsHeader *ws, uint32_t *flags, uint64_t flag_bytes, uint32_t *cursor0,
+                                 uint32_t *cursor1, uint64_t tag, cudaStream_t stream);
 cudaError_t launch_decompress(const LaunchArgs &a);
 cudaError_t launch_selftest_wait(WsHeader *ws, uint64_t *status, uint64_t limit_ns, cudaStream_t stream);
 
