@@ -394,9 +394,10 @@ def main():
     if not args.no_sweep and rank == 0 and world == 1:
         sweep = sweep_params(x, n, dev)
 
-    cfg1 = None
+    cfg1 = small = None
     if not args.no_cfg1 and rank == 0 and world == 1:
         cfg1 = white_noise_2e30(dev, peak)
+        small = white_noise_65536_latency(dev)
 
     batch = None
     if not args.no_batch and rank == 0 and world == 1:
@@ -430,10 +431,67 @@ def main():
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                      "alg_bytes_per_launch": alg_bytes, "traffic": recorded_traffic(key)},
         "cpu_baseline": cpu, "cpu_baseline_all_cores": cpu_all, "e2e": e2e, "gpu_launches": 3 * args.steps,
-        "white_noise_2e30": cfg1, "batch": batch, "sweep": sweep, "learned": learned, "serving": serving,
+        "white_noise_2e30": cfg1, "white_noise_65536": small, "batch": batch, "sweep": sweep, "learned": learned, "serving": serving,
         "clocks": clk, "wall_s_timed": wall,
     }
     print(json.dumps(line), flush=True)
+
+
+def white_noise_65536_latency(dev, reps=200):
+    """The 65,536-sample white-noise parity workload (N(300, 5), seed 0, basic,
+    L = 1024, w = 64): it fits in L2 and is bound by launch latency, so it is
+    reported as the time of one compress and one decompress call (median,
+    CUDA events), plus both replayed from one CUDA graph."""
+    import numpy as np
+    import torch
+
+    import paper_1805_01844_gb300 as pc
+    from paper_1805_01844_gb300 import datagen
+
+    x = torch.from_numpy(datagen.white_noise(65536, 300.0, 5.0, seed=0).view(np.int16)).to(dev)
+    n = x.numel()
+    codec = pc.Codec(pc.BASIC, 16, 64, 1024, max_samples=n, device=dev)
+    sbuf = torch.empty(codec.bound(n), dtype=torch.uint8, device=dev)
+    ybuf = torch.empty(n, dtype=torch.int16, device=dev)
+
+    def step():
+        codec.compress(x, out=sbuf)
+        codec.decompress(sbuf, sbuf.numel(), n, out=ybuf)
+
+    for _ in range(5):
+        step()
+    torch.cuda.synchronize()
+    assert torch.equal(ybuf, x) and codec.device_status() == 0
+    tc, td = [], []
+    for _ in range(reps):
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record()
+        codec.compress(x, out=sbuf)
+        e[1].record()
+        codec.decompress(sbuf, sbuf.numel(), n, out=ybuf)
+        e[2].record()
+        torch.cuda.synchronize()
+        tc.append(e[0].elapsed_time(e[1]))
+        td.append(e[1].elapsed_time(e[2]))
+    s = torch.cuda.Stream(dev)
+    with torch.cuda.stream(s):
+        step()
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            step()
+    tg = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        g.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        tg.append(e0.elapsed_time(e1))
+    assert torch.equal(ybuf, x)
+    med = lambda a: sorted(a)[len(a) // 2] * 1e3  # noqa: E731
+    return {"workload": "white_noise_N300_5_65536_u16", "variant": "basic", "block_len": 1024, "word_bits": 64,
+            "compress_us": med(tc), "decompress_us": med(td), "round_trip_graph_us": med(tg)}
 
 
 def white_noise_2e30(dev, peak, steps=20):

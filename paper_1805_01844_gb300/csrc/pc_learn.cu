@@ -30,8 +30,9 @@ static_assert(2 * NW + 4 * (NP - NW) == PC_MLP_WEIGHT_BYTES, "weight buffer size
 // ------------------------------------------------------------- features
 
 // Features of segment `seg` of a source (in, n), written by one warp to f[24];
-// lane l summarises sub-block l (128 samples).  Sums are exact: integers for
-// 16-bit samples, doubles (integers below 2^53 per lane) for 32-bit ones.
+// lane l summarises sub-block l (128 samples).  16-bit samples: exact integer
+// sums, the variance's numerator in integers, the rest in FP32 (GB300's FP64
+// rate is a small fraction of its FP32 rate); 32-bit samples: sums in FP64.
 template <typename T>
 __device__ __forceinline__ void segment_features(const T *__restrict__ in, uint64_t n, uint64_t seg, uint32_t d,
                                                  float *__restrict__ f)
@@ -82,16 +83,20 @@ __device__ __forceinline__ void segment_features(const T *__restrict__ in, uint6
             ++cnt;
         }
     }
-    if constexpr (sizeof(T) == 2) {
-        sum = (double)isum;  // < 2^23 and < 2^39 per lane: exact
-        sq = (double)isq;
-    }
     const uint32_t vmin = __reduce_min_sync(0xFFFFFFFFu, mn);
     const uint32_t vmax = __reduce_max_sync(0xFFFFFFFFu, mx);
     uint32_t tot = __reduce_add_sync(0xFFFFFFFFu, cnt);
-    for (int o = 16; o > 0; o >>= 1) {
-        sum += __shfl_xor_sync(0xFFFFFFFFu, sum, o);
-        sq += __shfl_xor_sync(0xFFFFFFFFu, sq, o);
+    if constexpr (sizeof(T) == 2) {
+        // exact integer totals (sum < 2^28, sum of squares < 2^44)
+        for (int o = 16; o > 0; o >>= 1) {
+            isum += __shfl_xor_sync(0xFFFFFFFFu, isum, o);
+            isq += __shfl_xor_sync(0xFFFFFFFFu, isq, o);
+        }
+    } else {
+        for (int o = 16; o > 0; o >>= 1) {
+            sum += __shfl_xor_sync(0xFFFFFFFFu, sum, o);
+            sq += __shfl_xor_sync(0xFFFFFFFFu, sq, o);
+        }
     }
     // sub-block range class: floor(log2(range + 1)), 0..15
     const uint32_t range = cnt ? mx - mn : 0;
@@ -106,16 +111,29 @@ __device__ __forceinline__ void segment_features(const T *__restrict__ in, uint6
         if (lane == b) hist = c;
     }
     if (tot == 0) tot = 1;
-    const double dmax = d == 16 ? 65535.0 : 4294967295.0;
-    const double mean = sum / tot;
-    const double var = fmax(sq / tot - mean * mean, 0.0);
     if (lane < 16) f[3 + lane] = hist / 32.0f;
     if (lane == 0) {
-        f[0] = (float)(vmin / dmax);
-        f[1] = (float)(vmax / dmax);
-        f[2] = (float)(log2((double)(vmax - vmin) + 1.0) / d);
-        f[19] = (float)(mean / dmax);
-        f[20] = (float)(log2(var + 1.0) / (2.0 * d));
+        if constexpr (sizeof(T) == 2) {
+            // FP32 from exact integers: tot^2 var = tot sum(v^2) - sum(v)^2 (< 2^56)
+            const float dmax = 65535.0f;
+            const uint64_t num = (uint64_t)tot * isq - isum * isum;
+            const float mean = (float)isum / (float)tot;
+            const float var = (float)num / ((float)tot * (float)tot);
+            f[0] = (float)vmin / dmax;
+            f[1] = (float)vmax / dmax;
+            f[2] = log2f((float)(vmax - vmin) + 1.0f) / 16.0f;
+            f[19] = mean / dmax;
+            f[20] = log2f(var + 1.0f) / 32.0f;
+        } else {
+            const double dmax = 4294967295.0;
+            const double mean = sum / tot;
+            const double var = fmax(sq / tot - mean * mean, 0.0);
+            f[0] = (float)(vmin / dmax);
+            f[1] = (float)(vmax / dmax);
+            f[2] = (float)(log2((double)(vmax - vmin) + 1.0) / d);
+            f[19] = (float)(mean / dmax);
+            f[20] = (float)(log2(var + 1.0) / (2.0 * d));
+        }
         f[21] = spike / 32.0f;
         f[22] = d / 32.0f;
         f[23] = (float)(seg & 63u) / 64.0f;
