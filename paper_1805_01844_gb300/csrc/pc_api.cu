@@ -117,7 +117,8 @@ pc_status pc_compress(const void *d_in, uint64_t n_samples, const pc_params *par
     const uint32_t nt = compress_threads(params->variant, params->dtype_bits, params->word_bits, params->block_len);
     const TileCfg cfg = tile_cfg(kKernelCompress, params->variant, params->dtype_bits, params->word_bits,
                                  params->block_len, lay.orbit, nt);
-    const uint64_t n_tiles = ceil_div(n_blocks, cfg.tb);
+    const uint32_t tb = small_stream_tb(n_blocks, cfg.tb);
+    const uint64_t n_tiles = ceil_div(n_blocks, tb);
     if (n_tiles >> 31) return PC_ERR_UNSUPPORTED;  // tile tickets are 32-bit
     uint64_t need = 0;
     pc_bound(params, n_samples, &need);
@@ -137,6 +138,7 @@ pc_status pc_compress(const void *d_in, uint64_t n_samples, const pc_params *par
     a.n_blocks = n_blocks;
     a.n_tiles = n_tiles;
     a.nt = nt;
+    a.tb = tb;
     a.limit_ns = kWaitLimitNs;
     a.stream = static_cast<cudaStream_t>(stream);
     if (clear_workspace(d_workspace, lay, a.w, a.stream) != cudaSuccess) return PC_ERR_CUDA;
@@ -169,6 +171,8 @@ pc_status pc_decompress(const void *d_in, uint64_t in_bytes, const pc_params *pa
     a.out = d_out;
     a.cap = out_capacity_samples;
     a.out_count = d_n_samples;
+    // warp tiles of the decoder, from the largest stream the call accepts
+    a.tb = small_stream_tb(ceil_div(out_capacity_samples, params->block_len), 32);
     fill_workspace(a, d_workspace, lay);
     a.limit_ns = kWaitLimitNs;
     a.stream = static_cast<cudaStream_t>(stream);

@@ -26,7 +26,8 @@ struct BatchItemDev {
     uint64_t n_tiles;  // real tiles (0 for an empty item, which still owns one ticket)
     uint32_t L;
     uint32_t key;      // dtype 32 << 2 | word 64 << 1 | advanced
-    uint64_t pad_;
+    uint32_t tb;       // blocks per tile
+    uint32_t pad_;
 };
 static_assert(sizeof(BatchItemDev) % 16 == 0, "descriptors stay 16-byte aligned");
 
@@ -68,6 +69,8 @@ k_compress_batch(const BatchItemDev *__restrict__ items, const uint64_t *__restr
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ uint64_t s_tile;
     __shared__ uint32_t s_item;
+    stage_bars_init();
+    uint32_t phase = 0;
     for (;;) {
         if (threadIdx.x == 0) {
             const uint64_t t = atomicAdd(&ws->ticket, 1u);
@@ -97,6 +100,7 @@ k_compress_batch(const BatchItemDev *__restrict__ items, const uint64_t *__restr
         sa.status = status + prefix[i];
         sa.n_blocks = it.n_blocks;
         sa.n_tiles = it.n_tiles;
+        sa.tb = it.tb;
         sa.ot = (it.key & 2u) ? ot64 : ot32;
         const uint64_t tile = t - prefix[i];
         if (it.n_tiles == 0) {
@@ -113,14 +117,14 @@ k_compress_batch(const BatchItemDev *__restrict__ items, const uint64_t *__restr
             continue;
         }
         switch (it.key) {
-        case 0: compress_tile<uint16_t, 32, 0, false, NT>(sa, tile, smem, ws, limit_ns); break;
-        case 1: compress_tile<uint16_t, 32, 1, true, NT>(sa, tile, smem, ws, limit_ns); break;
-        case 2: compress_tile<uint16_t, 64, 0, false, NT>(sa, tile, smem, ws, limit_ns); break;
-        case 3: compress_tile<uint16_t, 64, 1, true, NT>(sa, tile, smem, ws, limit_ns); break;
-        case 4: compress_tile<uint32_t, 32, 0, false, NT>(sa, tile, smem, ws, limit_ns); break;
-        case 5: compress_tile<uint32_t, 32, 1, true, NT>(sa, tile, smem, ws, limit_ns); break;
-        case 6: compress_tile<uint32_t, 64, 0, false, NT>(sa, tile, smem, ws, limit_ns); break;
-        default: compress_tile<uint32_t, 64, 1, true, NT>(sa, tile, smem, ws, limit_ns); break;
+        case 0: compress_tile<uint16_t, 32, 0, false, NT>(sa, tile, smem, ws, limit_ns, phase); break;
+        case 1: compress_tile<uint16_t, 32, 1, true, NT>(sa, tile, smem, ws, limit_ns, phase); break;
+        case 2: compress_tile<uint16_t, 64, 0, false, NT>(sa, tile, smem, ws, limit_ns, phase); break;
+        case 3: compress_tile<uint16_t, 64, 1, true, NT>(sa, tile, smem, ws, limit_ns, phase); break;
+        case 4: compress_tile<uint32_t, 32, 0, false, NT>(sa, tile, smem, ws, limit_ns, phase); break;
+        case 5: compress_tile<uint32_t, 32, 1, true, NT>(sa, tile, smem, ws, limit_ns, phase); break;
+        case 6: compress_tile<uint32_t, 64, 0, false, NT>(sa, tile, smem, ws, limit_ns, phase); break;
+        default: compress_tile<uint32_t, 64, 1, true, NT>(sa, tile, smem, ws, limit_ns, phase); break;
         }
     }
 }
@@ -151,6 +155,7 @@ __global__ void k_segment_items(const SourceDev *__restrict__ src, uint32_t n_sr
     it.out_bytes = s.out_bytes + j;
     it.n_blocks = ceil_div(it.n, L);
     it.n_tiles = 1;
+    it.tb = (uint32_t)it.n_blocks;  // the whole segment is one tile
     it.L = L;
     it.key = (d == 32 ? 4u : 0u) | (w == 64 ? 2u : 0u) | (variant ? 1u : 0u);
     it.pad_ = 0;
@@ -530,6 +535,7 @@ pc_status pc_batch_plan(const pc_batch_item *items, uint32_t n_items, const pc_b
         d.out_bytes = it.d_out_bytes;
         d.n_blocks = ceil_div(it.n_samples, p.block_len);
         d.n_tiles = item_tiles(it, info->cta_threads);
+        d.tb = tile_cfg(kKernelCompress, p.variant, p.dtype_bits, p.word_bits, p.block_len, true, info->cta_threads).tb;
         d.L = p.block_len;
         d.key = (p.dtype_bits == 32 ? 4u : 0u) | (p.word_bits == 64 ? 2u : 0u) | (p.variant ? 1u : 0u);
         dv[i] = d;

@@ -211,6 +211,19 @@ PCX_HD uint32_t compress_threads(uint32_t variant, uint32_t d, uint32_t w, uint3
 // Blocks per tile of the decompression offsets kernel (one thread per block).
 constexpr uint32_t kOffsetTileBlocks = kThreads;
 
+// Short streams: with few blocks, full tiles would leave most SMs idle, so
+// tiles shrink (halving while the stream has fewer than kSmallTiles tiles)
+// down to one block.  Compression tiles and the decoder's warp tiles (at most
+// 32 blocks each) follow the same rule; the workspace always has room for
+// 2 kSmallTiles + 1 look-back words and offsets.
+constexpr uint64_t kSmallTiles = 2432;  // 152 SMs x 16
+
+PCX_HD uint32_t small_stream_tb(uint64_t n_blocks, uint32_t tb)
+{
+    while (tb > 1 && ceil_div(n_blocks, tb) < kSmallTiles) tb = (tb + 1) / 2;
+    return tb;
+}
+
 // Workspace layout: the header; the series table (advanced with the table:
 // flags, headers, slots) at fixed offsets; the look-back words; the
 // decoding-tile offsets plus the total (decompression).  The table depends on
@@ -238,10 +251,12 @@ PCX_HD WsLayout ws_layout(uint32_t variant, uint32_t d, uint32_t w, uint32_t L, 
     const uint64_t n_blocks = ceil_div(n, L);
     WsLayout lay;
     lay.orbit = orbit && variant == PC_VARIANT_ADVANCED;
-    const uint64_t ctiles = ceil_div(
-        n_blocks, tile_cfg(kKernelCompress, variant, d, w, L, lay.orbit, compress_threads(variant, d, w, L)).tb);
+    const uint32_t ctb = tile_cfg(kKernelCompress, variant, d, w, L, lay.orbit, compress_threads(variant, d, w, L)).tb;
+    const uint64_t ctiles = ceil_div(n_blocks, small_stream_tb(n_blocks, ctb));
     const uint64_t otiles = ceil_div(n_blocks, kOffsetTileBlocks);
-    const uint64_t dtiles = ceil_div(n_blocks, tile_cfg(kKernelDecode, variant, d, w, L, lay.orbit).tb);
+    const uint64_t dtiles_cta = ceil_div(n_blocks, tile_cfg(kKernelDecode, variant, d, w, L, lay.orbit).tb);
+    const uint64_t dtiles_warp = ceil_div(n_blocks, small_stream_tb(n_blocks, 32));
+    const uint64_t dtiles = dtiles_cta > dtiles_warp ? dtiles_cta : dtiles_warp;
     lay.n_status = (ctiles > otiles ? ctiles : otiles) + 1;  // + 1: the self-test uses two words
     lay.n_offsets = dtiles + 1;
     lay.off_flags = sizeof(WsHeader);

@@ -33,6 +33,7 @@ static cudaError_t launch_compress_t(const LaunchArgs &a)
     sa.status = a.status;
     sa.n_blocks = a.n_blocks;
     sa.n_tiles = a.n_tiles;
+    sa.tb = a.tb;
     sa.ot = OrbitTable{a.orb_flags, a.orb_hdr, static_cast<ulonglong2 *>(a.orb_slots), &a.ws->orbit_cursor};
     kern<<<(unsigned)grid, NT, cfg.smem, a.stream>>>(sa, a.ws, a.limit_ns);
     return cudaGetLastError();

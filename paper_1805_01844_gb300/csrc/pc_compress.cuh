@@ -309,6 +309,16 @@ __device__ __forceinline__ void write_header(uint8_t *out, uint32_t L, uint64_t 
     h64[7] = 0;
 }
 
+// One mbarrier per warp for the bulk copies of its blocks (compression tiles).
+__shared__ uint64_t g_stage_bar[kMaxTileBlocks / 4];
+
+__device__ __forceinline__ void stage_bars_init()
+{
+    if (threadIdx.x < kMaxTileBlocks / 4) mbar_init(&g_stage_bar[threadIdx.x], 1);
+    mbar_init_fence();
+    __syncthreads();
+}
+
 // One stream as the compression kernels see it.
 struct StreamArgs {
     const void *in;
@@ -318,6 +328,7 @@ struct StreamArgs {
     uint64_t *out_bytes;
     uint64_t *status;  // look-back words of this stream's tiles
     uint64_t n_blocks, n_tiles;
+    uint32_t tb;       // blocks per tile (the tile layout's, or fewer for a short stream)
     OrbitTable ot;
 };
 
@@ -327,7 +338,8 @@ struct StreamArgs {
 // its payload offset, then write its table entries and packed words; the last
 // tile writes the header, the table padding and the stream size.
 template <typename T, uint32_t WB, uint32_t VAR, bool ORB, uint32_t NT = kThreads>
-__device__ void compress_tile(const StreamArgs &sa, uint64_t tile, uint8_t *smem, WsHeader *ws, uint64_t limit_ns)
+__device__ void compress_tile(const StreamArgs &sa, uint64_t tile, uint8_t *smem, WsHeader *ws, uint64_t limit_ns,
+                              uint32_t &phase)
 {
     using Word = typename WordOf<T, WB>::type;
     constexpr uint32_t D = sizeof(T) * 8;
@@ -339,25 +351,37 @@ __device__ void compress_tile(const StreamArgs &sa, uint64_t tile, uint8_t *smem
     const T *in = static_cast<const T *>(sa.in);
     const uint64_t n = sa.n, n_blocks = sa.n_blocks, n_tiles = sa.n_tiles;
     const uint64_t payload_off = PC_HEADER_BYTES + table_bytes(n_blocks, D);
-    const uint64_t blk0 = tile * cfg.tb;
-    const uint32_t nblk = (uint32_t)umin64(cfg.tb, n_blocks - blk0);
+    const uint64_t blk0 = tile * sa.tb;
+    const uint32_t nblk = (uint32_t)umin64(sa.tb, n_blocks - blk0);
     const uint64_t cnt = umin64(n - blk0 * L, (uint64_t)nblk * L);
 
     if ((L * sizeof(T)) % 16 == 0) {
-        // 1-2. each warp stages its own blocks (all granules in flight at
-        // once) and finds their min / max as soon as its copies land
+        // 1-2. each warp stages its own blocks and finds their min / max as
+        // soon as they land: lane 0 issues one bulk copy (TMA engine) per
+        // block, completing on the warp's mbarrier; the ragged end of the
+        // last block comes element by element
         constexpr uint32_t VE = 16 / sizeof(T);
+        if (lane == 0) {
+            uint32_t bytes = 0;
+            for (uint32_t b = warp; b < nblk; b += (NT / 32))
+                bytes += ((uint32_t)umin64(L, cnt - (uint64_t)b * L) / VE) * 16u;
+            fence_proxy_async_smem();  // the stage's earlier generic accesses before the async writes
+            mbar_arrive_expect_tx(&g_stage_bar[warp], bytes);
+            for (uint32_t b = warp; b < nblk; b += (NT / 32)) {
+                const uint32_t nb16 = ((uint32_t)umin64(L, cnt - (uint64_t)b * L) / VE) * 16u;
+                if (nb16)
+                    bulk_copy_g2s(smem + (uint64_t)b * cfg.stage_bytes, in + (blk0 + b) * L, nb16,
+                                  &g_stage_bar[warp]);
+            }
+        }
         for (uint32_t b = warp; b < nblk; b += (NT / 32)) {
             const uint32_t n_b = (uint32_t)umin64(L, cnt - (uint64_t)b * L);
-            const uint4 *src = reinterpret_cast<const uint4 *>(in + (blk0 + b) * L);
             uint8_t *dst = smem + (uint64_t)b * cfg.stage_bytes;
-            const uint32_t nv = n_b / VE;
-            for (uint32_t v = lane; v < nv; v += 32) cp_async16(dst + v * 16u, src + v);
-            for (uint32_t e = nv * VE + lane; e < n_b; e += 32)
+            for (uint32_t e = n_b / VE * VE + lane; e < n_b; e += 32)
                 reinterpret_cast<T *>(dst)[e] = in[(blk0 + b) * L + e];
         }
-        cp_async_commit();
-        cp_async_wait<0>();
+        if (!mbar_wait(&g_stage_bar[warp], phase & 1u, limit_ns) && lane == 0) record_error(ws, PC_ERR_TIMEOUT);
+        ++phase;  // every warp's barrier completed one phase
         __syncwarp();
         for (uint32_t b = warp; b < nblk; b += (NT / 32)) {
             const uint32_t n_b = (uint32_t)umin64(L, cnt - (uint64_t)b * L);
@@ -523,13 +547,15 @@ k_compress(StreamArgs sa, WsHeader *ws, uint64_t limit_ns)
         if (blockIdx.x == 0 && threadIdx.x == 0) write_empty_stream<sizeof(T) * 8, WB, VAR>(sa);
         return;
     }
+    stage_bars_init();
+    uint32_t phase = 0;
     for (;;) {
         if (threadIdx.x == 0) s_tile = atomicAdd(&ws->ticket, 1u);
         __syncthreads();
         const uint64_t tile = s_tile;
         __syncthreads();
         if (tile >= sa.n_tiles) break;
-        compress_tile<T, WB, VAR, ORB, NT>(sa, tile, smem, ws, limit_ns);
+        compress_tile<T, WB, VAR, ORB, NT>(sa, tile, smem, ws, limit_ns, phase);
     }
 }
 

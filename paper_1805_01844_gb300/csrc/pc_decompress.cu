@@ -808,7 +808,7 @@ __device__ __forceinline__ DecBlock shfl_block(const DecBlock &x, int src)
 }
 
 constexpr uint32_t kDecWarpsMax = 4;     // warps per CTA of k_decode_w (decw_warps)
-constexpr uint32_t kWarpTileBlocks = 32; // blocks per warp tile (one lane each)
+// blocks per warp tile: at most 32 (one lane each), fewer for a short stream (small_stream_tb)
 
 // Warp-granular decoding (basic, and advanced with the series table on 16-bit
 // data): no shared barrier at all.  A warp owns 32 consecutive blocks; lane b
@@ -823,7 +823,7 @@ constexpr uint32_t kWarpTileBlocks = 32; // blocks per warp tile (one lane each)
 template <typename T, uint32_t WB, uint32_t VAR, bool ORB, bool CHUNKED>
 __global__ void __launch_bounds__(kDecWarpsMax * 32, PCX_DECODE_MIN_CTAS)
 k_decode_w(const uint8_t *__restrict__ in, uint32_t L, T *__restrict__ out, uint64_t *__restrict__ n_out,
-           WsHeader *ws, const uint64_t *__restrict__ offsets, OrbitTable ot, uint64_t limit_ns)
+           WsHeader *ws, const uint64_t *__restrict__ offsets, OrbitTable ot, uint64_t limit_ns, uint32_t wtb)
 {
     using Word = typename WordT<T, WB>::type;
     constexpr uint32_t D = sizeof(T) * 8;
@@ -843,15 +843,15 @@ k_decode_w(const uint8_t *__restrict__ in, uint32_t L, T *__restrict__ out, uint
     if (*reinterpret_cast<volatile uint32_t *>(&ws->status) != PC_OK) return;
     const uint64_t *h64 = reinterpret_cast<const uint64_t *>(in);
     const uint64_t n = h64[2], n_blocks = h64[3];
-    const uint64_t n_wt = ceil_div(n_blocks, kWarpTileBlocks);
+    const uint64_t n_wt = ceil_div(n_blocks, wtb);
     const uint64_t payload_off = PC_HEADER_BYTES + table_bytes(n_blocks, D);
     const Word *payload = reinterpret_cast<const Word *>(in + payload_off);
     const uint64_t gw0 = (uint64_t)blockIdx.x * nwarps + warp, nw = (uint64_t)gridDim.x * nwarps;
     bool bad = false;
 
     for (uint64_t wt = gw0; wt < n_wt; wt += nw) {
-        const uint64_t blk0 = wt * kWarpTileBlocks;
-        const uint32_t nblk = (uint32_t)umin64(kWarpTileBlocks, n_blocks - blk0);
+        const uint64_t blk0 = wt * wtb;
+        const uint32_t nblk = (uint32_t)umin64(wtb, n_blocks - blk0);
         DecBlock mine{};
         if (lane < nblk) {
             const uint64_t gb = blk0 + lane;
@@ -1108,7 +1108,7 @@ static cudaError_t launch_decompress_t(const LaunchArgs &a)
         if (need < grid) grid = need;
         if (grid < 1) grid = 1;
         constexpr bool kWarpTiles = VAR == PC_VARIANT_BASIC || (ORB && sizeof(T) == 2);
-        const uint32_t dtb = kWarpTiles ? kWarpTileBlocks : cfg.tb;
+        const uint32_t dtb = kWarpTiles ? a.tb : cfg.tb;
         kern<<<(unsigned)grid, kThreads, 0, a.stream>>>(
             static_cast<const uint8_t *>(a.in), a.in_bytes, a.L, a.cap, a.out_count, a.ws, a.status,
             a.n_status, a.offsets, a.n_offsets, dtb, a.limit_ns, ot);
@@ -1136,7 +1136,7 @@ static cudaError_t launch_decompress_t(const LaunchArgs &a)
         if (grid < 1) grid = 1;
         kern<<<(unsigned)grid, nwarps * 32, smem, a.stream>>>(
             static_cast<const uint8_t *>(a.in), a.L, static_cast<T *>(a.out), a.out_count, a.ws, a.offsets, ot,
-            a.limit_ns);
+            a.limit_ns, a.tb);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     } else {
         auto kern = k_decode<T, WB, VAR, ORB>;

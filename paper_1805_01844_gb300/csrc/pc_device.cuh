@@ -53,6 +53,55 @@ __device__ __forceinline__ void cp_async_small(void *smem, const void *gmem)
     asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(s), "l"(gmem), "n"(BYTES) : "memory");
 }
 
+// Bulk (TMA engine) copies global -> shared completing on an mbarrier.
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    const unsigned a = (unsigned)__cvta_generic_to_shared(bar);
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_init_fence()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    const unsigned a = (unsigned)__cvta_generic_to_shared(bar);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes) : "memory");
+}
+
+// bytes: a multiple of 16; both addresses 16-byte aligned
+__device__ __forceinline__ void bulk_copy_g2s(void *smem, const void *gmem, uint32_t bytes, uint64_t *bar)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem);
+    const unsigned a = (unsigned)__cvta_generic_to_shared(bar);
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(d), "l"(gmem), "r"(bytes), "r"(a) : "memory");
+}
+
+// Bounded wait for the mbarrier phase of the given parity; false if it gave up.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint64_t limit_ns)
+{
+    const unsigned a = (unsigned)__cvta_generic_to_shared(bar);
+    const uint64_t t0 = globaltimer();
+    for (uint32_t spins = 0;; ++spins) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (spins > (1u << 22) || globaltimer() - t0 > limit_ns) return false;
+    }
+}
+
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 
 template <int N>
@@ -204,31 +253,6 @@ __device__ __forceinline__ void load_tile(const T *__restrict__ in, uint64_t g0,
             uint32_t bi = (uint32_t)(e / L), oi = (uint32_t)(e - (uint64_t)bi * L);
             reinterpret_cast<T *>(stage + (uint64_t)bi * stage_bytes)[oi] = in[g0 + e];
         }
-    }
-}
-
-// load_tile with asynchronous copies for the 16-byte granules (blocks must be
-// a whole number of granules); the ragged tail of the stream, if any, is
-// copied synchronously.  The caller commits the group and waits for it.
-template <typename T, uint32_t NT = kThreads>
-__device__ __forceinline__ void load_tile_async(const T *__restrict__ in, uint64_t g0, uint64_t cnt,
-                                                uint32_t L, uint8_t *stage, uint32_t stage_bytes)
-{
-    constexpr uint32_t VE = 16 / sizeof(T);
-    const uint32_t vpb = L / VE;
-    const uint64_t nvec = cnt / VE;
-    const uint4 *src = reinterpret_cast<const uint4 *>(in + g0);
-    uint32_t b = threadIdx.x / vpb, o = threadIdx.x - b * vpb;
-    const uint32_t sb = NT / vpb, so = NT - sb * vpb;
-    for (uint64_t v = threadIdx.x; v < nvec; v += NT) {
-        cp_async16(stage + (uint64_t)b * stage_bytes + o * 16u, src + v);
-        o += so;
-        b += sb;
-        if (o >= vpb) { o -= vpb; ++b; }
-    }
-    for (uint64_t e = nvec * VE + threadIdx.x; e < cnt; e += NT) {
-        uint32_t bi = (uint32_t)(e / L), oi = (uint32_t)(e - (uint64_t)bi * L);
-        reinterpret_cast<T *>(stage + (uint64_t)bi * stage_bytes)[oi] = in[g0 + e];
     }
 }
 

@@ -25,6 +25,7 @@ struct LaunchArgs {
     uint64_t n_offsets;    // entries available in offsets
     uint64_t n_blocks, n_tiles;
     uint32_t nt;             // compression: threads per CTA (128 or 256)
+    uint32_t tb;             // compression: blocks per tile; decompression: blocks per warp tile
     bool orbit;              // advanced: the series table is in the workspace
     uint32_t *orb_flags;
     uint64_t *orb_hdr;
