@@ -184,6 +184,21 @@ def dist_info():
     return world, rank, local
 
 
+def max_over_ranks(ms, dist, device):
+    """The slowest rank's time (every rank returns it)."""
+    import torch
+
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_scaling_value(world, raw_bytes, steps, total_ms):
+    """Whole-job GB/s: every rank compresses and decompresses its own copy of
+    the workload, so the job moves world x raw bytes per step."""
+    return world * raw_bytes * steps / (total_ms / 1e3) / GB
+
+
 # ------------------------------------------------------------------ oracle leg
 
 
@@ -354,12 +369,10 @@ def main():
     td = [ev[k][1].elapsed_time(ev[k][2]) for k in range(args.steps)]
     total_ms = ev[0][0].elapsed_time(ev[-1][2])
     if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+        total_ms = max_over_ranks(total_ms, dist, dev)
     tc_ms = sum(tc) / len(tc)
     td_ms = sum(td) / len(td)
-    value = world * raw_bytes * args.steps / (total_ms / 1e3) / GB
+    value = weak_scaling_value(world, raw_bytes, args.steps, total_ms)
     comp_gbs = raw_bytes / (tc_ms / 1e3) / GB
     dec_gbs = raw_bytes / (td_ms / 1e3) / GB
     peak, peak_kind = peaks()

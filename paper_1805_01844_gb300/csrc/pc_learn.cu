@@ -11,6 +11,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <cstddef>
 #include <cstdint>
 
 #include "pc.h"
@@ -377,15 +378,19 @@ pc_status pc_segments_features(const pc_segments_info *info, const void *d_plan,
     return cudaGetLastError() == cudaSuccess ? PC_OK : PC_ERR_CUDA;
 }
 
+// A grid of chunks of NB rows, at most as many CTAs as are resident at once
+// (the forward pass needs no gradient arrays, so more of its CTAs fit).
 static pc_status mlp_grid(const void *kern, uint32_t smem, uint64_t n, unsigned &grid)
 {
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return PC_ERR_CUDA;
-    int dev = 0, sms = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev))
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kMlpThreads, smem) != cudaSuccess)
         return PC_ERR_CUDA;
+    if (per_sm < 1) return PC_ERR_UNSUPPORTED;
     uint64_t g = ceil_div(n, NB);
-    if (g > (uint64_t)sms * 2) g = (uint64_t)sms * 2;
+    if (g > (uint64_t)sms * per_sm) g = (uint64_t)sms * per_sm;
     grid = (unsigned)(g ? g : 1);
     return PC_OK;
 }
@@ -396,7 +401,7 @@ pc_status pc_mlp_forward(const void *d_weights, const float *d_x, uint64_t n, fl
     if (!d_weights || (!d_x && n)) return PC_ERR_INVALID_ARG;
     if (n == 0) return PC_OK;
     unsigned grid;
-    const uint32_t smem = sizeof(MlpSmem);
+    const uint32_t smem = (uint32_t)offsetof(MlpSmem, D2);  // the forward pass stops before dH2
     pc_status st = mlp_grid(reinterpret_cast<const void *>(k_mlp_forward), smem, n, grid);
     if (st != PC_OK) return st;
     k_mlp_forward<<<grid, kMlpThreads, smem, static_cast<cudaStream_t>(stream)>>>(
