@@ -734,6 +734,7 @@ __device__ __forceinline__ void copy_block_out(T *dstg, const T *u, uint32_t n_b
 // Per-block decoding parameters, held by one lane each in k_decode_w.
 struct DecBlock {
     uint64_t B, Dh, MD;
+    uint64_t lim;  // basic: B^r when the last word's top p - r digits are padding, else 0 (its own lane's)
     uint32_t vmin, W, woff, p, n_b, hstar;
     Magic32 mg;
     OrbitView ov;
@@ -770,6 +771,14 @@ __device__ __forceinline__ DecBlock dec_setup(const uint8_t *in, uint64_t gb, ui
     if constexpr (VAR == PC_VARIANT_BASIC) {
         d.p = basic_p(d.B, WB);
         d.W = (n_b + d.p - 1) / d.p;
+        // the last word's digits past the block's end are padding (offset 0):
+        // with valid digits that is word < B^r, r = its digits inside the
+        // block (B^r < B^p < 2^w)
+        const uint32_t r = n_b - (d.W - 1) * d.p;
+        if (r < d.p) {
+            d.lim = 1;
+            for (uint32_t i = 0; i < r; ++i) d.lim *= d.B;
+        }
     } else {
         const uint64_t h = orbit_get<WB>(ot, (uint32_t)d.B, L, ws, limit_ns);  // B <= 65536 here
         if (h != ~0ull) {
@@ -886,9 +895,7 @@ k_decode_w(const uint8_t *__restrict__ in, uint32_t L, T *__restrict__ out, uint
                 } else if constexpr (VAR == PC_VARIANT_BASIC) {
                     const uint32_t p = k.p;
                     bad |= decode_basic_block<T, WB>(wsrc, u, u + L + kPad, 0, W, p, k.hstar, k.B, vmin, k.mg, k.Dh, k.MD);
-                    __syncwarp();
-                    if (lane == 0)
-                        for (uint32_t i = n_b; i < W * p; ++i) bad |= (uint32_t)u[i] != vmin;
+                    if (lane == b && mine.lim != 0) bad |= (uint64_t)wsrc[W - 1] >= mine.lim;  // block b's lane
                 } else {
                     const Word *src = wsrc;
                     const uint32_t hstar = k.hstar, B32 = (uint32_t)k.B;

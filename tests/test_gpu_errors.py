@@ -61,6 +61,19 @@ def test_corruptions_match_oracle(variant, w):
         "word_all_ones": s[:-(w // 8)] + b"\xff" * (w // 8),
         "first_word_all_ones": s[:payload_off] + b"\xff" * (w // 8) + s[payload_off + w // 8:],
     }
+    if variant == 0:
+        # a nonzero digit in the padding of the last block's last word, the
+        # word still below B^p (every digit valid): only the padding check
+        # rejects it
+        e = int.from_bytes(s[64 + 4 * (n_blocks - 1):64 + 4 * n_blocks], "little")
+        B = (e >> 16) + 1
+        pw = 0
+        while B ** (pw + 1) <= 2 ** w - 1:
+            pw += 1
+        last = int.from_bytes(s[-(w // 8):], "little")
+        n_last = x.size - (n_blocks - 1) * 1024
+        assert n_last % pw != 0 and last < B ** (pw - 1)
+        cases["padding_digit"] = s[:-(w // 8)] + (last + B ** (pw - 1)).to_bytes(w // 8, "little")
     for name, stream in cases.items():
         want = oracle_verdict(stream, x.size)
         got = run_decode(stream, p, x.size)
