@@ -598,99 +598,86 @@ k_decode(const uint8_t *__restrict__ in, uint32_t L, T *__restrict__ out, uint64
 }
 
 // Basic words j0 + lane + 32 k (k < NK) of one block, NK words per lane in
-// lockstep (NK independent division chains).  Digits land at u[j p + i];
-// lanes past the last word write theirs to `junk`.  Returns true if a word is
-// not the image of valid digits.
+// lockstep (NK independent division chains).  Digits land at u[j p + i]
+// (u at shared address ua; each lane walks its digits with a 32-bit shared
+// address); lanes past the last word write theirs to the junk slots at
+// junka.  Returns true if a word is not the image of valid digits.
 template <typename T, uint32_t WB, uint32_t NK>
 __device__ __forceinline__ bool decode_basic_group(const typename WordT<T, WB>::type *src /* shared */,
-                                                   uint32_t src0, T *u, T *junk, uint32_t j0, uint32_t W, uint32_t p,
-                                                   uint32_t hstar, uint64_t B, uint32_t vmin, Magic32 mg, uint64_t Dh,
-                                                   uint64_t MD)
+                                                   uint32_t src0, uint32_t ua, uint32_t junka, uint32_t j0, uint32_t W,
+                                                   uint32_t p, uint32_t hstar, uint64_t B, uint32_t vmin, Magic32 mg,
+                                                   uint64_t Dh, uint64_t MD)
 {
     using Word = typename WordT<T, WB>::type;
+    constexpr uint32_t E = sizeof(T);
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t B32 = (uint32_t)B;
     bool bad = false;
-    {
-        Word sv[NK];
-        T *d[NK];
-        bool ok[NK];
+    Word sv[NK];
+    uint32_t d[NK];  // shared address of the lane's next digit
+    bool ok[NK];
 #pragma unroll
-        for (uint32_t k = 0; k < NK; ++k) {
-            const uint32_t j = j0 + lane + 32 * k;
-            ok[k] = j < W;
-            sv[k] = ok[k] ? src[j - src0] : Word(0);  // src: the staged words from word src0 on
-            d[k] = ok[k] ? u + j * p : junk;
-        }
-        uint32_t x[NK];
-        uint32_t off = 0, rem = p;
-        if (WB == 64 && p > hstar) {
-            // split each word into pieces of h* digits (B^h* <= 2^32)
-            uint64_t hv[NK];
-#pragma unroll
-            for (uint32_t k = 0; k < NK; ++k) {
-                uint64_t lo;
-                hv[k] = divmod_inv64(sv[k], Dh, MD, lo);
-                x[k] = (uint32_t)lo;
-            }
-            for (uint32_t i = 0; i + 1 < hstar; ++i) {
-#pragma unroll
-                for (uint32_t k = 0; k < NK; ++k) {
-                    const uint32_t q = magic_div(x[k], mg);
-                    d[k][i] = (T)(x[k] - q * B32 + vmin);
-                    x[k] = q;
-                }
-            }
-#pragma unroll
-            for (uint32_t k = 0; k < NK; ++k) d[k][hstar - 1] = (T)(x[k] + vmin);
-            off = hstar;
-            rem = p - hstar;
-            if (rem > hstar) {  // p = 2 h* + 1: a middle piece of h* digits
-#pragma unroll
-                for (uint32_t k = 0; k < NK; ++k) {
-                    uint64_t lo;
-                    hv[k] = divmod_inv64(hv[k], Dh, MD, lo);
-                    x[k] = (uint32_t)lo;
-                }
-                for (uint32_t i = 0; i + 1 < hstar; ++i) {
-#pragma unroll
-                    for (uint32_t k = 0; k < NK; ++k) {
-                        const uint32_t q = magic_div(x[k], mg);
-                        d[k][off + i] = (T)(x[k] - q * B32 + vmin);
-                        x[k] = q;
-                    }
-                }
-#pragma unroll
-                for (uint32_t k = 0; k < NK; ++k) d[k][off + hstar - 1] = (T)(x[k] + vmin);
-                off += hstar;
-                rem -= hstar;
-            }
-#pragma unroll
-            for (uint32_t k = 0; k < NK; ++k) {
-                bad |= ok[k] && (hv[k] >> 32) != 0;
-                x[k] = (uint32_t)hv[k];
-            }
-        } else {
-#pragma unroll
-            for (uint32_t k = 0; k < NK; ++k) {
-                if (WB == 64) bad |= ok[k] && ((uint64_t)sv[k] >> 32) != 0;
-                x[k] = (uint32_t)sv[k];
-            }
-        }
-        for (uint32_t i = 0; i + 1 < rem; ++i) {
+    for (uint32_t k = 0; k < NK; ++k) {
+        const uint32_t j = j0 + lane + 32 * k;
+        ok[k] = j < W;
+        sv[k] = ok[k] ? src[j - src0] : Word(0);  // src: the staged words from word src0 on
+        d[k] = ok[k] ? ua + j * p * E : junka;
+    }
+    // h digits of each x[k], least significant first
+    auto piece = [&](uint32_t (&x)[NK], uint32_t h) {
+        for (uint32_t i = 0; i + 1 < h; ++i) {
 #pragma unroll
             for (uint32_t k = 0; k < NK; ++k) {
                 const uint32_t q = magic_div(x[k], mg);
-                d[k][off + i] = (T)(x[k] - q * B32 + vmin);
+                st_shared<T>(d[k], x[k] - q * B32 + vmin);
+                d[k] += E;
                 x[k] = q;
             }
         }
 #pragma unroll
         for (uint32_t k = 0; k < NK; ++k) {
-            d[k][off + rem - 1] = (T)(x[k] + vmin);
-            bad |= ok[k] && x[k] >= B;  // the top digit
+            st_shared<T>(d[k], x[k] + vmin);
+            d[k] += E;
+        }
+    };
+    uint32_t x[NK];
+    uint32_t rem = p;
+    if (WB == 64 && p > hstar) {
+        // split each word into pieces of h* digits (B^h* <= 2^32)
+        uint64_t hv[NK];
+#pragma unroll
+        for (uint32_t k = 0; k < NK; ++k) {
+            uint64_t lo;
+            hv[k] = divmod_inv64(sv[k], Dh, MD, lo);
+            x[k] = (uint32_t)lo;
+        }
+        piece(x, hstar);
+        rem = p - hstar;
+        if (rem > hstar) {  // p = 2 h* + 1: a middle piece of h* digits
+#pragma unroll
+            for (uint32_t k = 0; k < NK; ++k) {
+                uint64_t lo;
+                hv[k] = divmod_inv64(hv[k], Dh, MD, lo);
+                x[k] = (uint32_t)lo;
+            }
+            piece(x, hstar);
+            rem -= hstar;
+        }
+#pragma unroll
+        for (uint32_t k = 0; k < NK; ++k) {
+            bad |= ok[k] && (hv[k] >> 32) != 0;
+            x[k] = (uint32_t)hv[k];
+        }
+    } else {
+#pragma unroll
+        for (uint32_t k = 0; k < NK; ++k) {
+            if (WB == 64) bad |= ok[k] && ((uint64_t)sv[k] >> 32) != 0;
+            x[k] = (uint32_t)sv[k];
         }
     }
+    piece(x, rem);
+#pragma unroll
+    for (uint32_t k = 0; k < NK; ++k) bad |= ok[k] && x[k] >= B;  // the top digit (piece leaves it in x)
     return bad;
 }
 
@@ -705,11 +692,12 @@ __device__ __forceinline__ bool decode_basic_block(const typename WordT<T, WB>::
                                                    uint64_t B, uint32_t vmin, Magic32 mg, uint64_t Dh, uint64_t MD)
 {
     bool bad = false;
+    const uint32_t ua = (uint32_t)__cvta_generic_to_shared(u), junka = (uint32_t)__cvta_generic_to_shared(junk);
     uint32_t j0 = jb;
     for (; j0 + 128 <= je; j0 += 128)
-        bad |= decode_basic_group<T, WB, 4>(src, jb, u, junk, j0, je, p, hstar, B, vmin, mg, Dh, MD);
+        bad |= decode_basic_group<T, WB, 4>(src, jb, ua, junka, j0, je, p, hstar, B, vmin, mg, Dh, MD);
     for (; j0 < je; j0 += 32)
-        bad |= decode_basic_group<T, WB, 1>(src, jb, u, junk, j0, je, p, hstar, B, vmin, mg, Dh, MD);
+        bad |= decode_basic_group<T, WB, 1>(src, jb, ua, junka, j0, je, p, hstar, B, vmin, mg, Dh, MD);
     return bad;
 }
 

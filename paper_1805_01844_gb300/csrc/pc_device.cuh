@@ -53,6 +53,20 @@ __device__ __forceinline__ void cp_async_small(void *smem, const void *gmem)
     asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(s), "l"(gmem), "n"(BYTES) : "memory");
 }
 
+// Store of one T (16 or 32 bits, the low bits of v) at a 32-bit shared address.
+template <typename T>
+__device__ __forceinline__ void st_shared(uint32_t a, uint32_t v);
+template <>
+__device__ __forceinline__ void st_shared<uint16_t>(uint32_t a, uint32_t v)
+{
+    asm volatile("st.shared.u16 [%0], %1;" ::"r"(a), "h"((unsigned short)v) : "memory");
+}
+template <>
+__device__ __forceinline__ void st_shared<uint32_t>(uint32_t a, uint32_t v)
+{
+    asm volatile("st.shared.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+
 // Bulk (TMA engine) copies global -> shared completing on an mbarrier.
 __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
 {
