@@ -864,7 +864,14 @@ k_decode_w(const uint8_t *__restrict__ in, uint32_t L, T *__restrict__ out, uint
                 const uint32_t ob = __shfl_sync(0xFFFFFFFFu, mine.woff, (int)b);
                 const Word *g = payload + base + ob;
                 Word *dstw = wbuf + (b & 1u) * cw;
-                for (uint32_t j = lane; j < Wb; j += 32) cp_async_small<sizeof(Word)>(dstw + j, g + j);
+                uint32_t j = lane;
+                for (; j + 96 < Wb; j += 128) {  // four words per lane per step
+                    cp_async_small<sizeof(Word)>(dstw + j, g + j);
+                    cp_async_small<sizeof(Word)>(dstw + j + 32, g + j + 32);
+                    cp_async_small<sizeof(Word)>(dstw + j + 64, g + j + 64);
+                    cp_async_small<sizeof(Word)>(dstw + j + 96, g + j + 96);
+                }
+                for (; j < Wb; j += 32) cp_async_small<sizeof(Word)>(dstw + j, g + j);
                 cp_async_commit();
             };
             prefetch(0);
