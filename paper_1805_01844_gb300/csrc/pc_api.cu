@@ -172,7 +172,8 @@ pc_status pc_decompress(const void *d_in, uint64_t in_bytes, const pc_params *pa
     a.cap = out_capacity_samples;
     a.out_count = d_n_samples;
     // warp tiles of the decoder, from the largest stream the call accepts
-    a.tb = small_stream_tb(ceil_div(out_capacity_samples, params->block_len), 32);
+    a.tb = small_stream_tb(ceil_div(out_capacity_samples, params->block_len),
+                           dec_tile_cap(params->variant, params->dtype_bits, params->word_bits, params->block_len));
     fill_workspace(a, d_workspace, lay);
     a.limit_ns = kWaitLimitNs;
     a.stream = static_cast<cudaStream_t>(stream);

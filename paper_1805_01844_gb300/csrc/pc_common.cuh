@@ -224,6 +224,84 @@ PCX_HD uint32_t small_stream_tb(uint64_t n_blocks, uint32_t tb)
     return tb;
 }
 
+// Warp-granular decoding: shared memory of one warp (one block's samples
+// with padding and a junk area, two buffers of packed words) and the warps
+// per CTA that fit a 200 KB budget (1 to 4).
+constexpr uint32_t kDecChunk = 256;  // packed words staged at a time per warp (a multiple of 128)
+
+// Long blocks (two word buffers of a whole block above 8 KB) are decoded in
+// chunks of kDecChunk words, so that a warp's shared memory stays small and
+// enough warps share an SM; shorter ones stage a whole block's words.
+PCX_HD bool dec_chunked(uint32_t variant, uint32_t d, uint32_t w, uint32_t L)
+{
+    return 2 * words_bound(variant, d, w, L) * (w / 8) > 8192;
+}
+
+PCX_HD uint32_t dec_chunk_words(uint32_t variant, uint32_t d, uint32_t w, uint32_t L)
+{
+    return dec_chunked(variant, d, w, L) ? kDecChunk : (uint32_t)words_bound(variant, d, w, L);
+}
+
+// The warp decoder's per-block records (the decoder's DecBlock): basic
+// variant, advanced variant.
+constexpr uint32_t kDecRecBasic = 80;
+constexpr uint32_t kDecRecAdvanced = 112;
+constexpr uint32_t kDecWarpsMax = 4;  // warps per CTA of the warp decoder
+// CTAs of the warp decoder per SM that its register allocation allows
+#ifndef PCX_DECODE_MIN_CTAS
+#define PCX_DECODE_MIN_CTAS 5
+#endif
+constexpr uint32_t kSmemPerSm = 228u * 1024u;  // shared memory per SM, and the part each CTA reserves
+constexpr uint32_t kSmemReservedPerCta = 1024u;
+
+PCX_HD uint32_t dec_words_bytes(uint32_t variant, uint32_t d, uint32_t w, uint32_t L)
+{
+    return (uint32_t)round_up(2 * (uint64_t)dec_chunk_words(variant, d, w, L) * (w / 8), 16);
+}
+
+// Shared memory of one warp of the warp decoder: a block's sample slot, two
+// word buffers, the records of a tile of up to `recs` blocks.
+PCX_HD uint32_t decw_warp_bytes_for(uint32_t variant, uint32_t d, uint32_t w, uint32_t L, uint32_t recs)
+{
+    const uint64_t slot = round_up((uint64_t)(L + 2 * kPad) * (d / 8), 16);
+    const uint64_t rec = (uint64_t)recs * (variant == PC_VARIANT_BASIC ? kDecRecBasic : kDecRecAdvanced);
+    return (uint32_t)(slot + dec_words_bytes(variant, d, w, L) + rec);
+}
+
+// Warps per CTA that fit a 200 KB budget (1 to 4; 0: does not fit, which no
+// parameters reach) and the warps per SM that result.
+PCX_HD uint32_t decw_warps_for(uint32_t variant, uint32_t d, uint32_t w, uint32_t L, uint32_t recs)
+{
+    uint32_t k = (200u * 1024u) / decw_warp_bytes_for(variant, d, w, L, recs);
+    return k > kDecWarpsMax ? kDecWarpsMax : k;
+}
+
+PCX_HD uint32_t decw_warps_per_sm(uint32_t variant, uint32_t d, uint32_t w, uint32_t L, uint32_t recs)
+{
+    const uint32_t k = decw_warps_for(variant, d, w, L, recs);
+    if (k == 0) return 0;
+    uint32_t ctas = kSmemPerSm / (k * decw_warp_bytes_for(variant, d, w, L, recs) + kSmemReservedPerCta);
+    if (ctas > PCX_DECODE_MIN_CTAS) ctas = PCX_DECODE_MIN_CTAS;
+    return ctas * k;
+}
+
+// Blocks per warp tile of the warp decoder: 32 (one lane each), or 16 where
+// the records of 32 blocks would cost resident warps.
+PCX_HD uint32_t dec_tile_cap(uint32_t variant, uint32_t d, uint32_t w, uint32_t L)
+{
+    return decw_warps_per_sm(variant, d, w, L, 32) >= decw_warps_per_sm(variant, d, w, L, 16) ? 32u : 16u;
+}
+
+PCX_HD uint32_t decw_warp_bytes(uint32_t variant, uint32_t d, uint32_t w, uint32_t L)
+{
+    return decw_warp_bytes_for(variant, d, w, L, dec_tile_cap(variant, d, w, L));
+}
+
+PCX_HD uint32_t decw_warps(uint32_t variant, uint32_t d, uint32_t w, uint32_t L)
+{
+    return decw_warps_for(variant, d, w, L, dec_tile_cap(variant, d, w, L));
+}
+
 // Workspace layout: the header; the series table (advanced with the table:
 // flags, headers, slots) at fixed offsets; the look-back words; the
 // decoding-tile offsets plus the total (decompression).  The table depends on
@@ -255,7 +333,7 @@ PCX_HD WsLayout ws_layout(uint32_t variant, uint32_t d, uint32_t w, uint32_t L, 
     const uint64_t ctiles = ceil_div(n_blocks, small_stream_tb(n_blocks, ctb));
     const uint64_t otiles = ceil_div(n_blocks, kOffsetTileBlocks);
     const uint64_t dtiles_cta = ceil_div(n_blocks, tile_cfg(kKernelDecode, variant, d, w, L, lay.orbit).tb);
-    const uint64_t dtiles_warp = ceil_div(n_blocks, small_stream_tb(n_blocks, 32));
+    const uint64_t dtiles_warp = ceil_div(n_blocks, small_stream_tb(n_blocks, dec_tile_cap(variant, d, w, L)));
     const uint64_t dtiles = dtiles_cta > dtiles_warp ? dtiles_cta : dtiles_warp;
     lay.n_status = (ctiles > otiles ? ctiles : otiles) + 1;  // + 1: the self-test uses two words
     lay.n_offsets = dtiles + 1;
@@ -266,38 +344,6 @@ PCX_HD WsLayout ws_layout(uint32_t variant, uint32_t d, uint32_t w, uint32_t L, 
     lay.off_offsets = lay.off_status + 8 * lay.n_status;
     lay.bytes = round_up(lay.off_offsets + 8 * lay.n_offsets, 16);
     return lay;
-}
-
-// Warp-granular decoding: shared memory of one warp (one block's samples
-// with padding and a junk area, two buffers of packed words) and the warps
-// per CTA that fit a 200 KB budget (1 to 4).
-constexpr uint32_t kDecChunk = 256;  // packed words staged at a time per warp (a multiple of 128)
-
-// Long blocks (two word buffers of a whole block above 8 KB) are decoded in
-// chunks of kDecChunk words, so that a warp's shared memory stays small and
-// enough warps share an SM; shorter ones stage a whole block's words.
-PCX_HD bool dec_chunked(uint32_t variant, uint32_t d, uint32_t w, uint32_t L)
-{
-    return 2 * words_bound(variant, d, w, L) * (w / 8) > 8192;
-}
-
-PCX_HD uint32_t dec_chunk_words(uint32_t variant, uint32_t d, uint32_t w, uint32_t L)
-{
-    return dec_chunked(variant, d, w, L) ? kDecChunk : (uint32_t)words_bound(variant, d, w, L);
-}
-
-PCX_HD uint32_t decw_warp_bytes(uint32_t variant, uint32_t d, uint32_t w, uint32_t L)
-{
-    const uint64_t slot = round_up((uint64_t)(L + 2 * kPad) * (d / 8), 16);
-    const uint64_t words = round_up(2 * (uint64_t)dec_chunk_words(variant, d, w, L) * (w / 8), 16);
-    return (uint32_t)(slot + words);
-}
-
-PCX_HD uint32_t decw_warps(uint32_t variant, uint32_t d, uint32_t w, uint32_t L)
-{
-    uint32_t k = (200u * 1024u) / decw_warp_bytes(variant, d, w, L);
-    if (k > 4) k = 4;
-    return k;  // 0: does not fit (no parameters reach this)
 }
 
 PCX_HD uint64_t table_bytes(uint64_t n_blocks, uint32_t d)

@@ -719,14 +719,31 @@ __device__ __forceinline__ void copy_block_out(T *dstg, const T *u, uint32_t n_b
     }
 }
 
-// Per-block decoding parameters, held by one lane each in k_decode_w.
-struct DecBlock {
+// Per-block decoding parameters.  In k_decode_w lane b sets up block b of its
+// warp's tile and stores the record in the warp's shared record array: the
+// first kDecRecBasic bytes for the basic variant, all of it (with the series
+// view) for the advanced one.
+struct alignas(16) DecBlock {
     uint64_t B, Dh, MD;
-    uint64_t lim;  // basic: B^r when the last word's top p - r digits are padding, else 0 (its own lane's)
+    uint64_t lim;  // basic: B^r when the last word's top p - r digits are padding, else 0
     uint32_t vmin, W, woff, p, n_b, hstar;
     Magic32 mg;
+    uint32_t pad_[3];
     OrbitView ov;
 };
+static_assert(offsetof(DecBlock, ov) == kDecRecBasic && sizeof(DecBlock) == kDecRecAdvanced,
+              "decoder record sizes");
+
+// Lane `lane`'s record into the array (16-byte stores), for lane < nblk.
+template <uint32_t VAR>
+__device__ __forceinline__ void store_rec(uint8_t *recs, const DecBlock &d, uint32_t lane)
+{
+    constexpr uint32_t NV = (VAR == PC_VARIANT_BASIC ? kDecRecBasic : kDecRecAdvanced) / 16;
+    const uint4 *v = reinterpret_cast<const uint4 *>(&d);
+    uint4 *dst = reinterpret_cast<uint4 *>(recs + lane * (NV * 16));
+#pragma unroll
+    for (uint32_t i = 0; i < NV; ++i) dst[i] = v[i];
+}
 
 template <uint32_t WB, uint32_t VAR, bool ORB>
 __device__ __forceinline__ DecBlock dec_setup(const uint8_t *in, uint64_t gb, uint32_t n_b, uint32_t L,
@@ -777,46 +794,14 @@ __device__ __forceinline__ DecBlock dec_setup(const uint8_t *in, uint64_t gb, ui
     return d;
 }
 
-__device__ __forceinline__ DecBlock shfl_block(const DecBlock &x, int src)
-{
-    DecBlock d;
-    const unsigned F = 0xFFFFFFFFu;
-    d.B = __shfl_sync(F, x.B, src);
-    d.Dh = __shfl_sync(F, x.Dh, src);
-    d.MD = __shfl_sync(F, x.MD, src);
-    d.vmin = __shfl_sync(F, x.vmin, src);
-    d.W = __shfl_sync(F, x.W, src);
-    d.woff = __shfl_sync(F, x.woff, src);
-    d.p = __shfl_sync(F, x.p, src);
-    d.n_b = __shfl_sync(F, x.n_b, src);
-    d.hstar = __shfl_sync(F, x.hstar, src);
-    d.mg.m = __shfl_sync(F, x.mg.m, src);
-    d.mg.a = __shfl_sync(F, x.mg.a, src);
-    d.mg.s = __shfl_sync(F, x.mg.s, src);
-    d.ov.off = __shfl_sync(F, x.ov.off, src);
-    d.ov.Q = __shfl_sync(F, x.ov.Q, src);
-    d.ov.P = __shfl_sync(F, x.ov.P, src);
-    d.ov.SQ = __shfl_sync(F, x.ov.SQ, src);
-    d.ov.G = __shfl_sync(F, x.ov.G, src);
-    d.ov.mgP.m = __shfl_sync(F, x.ov.mgP.m, src);
-    d.ov.mgP.a = __shfl_sync(F, x.ov.mgP.a, src);
-    d.ov.mgP.s = __shfl_sync(F, x.ov.mgP.s, src);
-    return d;
-}
-
-constexpr uint32_t kDecWarpsMax = 4;     // warps per CTA of k_decode_w (decw_warps)
-// blocks per warp tile: at most 32 (one lane each), fewer for a short stream (small_stream_tb)
-
 // Warp-granular decoding (basic, and advanced with the series table on 16-bit
-// data): no shared barrier at all.  A warp owns 32 consecutive blocks; lane b
-// sets up block b (table entry, word count, division constants, series view),
-// then the warp decodes the blocks one by one into its own shared-memory slot
-// and stores each block's samples with 16-byte streaming stores.
-// 5 CTAs of 4 warps per SM: registers capped at 102 (the unconstrained
-// kernel takes ~127, which allows only 4)
-#ifndef PCX_DECODE_MIN_CTAS
-#define PCX_DECODE_MIN_CTAS 5
-#endif
+// data): no shared barrier at all.  A warp owns a tile of consecutive blocks
+// (up to dec_tile_cap, fewer for a short stream); lane b sets up block b
+// (table entry, word count, division constants, series view) and stores its
+// record in the warp's shared record array, then the warp decodes the blocks
+// one by one into its own shared-memory slot and stores each block's samples
+// with 16-byte streaming stores.  5 CTAs of 4 warps per SM: registers capped
+// at 102 (PCX_DECODE_MIN_CTAS).
 template <typename T, uint32_t WB, uint32_t VAR, bool ORB, bool CHUNKED>
 __global__ void __launch_bounds__(kDecWarpsMax * 32, PCX_DECODE_MIN_CTAS)
 k_decode_w(const uint8_t *__restrict__ in, uint32_t L, T *__restrict__ out, uint64_t *__restrict__ n_out,
@@ -836,6 +821,10 @@ k_decode_w(const uint8_t *__restrict__ in, uint32_t L, T *__restrict__ out, uint
     const uint32_t nwarps = blockDim.x >> 5;
     T *u = reinterpret_cast<T *>(smem + warp * warp_bytes);
     Word *wbuf = reinterpret_cast<Word *>(smem + warp * warp_bytes + slot_bytes);
+    // then the tile's block records
+    constexpr uint32_t kRec = VAR == PC_VARIANT_BASIC ? kDecRecBasic : kDecRecAdvanced;
+    uint8_t *recs = smem + warp * warp_bytes + slot_bytes + dec_words_bytes(VAR, D, WB, L);
+    auto rec = [&](uint32_t b) -> const DecBlock & { return *reinterpret_cast<const DecBlock *>(recs + b * kRec); };
 
     if (*reinterpret_cast<volatile uint32_t *>(&ws->status) != PC_OK) return;
     const uint64_t *h64 = reinterpret_cast<const uint64_t *>(in);
@@ -849,19 +838,24 @@ k_decode_w(const uint8_t *__restrict__ in, uint32_t L, T *__restrict__ out, uint
     for (uint64_t wt = gw0; wt < n_wt; wt += nw) {
         const uint64_t blk0 = wt * wtb;
         const uint32_t nblk = (uint32_t)umin64(wtb, n_blocks - blk0);
-        DecBlock mine{};
-        if (lane < nblk) {
-            const uint64_t gb = blk0 + lane;
-            const uint32_t n_b = (uint32_t)umin64(L, n - gb * L);
-            mine = dec_setup<WB, VAR, ORB>(in, gb, n_b, L, ot, ws, limit_ns, D);
+        uint32_t nz;  // lanes (blocks) with words
+        {
+            DecBlock mine{};
+            if (lane < nblk) {
+                const uint64_t gb = blk0 + lane;
+                const uint32_t n_b = (uint32_t)umin64(L, n - gb * L);
+                mine = dec_setup<WB, VAR, ORB>(in, gb, n_b, L, ot, ws, limit_ns, D);
+            }
+            const uint32_t incl = warp_incl_scan_u32(mine.W);
+            mine.woff = incl - mine.W;
+            nz = __ballot_sync(0xFFFFFFFFu, lane < nblk && mine.W > 0);
+            if (lane < nblk) store_rec<VAR>(recs, mine, lane);
+            __syncwarp();
         }
-        const uint32_t incl = warp_incl_scan_u32(mine.W);
-        mine.woff = incl - mine.W;
         if constexpr (!CHUNKED) {
             const uint64_t base = offsets[wt];
             auto prefetch = [&](uint32_t b) {  // block b's words into buffer b & 1
-                const uint32_t Wb = __shfl_sync(0xFFFFFFFFu, mine.W, (int)b);
-                const uint32_t ob = __shfl_sync(0xFFFFFFFFu, mine.woff, (int)b);
+                const uint32_t Wb = rec(b).W, ob = rec(b).woff;
                 const Word *g = payload + base + ob;
                 Word *dstw = wbuf + (b & 1u) * cw;
                 uint32_t j = lane;
@@ -881,7 +875,7 @@ k_decode_w(const uint8_t *__restrict__ in, uint32_t L, T *__restrict__ out, uint
                 else cp_async_commit();
                 cp_async_wait<1>();
                 __syncwarp();
-                const DecBlock k = shfl_block(mine, (int)b);
+                const DecBlock &k = rec(b);
                 const uint64_t gb = blk0 + b;
                 const uint32_t vmin = k.vmin, W = k.W, n_b = k.n_b;
                 const Word *wsrc = wbuf + (b & 1u) * cw;
@@ -890,7 +884,7 @@ k_decode_w(const uint8_t *__restrict__ in, uint32_t L, T *__restrict__ out, uint
                 } else if constexpr (VAR == PC_VARIANT_BASIC) {
                     const uint32_t p = k.p;
                     bad |= decode_basic_block<T, WB>(wsrc, u, u + L + kPad, 0, W, p, k.hstar, k.B, vmin, k.mg, k.Dh, k.MD);
-                    if (lane == b && mine.lim != 0) bad |= (uint64_t)wsrc[W - 1] >= mine.lim;  // block b's lane
+                    if (k.lim != 0) bad |= (uint64_t)wsrc[W - 1] >= k.lim;
                 } else {
                     const Word *src = wsrc;
                     const uint32_t hstar = k.hstar, B32 = (uint32_t)k.B;
@@ -965,10 +959,8 @@ k_decode_w(const uint8_t *__restrict__ in, uint32_t L, T *__restrict__ out, uint
             }
         } else {
             const uint64_t base = offsets[wt];
-            const uint32_t nz = __ballot_sync(0xFFFFFFFFu, lane < nblk && mine.W > 0);  // blocks with words
             auto prefetch = [&](uint32_t b, uint32_t c, uint32_t slot) {  // chunk c of block b into a buffer
-                const uint32_t Wb = __shfl_sync(0xFFFFFFFFu, mine.W, (int)b);
-                const uint32_t ob = __shfl_sync(0xFFFFFFFFu, mine.woff, (int)b);
+                const uint32_t Wb = rec(b).W, ob = rec(b).woff;
                 const uint32_t j0 = c * cw, cnt = min(cw, Wb - j0);
                 const Word *g = payload + base + ob + j0;
                 Word *dstw = wbuf + slot * cw;
@@ -979,7 +971,7 @@ k_decode_w(const uint8_t *__restrict__ in, uint32_t L, T *__restrict__ out, uint
             if (nz) prefetch((uint32_t)__ffs(nz) - 1u, 0, 0);
 
             for (uint32_t b = 0; b < nblk; ++b) {
-                const DecBlock k = shfl_block(mine, (int)b);
+                const DecBlock &k = rec(b);
                 const uint64_t gb = blk0 + b;
                 const uint32_t vmin = k.vmin, W = k.W, n_b = k.n_b;
                 if (W == 0) {
