@@ -234,13 +234,9 @@ __device__ void seg_warp(const T *__restrict__ in, uint32_t n, uint32_t L, uint8
         const uint32_t n_b = min(L, n - lane * L);
         if (B > 1) {
             if constexpr (VAR == PC_VARIANT_BASIC) {
-                p = basic_p(B, WB);
+                uint64_t geo;
+                p = basic_p_geo(B, WB, geo);
                 W = (n_b + p - 1) / p;
-                uint64_t geo = 0, pw = 1;
-                for (uint32_t i = 0; i < p; ++i) {
-                    geo += pw;
-                    pw *= B;
-                }
                 K = geo * vmin;
             } else {
                 const uint64_t h = orbit_get<WB>(ot, (uint32_t)B, L, ws, limit_ns);  // B <= 65536 for 16-bit data

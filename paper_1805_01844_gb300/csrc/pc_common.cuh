@@ -72,32 +72,56 @@ PCX_HD uint64_t mulhi64(uint64_t a, uint64_t b)
 #endif
 }
 
-// Eq. 1 (Sec. 3.1) in integer form: the largest p with B^p <= 2^w - 1.
-// B >= 2, B <= 2^32, w in {32, 64}.
+// Eq. 1 (Sec. 3.1) in integer form: the largest p with B^p <= 2^w - 1,
+// together with 1 + B + ... + B^(p-1) (mod 2^64), in one pass of p
+// multiplications.  B >= 2, B <= 2^32, w in {32, 64}.  Below 2^32 each step
+// is a 64 x 32-bit product held as 96 bits (two 32-bit multiplies), whose
+// top 32 bits say whether B^(p+1) still fits 64 bits.
+PCX_HD uint32_t eq1_p_geo(uint64_t B, uint32_t w, uint64_t &geo)
+{
+    uint64_t x = 1, g = 0;  // x = B^p, g = 1 + ... + B^(p-1)
+    uint32_t p = 0;
+    if (B <= 0xFFFFFFFFull) {
+        const uint32_t b = (uint32_t)B;
+        for (;;) {
+            const uint64_t lo = (uint64_t)(uint32_t)x * b;
+            const uint64_t mid = (x >> 32) * b + (lo >> 32);  // < 2^64
+            const uint64_t y = (mid << 32) | (uint32_t)lo;  // x b mod 2^64
+            if (w == 64 ? (mid >> 32) != 0 : y > 0xFFFFFFFFull) break;
+            g += x;
+            x = y;
+            ++p;
+        }
+    } else if (w == 64) {  // B = 2^32: B^1 fits, B^2 = 2^64 does not
+        g = 1;
+        p = 1;
+    }
+    geo = g;
+    return p;
+}
+
 PCX_HD uint32_t eq1_p(uint64_t B, uint32_t w)
 {
-    uint64_t x = 1;
-    uint32_t p = 0;
-    for (;;) {
-        if (w == 64) {
-            if (mulhi64(x, B) != 0) break;
-            x *= B;
-        } else {
-            uint64_t y = x * B;  // x < 2^32, B <= 2^32: no overflow
-            if (y > 0xFFFFFFFFull) break;
-            x = y;
-        }
-        ++p;
+    uint64_t g;
+    return eq1_p_geo(B, w, g);
+}
+
+// Digits per word of the basic variant: Eq. 1 clamped to >= 1 (B = 2^32 with
+// 32-bit words stores one offset per word), and its geometric sum.
+PCX_HD uint32_t basic_p_geo(uint64_t B, uint32_t w, uint64_t &geo)
+{
+    const uint32_t p = eq1_p_geo(B, w, geo);
+    if (p == 0) {
+        geo = 1;
+        return 1u;
     }
     return p;
 }
 
-// Digits per word of the basic variant: Eq. 1 clamped to >= 1 (B = 2^32 with
-// 32-bit words stores one offset per word).
 PCX_HD uint32_t basic_p(uint64_t B, uint32_t w)
 {
-    uint32_t p = eq1_p(B, w);
-    return p == 0 ? 1u : p;
+    uint64_t g;
+    return basic_p_geo(B, w, g);
 }
 
 // Largest word count of a block of n_b samples over every base B in

@@ -408,14 +408,10 @@ __device__ void compress_tile(const StreamArgs &sa, uint64_t tile, uint8_t *smem
             const uint32_t n_b = (uint32_t)umin64(L, cnt - (uint64_t)lane * L);
             if (B > 1) {
                 if constexpr (VAR == PC_VARIANT_BASIC) {
-                    const uint32_t p = basic_p(B, WB);
+                    uint64_t geo;  // 1 + B + ... + B^(p-1), mod 2^64
+                    const uint32_t p = basic_p_geo(B, WB, geo);
                     bv.p[lane] = p;
                     W = (n_b + p - 1) / p;
-                    uint64_t geo = 0, pw = 1;  // 1 + B + ... + B^(p-1), mod 2^64
-                    for (uint32_t i = 0; i < p; ++i) {
-                        geo += pw;
-                        pw *= B;
-                    }
                     bv.K[lane] = geo * bv.vmin[lane];
                 } else if (ORB && B <= kOrbitMaxB) {
                     // the series from the table: O(1) per word

@@ -222,3 +222,89 @@ int main() {
     subprocess.check_call(["g++", "-std=c++17", "-O2", "-I" + os.path.join(ROOT, "include"),
                            "-I" + os.path.join(ROOT, "paper_1805_01844_gb300", "csrc"), str(src), "-o", str(exe)])
     assert subprocess.run([str(exe)], capture_output=True, text=True).stdout.strip() == "ok"
+
+
+def test_digits_per_word_and_geometric_sum(tmp_path):
+    """Host-compiled check of Eq. 1 in integer form as the kernels compute it
+    (pc_common.cuh eq1_p_geo: p = max{p : B^p <= 2^w - 1} and
+    1 + B + ... + B^(p-1) mod 2^64 in one pass of 64 x 32-bit steps), against
+    128-bit brute force for every B in 2..2^20, the bases next to every
+    integer k-th root of 2^32 - 1 and 2^64 - 1, the powers of two, and the top
+    of the range; plus Eq. 1's values worked by hand for a few bases."""
+    import shutil
+    import subprocess
+
+    if shutil.which("g++") is None:
+        pytest.skip("no host C++ compiler")
+    src = tmp_path / "eq1.cpp"
+    src.write_text(r'''
+#include <cstdio>
+#include <cstdint>
+#include "pc_common.cuh"
+using namespace pcx;
+typedef unsigned __int128 u128;
+static uint32_t brute_p(uint64_t B, uint32_t w) {
+  const u128 C = w == 64 ? (u128)~0ull : (u128)0xFFFFFFFFull;
+  u128 x = 1; uint32_t p = 0;
+  while (x * B <= C) { x *= B; ++p; }
+  return p;
+}
+static uint64_t brute_geo(uint64_t B, uint32_t p) {
+  uint64_t g = 0, x = 1;
+  for (uint32_t i = 0; i < p; ++i) { g += x; x *= B; }
+  return g;
+}
+static int check(uint64_t B) {
+  for (uint32_t w = 32; w <= 64; w += 32) {
+    uint64_t g;
+    const uint32_t p = eq1_p_geo(B, w, g), rp = brute_p(B, w);
+    if (p != rp || g != brute_geo(B, rp)) { printf("bad B=%llu w=%u\n", (unsigned long long)B, w); return 1; }
+    const uint32_t pb = basic_p_geo(B, w, g), rb = rp ? rp : 1;
+    if (pb != rb || g != brute_geo(B, rb) || basic_p(B, w) != rb || eq1_p(B, w) != rp) {
+      printf("bad basic B=%llu w=%u\n", (unsigned long long)B, w); return 1;
+    }
+  }
+  return 0;
+}
+static uint64_t iroot(u128 c, uint32_t k) {  // largest r with r^k <= c
+  uint64_t lo = 1, hi = 1ull << 33;
+  while (lo < hi) {
+    const uint64_t mid = lo + (hi - lo + 1) / 2;
+    u128 x = 1; bool over = false;
+    for (uint32_t i = 0; i < k && !over; ++i) { if (x > c / mid) over = true; else x *= mid; }
+    if (!over && x <= c) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+int main() {
+  for (uint64_t B = 2; B <= (1ull << 20); ++B) if (check(B)) return 1;
+  for (uint32_t k = 1; k <= 64; ++k)
+    for (int c = 0; c < 2; ++c) {
+      const uint64_t r = iroot(c ? (u128)~0ull : (u128)0xFFFFFFFFull, k);
+      for (int64_t d = -2; d <= 2; ++d) {
+        const int64_t B = (int64_t)r + d;
+        if (B >= 2 && (uint64_t)B <= (1ull << 32) && check((uint64_t)B)) return 1;
+      }
+    }
+  for (uint32_t e = 1; e <= 32; ++e)
+    for (int d = -1; d <= 1; ++d) {
+      const uint64_t B = (1ull << e) + d;
+      if (B >= 2 && B <= (1ull << 32) && check(B)) return 1;
+    }
+  for (uint64_t B = 0xFFFFFFFFull - 4096; B <= (1ull << 32); ++B) if (check(B)) return 1;
+  const uint64_t Bs[] = {2, 3, 7, 9, 16, 34, 42, 256, 3850, 65535, 65536, 4294967295ull, 4294967296ull};
+  for (uint64_t B : Bs) printf("%llu %u %u\n", (unsigned long long)B, eq1_p(B, 32), eq1_p(B, 64));
+  printf("ok\n");
+  return 0;
+}
+''')
+    exe = tmp_path / "eq1"
+    subprocess.check_call(["g++", "-std=c++17", "-O2", "-I" + os.path.join(ROOT, "include"),
+                           "-I" + os.path.join(ROOT, "paper_1805_01844_gb300", "csrc"), str(src), "-o", str(exe)])
+    out = subprocess.run([str(exe)], capture_output=True, text=True).stdout.split("\n")
+    assert out[-2] == "ok", out[-5:]
+    got = {int(r.split()[0]): (int(r.split()[1]), int(r.split()[2])) for r in out[:-2]}
+    # Eq. 1 by hand: B^p <= 2^w - 1 < B^(p+1)
+    want = {2: (31, 63), 3: (20, 40), 7: (11, 22), 9: (10, 20), 16: (7, 15), 34: (6, 12), 42: (5, 11),
+            256: (3, 7), 3850: (2, 5), 65535: (2, 4), 65536: (1, 3), 4294967295: (1, 2), 4294967296: (0, 1)}
+    assert got == want
