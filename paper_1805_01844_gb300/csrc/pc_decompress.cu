@@ -42,6 +42,43 @@ __device__ __forceinline__ uint64_t divmod_inv64(uint64_t s, uint64_t D, uint64_
     return q;
 }
 
+// The same for D <= 2^31: the estimate's remainder s - q D lies in [0, 2 D),
+// below 2^32, so it is formed and corrected in 32-bit arithmetic.
+__device__ __forceinline__ uint64_t divmod_inv64_r32(uint64_t s, uint32_t D, uint64_t M, uint32_t &r)
+{
+    uint64_t q = __umul64hi(s, M);
+    uint32_t rr = (uint32_t)s - (uint32_t)q * D;
+    if (rr >= D) {
+        ++q;
+        rr -= D;
+    }
+    r = rr;
+    return q;
+}
+
+// NK words split by D = B^h* (<= 2^32): hv = s div D, x = s mod D; one
+// branch per call (D is the block's), then NK independent divisions.
+template <uint32_t NK, typename W>
+__device__ __forceinline__ void split_words(uint64_t (&hv)[NK], uint32_t (&x)[NK], const W (&s)[NK], uint64_t D,
+                                            uint64_t M)
+{
+    if (D <= 0x80000000ull) {
+#pragma unroll
+        for (uint32_t k = 0; k < NK; ++k) {
+            uint32_t lo;
+            hv[k] = divmod_inv64_r32(s[k], (uint32_t)D, M, lo);
+            x[k] = lo;
+        }
+    } else {
+#pragma unroll
+        for (uint32_t k = 0; k < NK; ++k) {
+            uint64_t lo;
+            hv[k] = divmod_inv64(s[k], D, M, lo);
+            x[k] = (uint32_t)lo;
+        }
+    }
+}
+
 // Digits of x (< B^k), least significant first, into dst[0..k), plus vmin;
 // returns the top digit (x div B^(k-1)), which is < B for a valid word.
 // K digits fully unrolled; one indexed branch per call picks K.
@@ -645,21 +682,11 @@ __device__ __forceinline__ bool decode_basic_group(const typename WordT<T, WB>::
     if (WB == 64 && p > hstar) {
         // split each word into pieces of h* digits (B^h* <= 2^32)
         uint64_t hv[NK];
-#pragma unroll
-        for (uint32_t k = 0; k < NK; ++k) {
-            uint64_t lo;
-            hv[k] = divmod_inv64(sv[k], Dh, MD, lo);
-            x[k] = (uint32_t)lo;
-        }
+        split_words<NK, Word>(hv, x, sv, Dh, MD);
         piece(x, hstar);
         rem = p - hstar;
         if (rem > hstar) {  // p = 2 h* + 1: a middle piece of h* digits
-#pragma unroll
-            for (uint32_t k = 0; k < NK; ++k) {
-                uint64_t lo;
-                hv[k] = divmod_inv64(hv[k], Dh, MD, lo);
-                x[k] = (uint32_t)lo;
-            }
+            split_words<NK, uint64_t>(hv, x, hv, Dh, MD);
             piece(x, hstar);
             rem -= hstar;
         }
