@@ -662,6 +662,7 @@ __device__ __forceinline__ bool decode_basic_group(const typename WordT<T, WB>::
     }
     // h digits of each x[k], least significant first
     auto piece = [&](uint32_t (&x)[NK], uint32_t h) {
+#pragma unroll 2  // h* = 3 for bases 257..1625: two divisions per piece, unrolled
         for (uint32_t i = 0; i + 1 < h; ++i) {
 #pragma unroll
             for (uint32_t k = 0; k < NK; ++k) {
@@ -704,7 +705,8 @@ __device__ __forceinline__ bool decode_basic_group(const typename WordT<T, WB>::
     }
     piece(x, rem);
 #pragma unroll
-    for (uint32_t k = 0; k < NK; ++k) bad |= ok[k] && x[k] >= B;  // the top digit (piece leaves it in x)
+    for (uint32_t k = 0; k < NK; ++k)  // the top digit (piece leaves it in x); B <= 2^16 for 16-bit data
+        bad |= ok[k] && (sizeof(T) == 2 ? x[k] >= B32 : x[k] >= B);
     return bad;
 }
 
