@@ -248,6 +248,7 @@ __device__ __forceinline__ void pack_basic_group(const T *u, uint32_t j0, uint32
         uint32_t a[NK];
 #pragma unroll
         for (uint32_t k = 0; k < NK; ++k) a[k] = g[k][p - 1];
+#pragma unroll 2  // 32-bit words: measured +8 % at L = 256 (none at 64 bits)
         for (int d = (int)p - 2; d >= 0; --d) {
 #pragma unroll
             for (uint32_t k = 0; k < NK; ++k) a[k] = a[k] * B32 + (uint32_t)g[k][d];
