@@ -510,6 +510,161 @@ __device__ void compress_tile(const StreamArgs &sa, uint64_t tile, uint8_t *smem
     __syncthreads();  // the stage and the per-tile arrays are free again
 }
 
+// Basic variant, long streams: one look-back tile is a pair of stage tiles
+// (2 tb blocks) staged one after the other in the same shared memory.  The
+// first half's min / max are taken, then its slots take the second half;
+// after the pair's single look-back the second half is packed where it sits
+// and each warp restages its own first-half blocks (just read, so from L2)
+// and packs them.  A look-back per 2 tb blocks instead of per tb: measured,
+// each tile's look-back waits several microseconds on its predecessors'
+// aggregates, and smaller tiles compress markedly slower.
+struct PairVars {  // per-pair arrays, in the BlockVars space of the stage
+    uint64_t B[2 * kMaxTileBlocks];
+    uint64_t K[2 * kMaxTileBlocks];
+    uint32_t vmin[2 * kMaxTileBlocks];
+    uint32_t W[2 * kMaxTileBlocks];
+    uint32_t woff[2 * kMaxTileBlocks];
+    uint32_t p[2 * kMaxTileBlocks];
+    uint64_t excl;
+    uint32_t agg;
+    uint32_t ok;
+};
+static_assert(sizeof(PairVars) <= sizeof(BlockVars), "pair arrays fit the tile arrays");
+
+template <typename T, uint32_t WB, uint32_t NT>
+__device__ void compress_tile_pair(const StreamArgs &sa, uint64_t tile, uint8_t *smem, WsHeader *ws,
+                                   uint64_t limit_ns, uint32_t &phase)
+{
+    using Word = typename WordOf<T, WB>::type;
+    constexpr uint32_t D = sizeof(T) * 8;
+    constexpr uint32_t VE = 16 / sizeof(T);
+    constexpr uint32_t NW = NT / 32;
+    const uint32_t L = sa.L;
+    const TileCfg cfg = tile_cfg(kKernelCompress, PC_VARIANT_BASIC, D, WB, L, false, NT);
+    const uint32_t H = cfg.tb;  // blocks per half
+    PairVars &pv = *reinterpret_cast<PairVars *>(smem + cfg.off_blk);
+    const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+    const T *in = static_cast<const T *>(sa.in);
+    const uint64_t n = sa.n, n_blocks = sa.n_blocks, n_tiles = sa.n_tiles;
+    const uint64_t payload_off = PC_HEADER_BYTES + table_bytes(n_blocks, D);
+    const uint64_t blk0 = tile * 2 * H;
+    const uint32_t nblk = (uint32_t)umin64(2 * H, n_blocks - blk0);
+    const uint32_t nh0 = nblk < H ? nblk : H, nh1 = nblk - nh0;
+    auto n_of = [&](uint32_t b) -> uint32_t { return (uint32_t)umin64(L, n - (blk0 + b) * L); };
+    auto slot = [&](uint32_t b) -> T * { return reinterpret_cast<T *>(smem + (uint64_t)(b % H) * cfg.stage_bytes); };
+
+    // this warp's blocks of half h into their slots: one bulk copy per block
+    // (lane 0) on the warp's mbarrier, the ragged end by plain loads
+    auto stage_half = [&](uint32_t h, uint32_t nh) {
+        __syncwarp();  // the warp's earlier accesses to its slots come first
+        if (lane == 0) {
+            uint32_t bytes = 0;
+            for (uint32_t b = warp; b < nh; b += NW) bytes += (n_of(h * H + b) / VE) * 16u;
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(&g_stage_bar[warp], bytes);
+            for (uint32_t b = warp; b < nh; b += NW) {
+                const uint32_t nb16 = (n_of(h * H + b) / VE) * 16u;
+                if (nb16) bulk_copy_g2s(slot(b), in + (blk0 + h * H + b) * L, nb16, &g_stage_bar[warp]);
+            }
+        }
+        for (uint32_t b = warp; b < nh; b += NW) {
+            const uint32_t n_b = n_of(h * H + b);
+            T *dst = slot(b);
+            for (uint32_t e = n_b / VE * VE + lane; e < n_b; e += 32) dst[e] = in[(blk0 + h * H + b) * L + e];
+        }
+        if (!mbar_wait(&g_stage_bar[warp], phase & 1u, limit_ns) && lane == 0) record_error(ws, PC_ERR_TIMEOUT);
+        ++phase;  // every warp's barrier completed one phase
+        __syncwarp();
+    };
+
+    // 1-2. min / max of both halves, the second staged over the first
+    stage_half(0, nh0);
+    for (uint32_t b = warp; b < nh0; b += NW) block_minmax<T>(slot(b), n_of(b), &pv.vmin[b], &pv.B[b]);
+    if (nh1) {
+        stage_half(1, nh1);
+        for (uint32_t b = warp; b < nh1; b += NW) block_minmax<T>(slot(b), n_of(H + b), &pv.vmin[H + b], &pv.B[H + b]);
+    }
+    __syncthreads();
+
+    // 3-4. word counts (lane per block, two passes), scan, aggregate, look-back
+    if (warp == 0) {
+        uint32_t Wv[2] = {0u, 0u};
+#pragma unroll
+        for (uint32_t h = 0; h < 2; ++h) {
+            const uint32_t b = 32 * h + lane;
+            if (b < nblk) {
+                const uint64_t B = pv.B[b];
+                if (B > 1) {
+                    uint64_t geo;  // 1 + B + ... + B^(p-1), mod 2^64
+                    const uint32_t p = basic_p_geo(B, WB, geo);
+                    pv.p[b] = p;
+                    Wv[h] = (n_of(b) + p - 1) / p;
+                    pv.K[b] = geo * pv.vmin[b];
+                }
+                pv.W[b] = Wv[h];
+            }
+        }
+        const uint32_t i0 = warp_incl_scan_u32(Wv[0]), i1 = warp_incl_scan_u32(Wv[1]);
+        const uint32_t t0 = __shfl_sync(0xFFFFFFFFu, i0, 31);
+        if (lane < nblk) pv.woff[lane] = i0 - Wv[0];
+        if (32 + lane < nblk) pv.woff[32 + lane] = t0 + i1 - Wv[1];
+        const uint32_t agg = t0 + __shfl_sync(0xFFFFFFFFu, i1, 31);
+        lookback_publish(sa.status, tile, agg);
+        uint64_t excl = 0;
+        const bool ok = lookback_complete(sa.status, tile, agg, ws, limit_ns, &excl);
+        if (lane == 0) {
+            pv.agg = agg;
+            pv.excl = excl;
+            pv.ok = ok ? 1u : 0u;
+        }
+    }
+    __syncthreads();
+
+    // 5. table entries; the second half packed from the stage, then each warp
+    // restages and packs its first-half blocks; the stream's closing bytes
+    if (pv.ok) {
+        for (uint32_t b = threadIdx.x; b < nblk; b += NT) {
+            const uint64_t gb = blk0 + b;
+            const uint64_t Bm1 = pv.B[b] - 1;
+            if constexpr (D == 16) {
+                reinterpret_cast<uint32_t *>(sa.out + PC_HEADER_BYTES)[gb] = pv.vmin[b] | ((uint32_t)Bm1 << 16);
+            } else {
+                reinterpret_cast<uint64_t *>(sa.out + PC_HEADER_BYTES)[gb] = (uint64_t)pv.vmin[b] | (Bm1 << 32);
+            }
+        }
+        Word *payload = reinterpret_cast<Word *>(sa.out + payload_off) + pv.excl;
+        auto pack_half = [&](uint32_t h, uint32_t nh) {
+            for (uint32_t b = warp; b < nh; b += NW) {
+                const uint32_t bb = h * H + b;
+                const uint32_t W = pv.W[bb];
+                if (W == 0) continue;
+                pack_basic_block<T, WB>(slot(b), W, pv.p[bb], (uint32_t)pv.B[bb], pv.K[bb], payload + pv.woff[bb]);
+            }
+        };
+        if (nh1) {
+            pack_half(1, nh1);
+            stage_half(0, nh0);
+            for (uint32_t b = warp; b < nh0; b += NW) {  // padding: the first half's minimum again
+                T *u = slot(b);
+                const uint32_t n_b = n_of(b);
+                for (uint32_t i = lane; i < kPad; i += 32) u[n_b + i] = (T)pv.vmin[b];
+            }
+            __syncwarp();
+        }
+        pack_half(0, nh0);
+        if (tile == n_tiles - 1) {
+            const uint64_t payload_words = pv.excl + pv.agg;
+            const uint64_t tend = PC_HEADER_BYTES + n_blocks * 2u * (D / 8);
+            for (uint64_t o = tend + threadIdx.x; o < payload_off; o += NT) sa.out[o] = 0;
+            if (threadIdx.x == 0) {
+                write_header<D, WB, PC_VARIANT_BASIC>(sa.out, L, n, n_blocks, payload_words);
+                *sa.out_bytes = payload_off + payload_words * (WB / 8);
+            }
+        }
+    }
+    __syncthreads();  // the stage and the pair arrays are free again
+}
+
 // Header of an empty stream (no blocks).
 template <uint32_t D, uint32_t WB, uint32_t VAR>
 __device__ void write_empty_stream(const StreamArgs &sa)
@@ -534,7 +689,7 @@ template <uint32_t VAR, uint32_t NT>
 constexpr int kCompressMinCtas =
     (VAR == PC_VARIANT_BASIC ? PCX_COMPRESS_MIN_CTAS_BASIC : PCX_COMPRESS_MIN_CTAS_ADVANCED) * (NT <= 128 ? 2 : 1);
 
-template <typename T, uint32_t WB, uint32_t VAR, bool ORB, uint32_t NT>
+template <typename T, uint32_t WB, uint32_t VAR, bool ORB, uint32_t NT, bool PAIR = false>
 __global__ void __launch_bounds__(NT, kCompressMinCtas<VAR, NT>)
 k_compress(StreamArgs sa, WsHeader *ws, uint64_t limit_ns)
 {
@@ -552,7 +707,8 @@ k_compress(StreamArgs sa, WsHeader *ws, uint64_t limit_ns)
         const uint64_t tile = s_tile;
         __syncthreads();
         if (tile >= sa.n_tiles) break;
-        compress_tile<T, WB, VAR, ORB, NT>(sa, tile, smem, ws, limit_ns, phase);
+        if constexpr (PAIR) compress_tile_pair<T, WB, NT>(sa, tile, smem, ws, limit_ns, phase);
+        else compress_tile<T, WB, VAR, ORB, NT>(sa, tile, smem, ws, limit_ns, phase);
     }
 }
 

@@ -1,0 +1,45 @@
+"""Long basic streams are compressed with pair tiles (one look-back per two
+stage tiles, the first half restaged after the second is packed).  Every
+byte of such streams equals the oracle's, for ragged ends where the last
+pair has a partial second half or none, and for both word sizes."""
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import numpy as np  # noqa: E402
+
+import oracle  # noqa: E402
+import paper_1805_01844_gb300 as pc  # noqa: E402
+from paper_1805_01844_gb300 import datagen, native  # noqa: E402
+
+SMALL_TILES = 2432  # tiles a stream needs before its compression takes pairs (one wave of 152 SMs x 16)
+
+
+def stage_blocks(L):
+    # blocks per stage tile of the basic compressor: 72 KB over (L + 64) uint16 slots, a multiple of 8
+    tb = min(32, (72 * 1024) // (((L + 64) * 2 + 15) // 16 * 16))
+    return tb & ~7 if tb >= 8 else tb
+
+
+@pytest.mark.parametrize("L,w,extra_blocks", [(1024, 64, 40), (1024, 64, 5), (1024, 32, 33), (4096, 64, 9)])
+def test_pair_tiles_match_oracle(L, w, extra_blocks):
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    dev = torch.device("cuda:0")
+    pair = 2 * stage_blocks(L)
+    n_blocks = pair * SMALL_TILES + extra_blocks
+    n = (n_blocks - 1) * L + 777  # ragged last block
+    x = datagen.white_noise(n, 300.0, 5.0, seed=L + w + extra_blocks)
+    # a few wide blocks so that several bases occur
+    for b in range(0, n_blocks - 1, 997):
+        x[b * L] = 4000
+    want = oracle.compress(x, 0, w, L)
+    xd = torch.from_numpy(x.view(np.int16)).to(dev)
+    codec = pc.Codec(0, 16, w, L, max_samples=n, device=dev)
+    sbuf = torch.empty(codec.bound(n), dtype=torch.uint8, device=dev)
+    _, nb = codec.compress(xd, out=sbuf)
+    assert codec.device_status() == native.PC_OK
+    got = sbuf[: int(nb.item())].cpu().numpy().tobytes()
+    assert len(got) == len(want)
+    assert got == want
