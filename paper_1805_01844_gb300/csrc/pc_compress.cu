@@ -9,13 +9,15 @@ template <typename T, uint32_t WB, uint32_t VAR, bool ORB, uint32_t NT>
 static cudaError_t launch_compress_t(const LaunchArgs &a)
 {
     const TileCfg cfg = tile_cfg(kKernelCompress, VAR, sizeof(T) * 8, WB, a.L, ORB, NT);
-    // basic streams long enough for pairs of full tiles on every SM: one
-    // look-back per pair (compress_tile_pair); the stage layout is the same
-    constexpr bool kPairable = VAR == PC_VARIANT_BASIC && NT == kThreads;
-    const bool pair = kPairable && a.tb == cfg.tb && cfg.tb >= 8 && (a.L * sizeof(T)) % 16 == 0 &&
-                      ceil_div(a.n_blocks, 2ull * cfg.tb) >= kSmallTiles;
-    auto kern = pair ? k_compress<T, WB, VAR, ORB, NT, kPairable> : k_compress<T, WB, VAR, ORB, NT, false>;
-    const uint64_t n_tiles = pair ? ceil_div(a.n_blocks, 2ull * cfg.tb) : a.n_tiles;
+    // basic streams long enough for look-back tiles of several full stage
+    // tiles on every SM: one look-back per multi_k stage tiles
+    // (compress_tile_multi); the stage layout is the same
+    constexpr bool kMultiOk = VAR == PC_VARIANT_BASIC && NT == kThreads;
+    const uint32_t k = multi_k(cfg.tb);
+    const bool multi = kMultiOk && k >= 2 && a.tb == cfg.tb && cfg.tb >= 8 && (a.L * sizeof(T)) % 16 == 0 &&
+                       ceil_div(a.n_blocks, (uint64_t)k * cfg.tb) >= kSmallTiles;
+    auto kern = multi ? k_compress<T, WB, VAR, ORB, NT, kMultiOk> : k_compress<T, WB, VAR, ORB, NT, false>;
+    const uint64_t n_tiles = multi ? ceil_div(a.n_blocks, (uint64_t)k * cfg.tb) : a.n_tiles;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.smem);
     if (e != cudaSuccess) return e;
     // all of the unified L1 / shared storage as shared memory, so that the
@@ -39,7 +41,7 @@ static cudaError_t launch_compress_t(const LaunchArgs &a)
     sa.status = a.status;
     sa.n_blocks = a.n_blocks;
     sa.n_tiles = n_tiles;
-    sa.tb = pair ? 2 * cfg.tb : a.tb;
+    sa.tb = multi ? k * cfg.tb : a.tb;
     sa.ot = OrbitTable{a.orb_flags, a.orb_hdr, static_cast<ulonglong2 *>(a.orb_slots), &a.ws->orbit_cursor};
     kern<<<(unsigned)grid, NT, cfg.smem, a.stream>>>(sa, a.ws, a.limit_ns);
     return cudaGetLastError();

@@ -510,30 +510,43 @@ __device__ void compress_tile(const StreamArgs &sa, uint64_t tile, uint8_t *smem
     __syncthreads();  // the stage and the per-tile arrays are free again
 }
 
-// Basic variant, long streams: one look-back tile is a pair of stage tiles
-// (2 tb blocks) staged one after the other in the same shared memory.  The
-// first half's min / max are taken, then its slots take the second half;
-// after the pair's single look-back the second half is packed where it sits
-// and each warp restages its own first-half blocks (just read, so from L2)
-// and packs them.  A look-back per 2 tb blocks instead of per tb: measured,
-// each tile's look-back waits several microseconds on its predecessors'
-// aggregates, and smaller tiles compress markedly slower.
-struct PairVars {  // per-pair arrays, in the BlockVars space of the stage
-    uint64_t B[2 * kMaxTileBlocks];
-    uint64_t K[2 * kMaxTileBlocks];
-    uint32_t vmin[2 * kMaxTileBlocks];
-    uint32_t W[2 * kMaxTileBlocks];
-    uint32_t woff[2 * kMaxTileBlocks];
-    uint32_t p[2 * kMaxTileBlocks];
+// Basic variant, long streams: one look-back tile spans K stage tiles
+// (K tb blocks, sa.tb = K tb) staged one after the other in the same shared
+// memory.  Each stage tile's min / max are taken before the next overwrites
+// its slots; after the single look-back the last stage tile is packed where
+// it sits and each warp restages its own blocks of the earlier ones (just
+// read, so from L2) and packs them, last to first.  A look-back per K tb
+// blocks instead of per tb: measured, each tile's look-back waits several
+// microseconds on its predecessors' aggregates, and smaller tiles compress
+// markedly slower.
+constexpr uint32_t kMultiMaxBlocks = 96;  // blocks of one look-back tile
+
+struct MultiVars {  // per-tile arrays, in the BlockVars space of the stage
+    uint64_t B[kMultiMaxBlocks];
+    uint64_t K[kMultiMaxBlocks];
+    uint32_t vmin[kMultiMaxBlocks];
+    uint32_t W[kMultiMaxBlocks];
+    uint32_t woff[kMultiMaxBlocks];
+    uint32_t p[kMultiMaxBlocks];
     uint64_t excl;
     uint32_t agg;
     uint32_t ok;
 };
-static_assert(sizeof(PairVars) <= sizeof(BlockVars), "pair arrays fit the tile arrays");
+static_assert(sizeof(MultiVars) <= sizeof(BlockVars), "look-back tile arrays fit the stage tile arrays");
+
+// Stage tiles per look-back tile for stage tiles of tb blocks.
+#ifndef PCX_MULTI_K_MAX
+#define PCX_MULTI_K_MAX 8
+#endif
+PCX_HD uint32_t multi_k(uint32_t tb)
+{
+    uint32_t k = kMultiMaxBlocks / tb;
+    return k > PCX_MULTI_K_MAX ? PCX_MULTI_K_MAX : k;
+}
 
 template <typename T, uint32_t WB, uint32_t NT>
-__device__ void compress_tile_pair(const StreamArgs &sa, uint64_t tile, uint8_t *smem, WsHeader *ws,
-                                   uint64_t limit_ns, uint32_t &phase)
+__device__ void compress_tile_multi(const StreamArgs &sa, uint64_t tile, uint8_t *smem, WsHeader *ws,
+                                    uint64_t limit_ns, uint32_t &phase)
 {
     using Word = typename WordOf<T, WB>::type;
     constexpr uint32_t D = sizeof(T) * 8;
@@ -541,33 +554,35 @@ __device__ void compress_tile_pair(const StreamArgs &sa, uint64_t tile, uint8_t 
     constexpr uint32_t NW = NT / 32;
     const uint32_t L = sa.L;
     const TileCfg cfg = tile_cfg(kKernelCompress, PC_VARIANT_BASIC, D, WB, L, false, NT);
-    const uint32_t H = cfg.tb;  // blocks per half
-    PairVars &pv = *reinterpret_cast<PairVars *>(smem + cfg.off_blk);
+    const uint32_t H = cfg.tb;  // blocks per stage tile; sa.tb = K H
+    MultiVars &mv = *reinterpret_cast<MultiVars *>(smem + cfg.off_blk);
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
     const T *in = static_cast<const T *>(sa.in);
     const uint64_t n = sa.n, n_blocks = sa.n_blocks, n_tiles = sa.n_tiles;
     const uint64_t payload_off = PC_HEADER_BYTES + table_bytes(n_blocks, D);
-    const uint64_t blk0 = tile * 2 * H;
-    const uint32_t nblk = (uint32_t)umin64(2 * H, n_blocks - blk0);
-    const uint32_t nh0 = nblk < H ? nblk : H, nh1 = nblk - nh0;
+    const uint64_t blk0 = tile * sa.tb;
+    const uint32_t nblk = (uint32_t)umin64(sa.tb, n_blocks - blk0);
+    const uint32_t nst = (nblk + H - 1) / H;  // stage tiles in this tile
+    auto nh = [&](uint32_t h) -> uint32_t { return nblk - h * H < H ? nblk - h * H : H; };
     auto n_of = [&](uint32_t b) -> uint32_t { return (uint32_t)umin64(L, n - (blk0 + b) * L); };
     auto slot = [&](uint32_t b) -> T * { return reinterpret_cast<T *>(smem + (uint64_t)(b % H) * cfg.stage_bytes); };
 
-    // this warp's blocks of half h into their slots: one bulk copy per block
-    // (lane 0) on the warp's mbarrier, the ragged end by plain loads
-    auto stage_half = [&](uint32_t h, uint32_t nh) {
+    // this warp's blocks of stage tile h into their slots: one bulk copy per
+    // block (lane 0) on the warp's mbarrier, the ragged end by plain loads
+    auto stage = [&](uint32_t h) {
+        const uint32_t m = nh(h);
         __syncwarp();  // the warp's earlier accesses to its slots come first
         if (lane == 0) {
             uint32_t bytes = 0;
-            for (uint32_t b = warp; b < nh; b += NW) bytes += (n_of(h * H + b) / VE) * 16u;
+            for (uint32_t b = warp; b < m; b += NW) bytes += (n_of(h * H + b) / VE) * 16u;
             fence_proxy_async_smem();
             mbar_arrive_expect_tx(&g_stage_bar[warp], bytes);
-            for (uint32_t b = warp; b < nh; b += NW) {
+            for (uint32_t b = warp; b < m; b += NW) {
                 const uint32_t nb16 = (n_of(h * H + b) / VE) * 16u;
                 if (nb16) bulk_copy_g2s(slot(b), in + (blk0 + h * H + b) * L, nb16, &g_stage_bar[warp]);
             }
         }
-        for (uint32_t b = warp; b < nh; b += NW) {
+        for (uint32_t b = warp; b < m; b += NW) {
             const uint32_t n_b = n_of(h * H + b);
             T *dst = slot(b);
             for (uint32_t e = n_b / VE * VE + lane; e < n_b; e += 32) dst[e] = in[(blk0 + h * H + b) * L + e];
@@ -577,83 +592,80 @@ __device__ void compress_tile_pair(const StreamArgs &sa, uint64_t tile, uint8_t 
         __syncwarp();
     };
 
-    // 1-2. min / max of both halves, the second staged over the first
-    stage_half(0, nh0);
-    for (uint32_t b = warp; b < nh0; b += NW) block_minmax<T>(slot(b), n_of(b), &pv.vmin[b], &pv.B[b]);
-    if (nh1) {
-        stage_half(1, nh1);
-        for (uint32_t b = warp; b < nh1; b += NW) block_minmax<T>(slot(b), n_of(H + b), &pv.vmin[H + b], &pv.B[H + b]);
+    // 1-2. min / max, stage tile by stage tile over the same slots
+    for (uint32_t h = 0; h < nst; ++h) {
+        stage(h);
+        for (uint32_t b = warp; b < nh(h); b += NW)
+            block_minmax<T>(slot(b), n_of(h * H + b), &mv.vmin[h * H + b], &mv.B[h * H + b]);
     }
     __syncthreads();
 
-    // 3-4. word counts (lane per block, two passes), scan, aggregate, look-back
+    // 3-4. word counts (lane per block, 32 at a time), scan, aggregate, look-back
     if (warp == 0) {
-        uint32_t Wv[2] = {0u, 0u};
-#pragma unroll
-        for (uint32_t h = 0; h < 2; ++h) {
-            const uint32_t b = 32 * h + lane;
+        uint32_t run = 0;
+        for (uint32_t b0 = 0; b0 < nblk; b0 += 32) {
+            const uint32_t b = b0 + lane;
+            uint32_t W = 0;
             if (b < nblk) {
-                const uint64_t B = pv.B[b];
+                const uint64_t B = mv.B[b];
                 if (B > 1) {
                     uint64_t geo;  // 1 + B + ... + B^(p-1), mod 2^64
                     const uint32_t p = basic_p_geo(B, WB, geo);
-                    pv.p[b] = p;
-                    Wv[h] = (n_of(b) + p - 1) / p;
-                    pv.K[b] = geo * pv.vmin[b];
+                    mv.p[b] = p;
+                    W = (n_of(b) + p - 1) / p;
+                    mv.K[b] = geo * mv.vmin[b];
                 }
-                pv.W[b] = Wv[h];
+                mv.W[b] = W;
             }
+            const uint32_t incl = warp_incl_scan_u32(W);
+            if (b < nblk) mv.woff[b] = run + incl - W;
+            run += __shfl_sync(0xFFFFFFFFu, incl, 31);
         }
-        const uint32_t i0 = warp_incl_scan_u32(Wv[0]), i1 = warp_incl_scan_u32(Wv[1]);
-        const uint32_t t0 = __shfl_sync(0xFFFFFFFFu, i0, 31);
-        if (lane < nblk) pv.woff[lane] = i0 - Wv[0];
-        if (32 + lane < nblk) pv.woff[32 + lane] = t0 + i1 - Wv[1];
-        const uint32_t agg = t0 + __shfl_sync(0xFFFFFFFFu, i1, 31);
+        const uint32_t agg = run;
         lookback_publish(sa.status, tile, agg);
         uint64_t excl = 0;
         const bool ok = lookback_complete(sa.status, tile, agg, ws, limit_ns, &excl);
         if (lane == 0) {
-            pv.agg = agg;
-            pv.excl = excl;
-            pv.ok = ok ? 1u : 0u;
+            mv.agg = agg;
+            mv.excl = excl;
+            mv.ok = ok ? 1u : 0u;
         }
     }
     __syncthreads();
 
-    // 5. table entries; the second half packed from the stage, then each warp
-    // restages and packs its first-half blocks; the stream's closing bytes
-    if (pv.ok) {
+    // 5. table entries; the last stage tile packed from the stage, then each
+    // warp restages and packs its blocks of the earlier ones; the stream's
+    // closing bytes
+    if (mv.ok) {
         for (uint32_t b = threadIdx.x; b < nblk; b += NT) {
             const uint64_t gb = blk0 + b;
-            const uint64_t Bm1 = pv.B[b] - 1;
+            const uint64_t Bm1 = mv.B[b] - 1;
             if constexpr (D == 16) {
-                reinterpret_cast<uint32_t *>(sa.out + PC_HEADER_BYTES)[gb] = pv.vmin[b] | ((uint32_t)Bm1 << 16);
+                reinterpret_cast<uint32_t *>(sa.out + PC_HEADER_BYTES)[gb] = mv.vmin[b] | ((uint32_t)Bm1 << 16);
             } else {
-                reinterpret_cast<uint64_t *>(sa.out + PC_HEADER_BYTES)[gb] = (uint64_t)pv.vmin[b] | (Bm1 << 32);
+                reinterpret_cast<uint64_t *>(sa.out + PC_HEADER_BYTES)[gb] = (uint64_t)mv.vmin[b] | (Bm1 << 32);
             }
         }
-        Word *payload = reinterpret_cast<Word *>(sa.out + payload_off) + pv.excl;
-        auto pack_half = [&](uint32_t h, uint32_t nh) {
-            for (uint32_t b = warp; b < nh; b += NW) {
+        Word *payload = reinterpret_cast<Word *>(sa.out + payload_off) + mv.excl;
+        for (uint32_t h = nst; h-- > 0;) {
+            if (h + 1 < nst) {
+                stage(h);
+                for (uint32_t b = warp; b < nh(h); b += NW) {  // padding: this stage tile's minimum again
+                    T *u = slot(b);
+                    const uint32_t n_b = n_of(h * H + b);
+                    for (uint32_t i = lane; i < kPad; i += 32) u[n_b + i] = (T)mv.vmin[h * H + b];
+                }
+                __syncwarp();
+            }
+            for (uint32_t b = warp; b < nh(h); b += NW) {
                 const uint32_t bb = h * H + b;
-                const uint32_t W = pv.W[bb];
+                const uint32_t W = mv.W[bb];
                 if (W == 0) continue;
-                pack_basic_block<T, WB>(slot(b), W, pv.p[bb], (uint32_t)pv.B[bb], pv.K[bb], payload + pv.woff[bb]);
+                pack_basic_block<T, WB>(slot(b), W, mv.p[bb], (uint32_t)mv.B[bb], mv.K[bb], payload + mv.woff[bb]);
             }
-        };
-        if (nh1) {
-            pack_half(1, nh1);
-            stage_half(0, nh0);
-            for (uint32_t b = warp; b < nh0; b += NW) {  // padding: the first half's minimum again
-                T *u = slot(b);
-                const uint32_t n_b = n_of(b);
-                for (uint32_t i = lane; i < kPad; i += 32) u[n_b + i] = (T)pv.vmin[b];
-            }
-            __syncwarp();
         }
-        pack_half(0, nh0);
         if (tile == n_tiles - 1) {
-            const uint64_t payload_words = pv.excl + pv.agg;
+            const uint64_t payload_words = mv.excl + mv.agg;
             const uint64_t tend = PC_HEADER_BYTES + n_blocks * 2u * (D / 8);
             for (uint64_t o = tend + threadIdx.x; o < payload_off; o += NT) sa.out[o] = 0;
             if (threadIdx.x == 0) {
@@ -662,7 +674,7 @@ __device__ void compress_tile_pair(const StreamArgs &sa, uint64_t tile, uint8_t 
             }
         }
     }
-    __syncthreads();  // the stage and the pair arrays are free again
+    __syncthreads();  // the stage and the tile arrays are free again
 }
 
 // Header of an empty stream (no blocks).
@@ -689,7 +701,7 @@ template <uint32_t VAR, uint32_t NT>
 constexpr int kCompressMinCtas =
     (VAR == PC_VARIANT_BASIC ? PCX_COMPRESS_MIN_CTAS_BASIC : PCX_COMPRESS_MIN_CTAS_ADVANCED) * (NT <= 128 ? 2 : 1);
 
-template <typename T, uint32_t WB, uint32_t VAR, bool ORB, uint32_t NT, bool PAIR = false>
+template <typename T, uint32_t WB, uint32_t VAR, bool ORB, uint32_t NT, bool MULTI = false>
 __global__ void __launch_bounds__(NT, kCompressMinCtas<VAR, NT>)
 k_compress(StreamArgs sa, WsHeader *ws, uint64_t limit_ns)
 {
@@ -707,7 +719,7 @@ k_compress(StreamArgs sa, WsHeader *ws, uint64_t limit_ns)
         const uint64_t tile = s_tile;
         __syncthreads();
         if (tile >= sa.n_tiles) break;
-        if constexpr (PAIR) compress_tile_pair<T, WB, NT>(sa, tile, smem, ws, limit_ns, phase);
+        if constexpr (MULTI) compress_tile_multi<T, WB, NT>(sa, tile, smem, ws, limit_ns, phase);
         else compress_tile<T, WB, VAR, ORB, NT>(sa, tile, smem, ws, limit_ns, phase);
     }
 }

@@ -1,7 +1,8 @@
-"""Long basic streams are compressed with pair tiles (one look-back per two
-stage tiles, the first half restaged after the second is packed).  Every
-byte of such streams equals the oracle's, for ragged ends where the last
-pair has a partial second half or none, and for both word sizes."""
+"""Long basic streams are compressed with look-back tiles of several stage
+tiles (one look-back per K stage tiles, the earlier ones restaged after the
+last is packed).  Every byte of such streams equals the oracle's, for ragged
+ends where the last look-back tile has one, two or three stage tiles, the last
+partial, and for both word sizes."""
 import pytest
 
 torch = pytest.importorskip("torch")
@@ -13,7 +14,7 @@ import oracle  # noqa: E402
 import paper_1805_01844_gb300 as pc  # noqa: E402
 from paper_1805_01844_gb300 import datagen, native  # noqa: E402
 
-SMALL_TILES = 2432  # tiles a stream needs before its compression takes pairs (one wave of 152 SMs x 16)
+SMALL_TILES = 2432  # tiles a stream needs before its compression takes multi-stage tiles (152 SMs x 16)
 
 
 def stage_blocks(L):
@@ -22,13 +23,18 @@ def stage_blocks(L):
     return tb & ~7 if tb >= 8 else tb
 
 
-@pytest.mark.parametrize("L,w,extra_blocks", [(1024, 64, 40), (1024, 64, 5), (1024, 32, 33), (4096, 64, 9)])
-def test_pair_tiles_match_oracle(L, w, extra_blocks):
+def stage_tiles_per_lookback(tb):
+    # stage tiles per look-back tile: up to 96 blocks, at most 8 stage tiles
+    return min(8, 96 // tb)
+
+
+@pytest.mark.parametrize("L,w,extra_blocks", [(1024, 64, 70), (1024, 64, 5), (1024, 32, 40), (4096, 64, 9)])
+def test_multi_stage_tiles_match_oracle(L, w, extra_blocks):
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     dev = torch.device("cuda:0")
-    pair = 2 * stage_blocks(L)
-    n_blocks = pair * SMALL_TILES + extra_blocks
+    tb = stage_blocks(L)
+    n_blocks = stage_tiles_per_lookback(tb) * tb * SMALL_TILES + extra_blocks
     n = (n_blocks - 1) * L + 777  # ragged last block
     x = datagen.white_noise(n, 300.0, 5.0, seed=L + w + extra_blocks)
     # a few wide blocks so that several bases occur
