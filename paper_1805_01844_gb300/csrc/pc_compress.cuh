@@ -568,18 +568,22 @@ __device__ void compress_tile_multi(const StreamArgs &sa, uint64_t tile, uint8_t
     auto slot = [&](uint32_t b) -> T * { return reinterpret_cast<T *>(smem + (uint64_t)(b % H) * cfg.stage_bytes); };
 
     // this warp's blocks of stage tile h into their slots: one bulk copy per
-    // block (lane 0) on the warp's mbarrier, the ragged end by plain loads
-    auto stage = [&](uint32_t h) {
+    // block (lane 0) on the warp's mbarrier, the ragged end by plain loads.
+    // A stage tile that will be restaged is read with evict_last priority
+    // in L2, the last reads of every tile with evict_first.
+    auto stage = [&](uint32_t h, bool again) {
         const uint32_t m = nh(h);
         __syncwarp();  // the warp's earlier accesses to its slots come first
         if (lane == 0) {
             uint32_t bytes = 0;
             for (uint32_t b = warp; b < m; b += NW) bytes += (n_of(h * H + b) / VE) * 16u;
+            const uint64_t policy = again ? l2_policy_evict_last() : l2_policy_evict_first();
             fence_proxy_async_smem();
             mbar_arrive_expect_tx(&g_stage_bar[warp], bytes);
             for (uint32_t b = warp; b < m; b += NW) {
                 const uint32_t nb16 = (n_of(h * H + b) / VE) * 16u;
-                if (nb16) bulk_copy_g2s(slot(b), in + (blk0 + h * H + b) * L, nb16, &g_stage_bar[warp]);
+                if (nb16)
+                    bulk_copy_g2s_hint(slot(b), in + (blk0 + h * H + b) * L, nb16, &g_stage_bar[warp], policy);
             }
         }
         for (uint32_t b = warp; b < m; b += NW) {
@@ -594,7 +598,7 @@ __device__ void compress_tile_multi(const StreamArgs &sa, uint64_t tile, uint8_t
 
     // 1-2. min / max, stage tile by stage tile over the same slots
     for (uint32_t h = 0; h < nst; ++h) {
-        stage(h);
+        stage(h, h + 1 < nst);
         for (uint32_t b = warp; b < nh(h); b += NW)
             block_minmax<T>(slot(b), n_of(h * H + b), &mv.vmin[h * H + b], &mv.B[h * H + b]);
     }
@@ -649,7 +653,7 @@ __device__ void compress_tile_multi(const StreamArgs &sa, uint64_t tile, uint8_t
         Word *payload = reinterpret_cast<Word *>(sa.out + payload_off) + mv.excl;
         for (uint32_t h = nst; h-- > 0;) {
             if (h + 1 < nst) {
-                stage(h);
+                stage(h, false);
                 for (uint32_t b = warp; b < nh(h); b += NW) {  // padding: this stage tile's minimum again
                     T *u = slot(b);
                     const uint32_t n_b = n_of(h * H + b);

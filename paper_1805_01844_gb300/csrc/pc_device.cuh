@@ -99,6 +99,33 @@ __device__ __forceinline__ void bulk_copy_g2s(void *smem, const void *gmem, uint
                  ::"r"(d), "l"(gmem), "r"(bytes), "r"(a) : "memory");
 }
 
+// The same with an L2 eviction-priority policy (createpolicy) for the lines
+// it reads: evict_last for data read again soon, evict_first for data read
+// for the last time.
+__device__ __forceinline__ void bulk_copy_g2s_hint(void *smem, const void *gmem, uint32_t bytes, uint64_t *bar,
+                                                   uint64_t policy)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem);
+    const unsigned a = (unsigned)__cvta_generic_to_shared(bar);
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;"
+        ::"r"(d), "l"(gmem), "r"(bytes), "r"(a), "l"(policy) : "memory");
+}
+
+__device__ __forceinline__ uint64_t l2_policy_evict_last()
+{
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+__device__ __forceinline__ uint64_t l2_policy_evict_first()
+{
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
 // Bounded wait for the mbarrier phase of the given parity; false if it gave up.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint64_t limit_ns)
 {
