@@ -17,9 +17,9 @@ from paper_1805_01844_gb300 import datagen, native  # noqa: E402
 SMALL_TILES = 2432  # tiles a stream needs before its compression takes multi-stage tiles (152 SMs x 16)
 
 
-def stage_blocks(L):
-    # blocks per stage tile of the basic compressor: 72 KB over (L + 64) uint16 slots, a multiple of 8
-    tb = min(32, (72 * 1024) // (((L + 64) * 2 + 15) // 16 * 16))
+def stage_blocks(L, d=16):
+    # blocks per stage tile of the basic compressor: 72 KB over (L + 64)-sample slots, a multiple of 8
+    tb = min(32, (72 * 1024) // (((L + 64) * (d // 8) + 15) // 16 * 16))
     return tb & ~7 if tb >= 8 else tb
 
 
@@ -28,21 +28,23 @@ def stage_tiles_per_lookback(tb):
     return min(8, 96 // tb)
 
 
-@pytest.mark.parametrize("L,w,extra_blocks", [(1024, 64, 70), (1024, 64, 5), (1024, 32, 40), (4096, 64, 9)])
-def test_multi_stage_tiles_match_oracle(L, w, extra_blocks):
+@pytest.mark.parametrize("d,L,w,extra_blocks", [(16, 1024, 64, 70), (16, 1024, 64, 5), (16, 1024, 32, 40),
+                                                 (16, 4096, 64, 9), (32, 1024, 64, 50)])
+def test_multi_stage_tiles_match_oracle(d, L, w, extra_blocks):
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     dev = torch.device("cuda:0")
-    tb = stage_blocks(L)
+    tb = stage_blocks(L, d)
     n_blocks = stage_tiles_per_lookback(tb) * tb * SMALL_TILES + extra_blocks
     n = (n_blocks - 1) * L + 777  # ragged last block
-    x = datagen.white_noise(n, 300.0, 5.0, seed=L + w + extra_blocks)
+    dt = np.uint16 if d == 16 else np.uint32
+    x = datagen.white_noise(n, 300.0 if d == 16 else 70000.0, 5.0, seed=L + w + extra_blocks, dtype=dt)
     # a few wide blocks so that several bases occur
     for b in range(0, n_blocks - 1, 997):
-        x[b * L] = 4000
+        x[b * L] = 4000 if d == 16 else 3000000
     want = oracle.compress(x, 0, w, L)
-    xd = torch.from_numpy(x.view(np.int16)).to(dev)
-    codec = pc.Codec(0, 16, w, L, max_samples=n, device=dev)
+    xd = torch.from_numpy(x.view(np.int16 if d == 16 else np.int32)).to(dev)
+    codec = pc.Codec(0, d, w, L, max_samples=n, device=dev)
     sbuf = torch.empty(codec.bound(n), dtype=torch.uint8, device=dev)
     _, nb = codec.compress(xd, out=sbuf)
     assert codec.device_status() == native.PC_OK
