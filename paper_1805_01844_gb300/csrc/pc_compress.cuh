@@ -231,7 +231,7 @@ __device__ __forceinline__ void adv_words_orbit(const OrbitTable &ot, const Orbi
 // per lane in lockstep so that their Horner chains are independent for the
 // scheduler.  Lanes past the last word recompute the last word and do not
 // store it.
-template <typename T, uint32_t WB, uint32_t NK>
+template <typename T, uint32_t WB, uint32_t NK, bool FULL = false>
 __device__ __forceinline__ void pack_basic_group(const T *u, uint32_t j0, uint32_t W, uint32_t p, uint32_t B32,
                                                  uint64_t K, typename WordOf<T, WB>::type *dst)
 {
@@ -240,7 +240,7 @@ __device__ __forceinline__ void pack_basic_group(const T *u, uint32_t j0, uint32
     const T *g[NK];
 #pragma unroll
     for (uint32_t k = 0; k < NK; ++k) {
-        const uint32_t j = min(j0 + lane + 32 * k, W - 1);
+        const uint32_t j = FULL ? j0 + lane + 32 * k : min(j0 + lane + 32 * k, W - 1);
         g[k] = u + j * p;
     }
     Word acc[NK];
@@ -272,7 +272,7 @@ __device__ __forceinline__ void pack_basic_group(const T *u, uint32_t j0, uint32
 #pragma unroll
     for (uint32_t k = 0; k < NK; ++k) {
         const uint32_t j = j0 + lane + 32 * k;
-        if (j < W) dst[j] = acc[k];
+        if (FULL || j < W) dst[j] = acc[k];
     }
 }
 
@@ -283,7 +283,7 @@ __device__ __forceinline__ void pack_basic_block(const T *u, uint32_t W, uint32_
                                                  typename WordOf<T, WB>::type *dst)
 {
     uint32_t j0 = 0;
-    for (; j0 + 128 <= W; j0 += 128) pack_basic_group<T, WB, 4>(u, j0, W, p, B32, K, dst);
+    for (; j0 + 128 <= W; j0 += 128) pack_basic_group<T, WB, 4, true>(u, j0, W, p, B32, K, dst);
     const uint32_t rest = W - j0;
     if (rest > 96) pack_basic_group<T, WB, 4>(u, j0, W, p, B32, K, dst);
     else if (rest > 64) pack_basic_group<T, WB, 3>(u, j0, W, p, B32, K, dst);

@@ -639,7 +639,7 @@ k_decode(const uint8_t *__restrict__ in, uint32_t L, T *__restrict__ out, uint64
 // (u at shared address ua; each lane walks its digits with a 32-bit shared
 // address); lanes past the last word write theirs to the junk slots at
 // junka.  Returns true if a word is not the image of valid digits.
-template <typename T, uint32_t WB, uint32_t NK>
+template <typename T, uint32_t WB, uint32_t NK, bool FULL = false>
 __device__ __forceinline__ bool decode_basic_group(const typename WordT<T, WB>::type *src /* shared */,
                                                    uint32_t src0, uint32_t ua, uint32_t junka, uint32_t j0, uint32_t W,
                                                    uint32_t p, uint32_t hstar, uint64_t B, uint32_t vmin, Magic32 mg,
@@ -656,7 +656,7 @@ __device__ __forceinline__ bool decode_basic_group(const typename WordT<T, WB>::
 #pragma unroll
     for (uint32_t k = 0; k < NK; ++k) {
         const uint32_t j = j0 + lane + 32 * k;
-        ok[k] = j < W;
+        ok[k] = FULL || j < W;  // a full group: every lane's words exist
         sv[k] = ok[k] ? src[j - src0] : Word(0);  // src: the staged words from word src0 on
         d[k] = ok[k] ? ua + j * p * E : junka;
     }
@@ -724,7 +724,7 @@ __device__ __forceinline__ bool decode_basic_block(const typename WordT<T, WB>::
     const uint32_t ua = (uint32_t)__cvta_generic_to_shared(u), junka = (uint32_t)__cvta_generic_to_shared(junk);
     uint32_t j0 = jb;
     for (; j0 + 128 <= je; j0 += 128)
-        bad |= decode_basic_group<T, WB, 4>(src, jb, ua, junka, j0, je, p, hstar, B, vmin, mg, Dh, MD);
+        bad |= decode_basic_group<T, WB, 4, true>(src, jb, ua, junka, j0, je, p, hstar, B, vmin, mg, Dh, MD);
     for (; j0 < je; j0 += 32)
         bad |= decode_basic_group<T, WB, 1>(src, jb, ua, junka, j0, je, p, hstar, B, vmin, mg, Dh, MD);
     return bad;
