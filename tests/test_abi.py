@@ -98,7 +98,8 @@ def test_every_tile_configuration_fits_shared_memory(tmp_path):
     """Host-compiled check of the kernels' tile layout (pc_common.cuh) for
     every variant, sample width, word width and block length 1..8192: the
     dynamic shared memory stays within the 227 KB a CTA can have and tiles
-    hold 1..32 blocks, for both CTA sizes of the compression kernel."""
+    hold 1..32 blocks, for both CTA sizes of the compression kernel; the warp
+    decoder's tiles (32 blocks, or 16) keep the most resident warps."""
     import shutil
     import subprocess
 
@@ -116,8 +117,12 @@ int main() {
     TileCfg c = tile_cfg(k, v, d, w, L, orb != 0, nt);
     if (c.smem > 227u * 1024u || c.tb < 1 || c.tb > 32) { printf("bad %u %u %u %u %u\n", k, v, d, w, L); return 1; }
     if (k == 1) {
-      unsigned nw = decw_warps(v, d, w, L);
+      unsigned nw = decw_warps(v, d, w, L), cap = dec_tile_cap(v, d, w, L);
       if (nw < 1 || nw > 4 || nw * decw_warp_bytes(v, d, w, L) > 227u * 1024u) { printf("decw %u %u %u %u\n", v, d, w, L); return 1; }
+      // warp tiles of 32 blocks, or 16 where the records of 32 would cost resident warps
+      if ((cap != 16 && cap != 32) || decw_warps_per_sm(v, d, w, L, cap) < decw_warps_per_sm(v, d, w, L, 48 - cap)) {
+        printf("cap %u %u %u %u\n", v, d, w, L); return 1;
+      }
     }
   }
   printf("ok\n");
