@@ -190,8 +190,16 @@ struct BlockVars {        // per-tile arrays in shared memory
 enum : uint32_t { kKernelCompress = 0, kKernelDecode = 1 };
 
 // Tile of the compression kernel (kind 0) or of the decoding kernel (kind 1).
+// Basic compression with look-back tiles of several stage tiles, four CTAs
+// per SM: the stage budget that fits four (used where it still gives stage
+// tiles of >= 24 blocks, see compress_tile_multi).
+#ifndef PCX_TILE_BUDGET_MULTI4
+#define PCX_TILE_BUDGET_MULTI4 (54u * 1024u)
+#endif
+constexpr uint32_t kTileBudgetMulti4 = PCX_TILE_BUDGET_MULTI4;
+
 PCX_HD TileCfg tile_cfg(uint32_t kind, uint32_t variant, uint32_t d, uint32_t w, uint32_t L, bool orbit,
-                        uint32_t nt = kThreads)
+                        uint32_t nt = kThreads, uint32_t budget_override = 0)
 {
     TileCfg c;
     c.S = L + kPad;
@@ -201,8 +209,9 @@ PCX_HD TileCfg tile_cfg(uint32_t kind, uint32_t variant, uint32_t d, uint32_t w,
     const bool walk = variant == PC_VARIANT_ADVANCED && !(orbit && d == 16);
     c.wcap = walk ? (uint32_t)words_bound(variant, d, w, L) : 0u;
     // a 128-thread CTA gets about half the shared memory of a 256-thread one
-    const uint32_t budget = (variant == PC_VARIANT_ADVANCED ? kTileBudgetAdvanced : kTileBudgetBasic) /
-                            (nt <= 128 ? 2u : 1u);
+    const uint32_t budget = budget_override ? budget_override
+                                            : (variant == PC_VARIANT_ADVANCED ? kTileBudgetAdvanced : kTileBudgetBasic) /
+                                                  (nt <= 128 ? 2u : 1u);
     const uint32_t per_block = c.stage_bytes + c.wcap * 12u;
     uint32_t tb = budget / per_block;
     if (tb < 1) tb = 1;

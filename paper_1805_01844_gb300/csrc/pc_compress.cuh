@@ -544,7 +544,7 @@ PCX_HD uint32_t multi_k(uint32_t tb)
     return k > PCX_MULTI_K_MAX ? PCX_MULTI_K_MAX : k;
 }
 
-template <typename T, uint32_t WB, uint32_t NT>
+template <typename T, uint32_t WB, uint32_t NT, bool FOUR>
 __device__ void compress_tile_multi(const StreamArgs &sa, uint64_t tile, uint8_t *smem, WsHeader *ws,
                                     uint64_t limit_ns, uint32_t &phase)
 {
@@ -553,7 +553,7 @@ __device__ void compress_tile_multi(const StreamArgs &sa, uint64_t tile, uint8_t
     constexpr uint32_t VE = 16 / sizeof(T);
     constexpr uint32_t NW = NT / 32;
     const uint32_t L = sa.L;
-    const TileCfg cfg = tile_cfg(kKernelCompress, PC_VARIANT_BASIC, D, WB, L, false, NT);
+    const TileCfg cfg = tile_cfg(kKernelCompress, PC_VARIANT_BASIC, D, WB, L, false, NT, FOUR ? kTileBudgetMulti4 : 0u);
     const uint32_t H = cfg.tb;  // blocks per stage tile; sa.tb = K H
     MultiVars &mv = *reinterpret_cast<MultiVars *>(smem + cfg.off_blk);
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
@@ -705,8 +705,10 @@ template <uint32_t VAR, uint32_t NT>
 constexpr int kCompressMinCtas =
     (VAR == PC_VARIANT_BASIC ? PCX_COMPRESS_MIN_CTAS_BASIC : PCX_COMPRESS_MIN_CTAS_ADVANCED) * (NT <= 128 ? 2 : 1);
 
-template <typename T, uint32_t WB, uint32_t VAR, bool ORB, uint32_t NT, bool MULTI = false>
-__global__ void __launch_bounds__(NT, kCompressMinCtas<VAR, NT>)
+// MULTI: look-back tiles of several stage tiles (compress_tile_multi); FOUR:
+// its stage tiles sized for four CTAs per SM (registers capped at 64).
+template <typename T, uint32_t WB, uint32_t VAR, bool ORB, uint32_t NT, bool MULTI = false, bool FOUR = false>
+__global__ void __launch_bounds__(NT, FOUR ? 4 : kCompressMinCtas<VAR, NT>)
 k_compress(StreamArgs sa, WsHeader *ws, uint64_t limit_ns)
 {
     extern __shared__ __align__(16) uint8_t smem[];
@@ -723,7 +725,7 @@ k_compress(StreamArgs sa, WsHeader *ws, uint64_t limit_ns)
         const uint64_t tile = s_tile;
         __syncthreads();
         if (tile >= sa.n_tiles) break;
-        if constexpr (MULTI) compress_tile_multi<T, WB, NT>(sa, tile, smem, ws, limit_ns, phase);
+        if constexpr (MULTI) compress_tile_multi<T, WB, NT, FOUR>(sa, tile, smem, ws, limit_ns, phase);
         else compress_tile<T, WB, VAR, ORB, NT>(sa, tile, smem, ws, limit_ns, phase);
     }
 }
