@@ -101,7 +101,10 @@ pc_status pc_bound(const pc_params *params, uint64_t n_samples, uint64_t *max_by
 pc_status pc_workspace_size(const pc_params *params, uint64_t n_samples, uint64_t *bytes);
 
 /* Compress n_samples samples (uint16 or uint32 per params->dtype_bits) from
- * device memory d_in into a version-1 stream at device memory d_out.
+ * device memory d_in into a version-1 stream at device memory d_out: blocked
+ * compression (Sec. 3.3) with, per block, the minimum and base of Sec. 3.1
+ * (Fig. 2's block header) and the packing of Eq. 2 (basic, Sec. 3.1) or of
+ * the split-base series (advanced, Sec. 3.2).
  *   d_in           device pointer, 16-byte aligned (may be NULL if n_samples = 0)
  *   d_out          device pointer, 16-byte aligned, out_capacity bytes; must be
  *                  at least pc_bound(params, n_samples) (else PC_ERR_CAPACITY)
@@ -122,7 +125,13 @@ pc_status pc_compress(const void *d_in, uint64_t n_samples, const pc_params *par
                       void *d_workspace, uint64_t workspace_bytes, pc_stream_t stream);
 
 /* Decompress the stream of in_bytes bytes at device memory d_in into device
- * memory d_out (uint16 or uint32 samples).
+ * memory d_out (uint16 or uint32 samples): the inverse of the packing by
+ * repeated division by B, Sec. 3.1 ("polynomial division"), and, for the
+ * advanced variant, by the split bases R_i of Sec. 3.2.  The params argument
+ * is this library's addition to the boundary: it selects the kernel
+ * instantiation on the host without reading the stream's header back from
+ * the device (which would synchronise the stream); the device checks it
+ * against the header.
  *   params         the parameters the stream was written with; the device
  *                  checks that the header matches them (else PC_ERR_CORRUPT)
  *   d_in           device pointer, 16-byte aligned
@@ -338,9 +347,14 @@ pc_status pc_compress_segments(const pc_segments_info *info, const void *d_plan,
  * library.  Same arguments, checks and output as pc_compress, but the
  * workspace is a static device array of PC_NOALLOC_SCRATCH_BYTES bytes inside
  * libpc.so, held by every GPU that loads the library until the process exits.
- *   - n_samples whose pc_workspace_size exceeds PC_NOALLOC_SCRATCH_BYTES is
- *     rejected with PC_ERR_UNSUPPORTED (1 MiB: about 131,000 tiles, e.g.
- *     4.29e9 uint16 samples with block_len 1024, basic variant);
+ *   - the call needs the look-back part of the workspace only (the header,
+ *     one 8-byte word per tile and the decoding offsets pc_workspace_size
+ *     also counts, without the advanced variant's series table); where that
+ *     exceeds PC_NOALLOC_SCRATCH_BYTES the call returns PC_ERR_UNSUPPORTED
+ *     before touching the device.  With 1 MiB that allows about 2.1e9 uint16
+ *     samples at block_len 1024 (basic or advanced), 5.4e8 at block_len 256;
+ *   - advanced streams compress with the serial series walk of each block
+ *     (the series table does not fit the scratch): the same bytes, slower;
  *   - the first call on a device looks up the array's device address with
  *     cudaGetSymbolAddress (with that device current); make that first call
  *     before any stream capture;

@@ -316,3 +316,118 @@ def test_exhaustive_labels_pick_the_smallest_stream():
     lab, sizes = mlp.labels(x, 1)
     assert (sizes[np.arange(3), lab] == sizes.min(axis=1)).all()
     assert mlp.option_params(int(lab[1]))[0] < 4096
+
+
+def _read_mlp_golden(path):
+    from oracle import mlp
+
+    P = {k: np.zeros(mlp.SHAPES[k]) for k in mlp.NAMES}
+    X = np.zeros((2, 24))
+    Z = np.zeros((2, 12))
+    with open(path) as f:
+        for line in f:
+            t = line.split()
+            if not t or t[0].startswith("#"):
+                continue
+            idx = tuple(int(v) for v in t[1:-1])
+            target = {"X": X, "Z": Z}.get(t[0], P.get(t[0]))
+            target[idx] = float(t[-1])
+    return P, X, Z
+
+
+def test_mlp_oracle_forward_worked_example(golden_dir):
+    """oracle.mlp.forward on a hand-worked network (golden file with the
+    arithmetic): one ReLU clips in each hidden layer, W2 is asymmetric so a
+    transposed operand changes a logit, and b3 is non-zero.  loss_grad's own
+    forward pass must give the same logits (its loss at uniform labels)."""
+    from oracle import mlp
+
+    P, X, Z = _read_mlp_golden(os.path.join(golden_dir, "mlp_forward_worked_example.txt"))
+    got = mlp.forward(P, X)
+    assert np.array_equal(got, Z), got
+    # loss_grad runs its own forward pass: its loss must be the cross-entropy of these logits
+    y = np.array([1, 0])
+    loss, _ = mlp.loss_grad(P, X, y)
+    lse = [np.log(np.sum(np.exp(Z[r]))) for r in range(2)]
+    assert abs(loss - np.mean([lse[0] - 5.25, lse[1] - 21.5])) < 1e-12
+
+
+def test_mlp_oracle_loss_special_cases():
+    """Softmax cross-entropy facts that do not depend on how it is written:
+    with all logits equal the loss is ln 12 and dL/db3 = mean(1/12 - onehot(y));
+    with one logit 20 above the other eleven the loss is ln(1 + 11 e^-20) at
+    that option and 20 + ln(1 + 11 e^-20) at another."""
+    from oracle import mlp
+
+    rng = np.random.default_rng(5)
+    P = {k: rng.normal(0, 0.3, mlp.SHAPES[k]) for k in mlp.NAMES}
+    P["W3"][:] = 0.0
+    P["b3"][:] = 0.0
+    X = rng.uniform(0, 1, (5, 24))
+    y = np.array([0, 3, 3, 11, 6])
+    loss, G = mlp.loss_grad(P, X, y)
+    assert abs(loss - np.log(12.0)) < 1e-14
+    want = np.full(12, 1.0 / 12.0)
+    for v in y:
+        want[v] -= 1.0 / 5.0
+    assert np.allclose(G["b3"], want, atol=1e-15, rtol=0)
+    assert np.all(G["W2"] == 0) and np.all(G["W1"] == 0)  # nothing flows back through W3 = 0
+    P["b3"][4] = 20.0
+    tail = 11.0 * np.exp(-20.0)  # ln(1 + t) = t - t^2 / 2 + ...
+    loss, _ = mlp.loss_grad(P, X[:1], np.array([4]))
+    assert abs(loss - (tail - tail * tail / 2)) < 1e-6 * tail
+    loss, _ = mlp.loss_grad(P, X[:1], np.array([2]))
+    assert abs(loss - (20.0 + tail)) < 1e-12
+
+
+def test_mlp_oracle_variance_and_spike_features():
+    """Feature 20 (log2(variance + 1) / 2d) and feature 21 (fraction of the
+    32 sub-blocks whose range exceeds 4 (smallest range + 1)) where they are
+    not zero, on segments whose statistics are known exactly."""
+    from oracle import mlp
+
+    # alternating v, v + 2: mean v + 1, variance exactly 1; every sub-block range 2
+    a = np.tile(np.array([700, 702], np.uint16), 2048)
+    f = mlp.features(a, 16)[0]
+    assert f[20] == 1.0 / 32.0  # log2(1 + 1) / (2 * 16)
+    assert f[21] == 0.0  # 2 <= 4 * (2 + 1)
+    assert f[3 + 1] == 1.0 and abs(f[2] - np.log2(3.0) / 16) < 1e-15 and f[19] == 701 / 65535
+    # 31 flat sub-blocks and one with range 100: one spike (100 > 4 * (0 + 1))
+    s = np.full(4096, 500, np.uint16)
+    s[7 * 128 + 40] = 600
+    f = mlp.features(s, 16)[0]
+    assert f[21] == 1.0 / 32.0
+    assert f[3] == 31.0 / 32.0 and f[3 + 6] == 1.0 / 32.0  # floor(log2(101)) = 6
+    q = 1.0 / 4096.0  # one sample 100 above the rest: Bernoulli variance 100^2 q (1 - q)
+    assert abs(f[20] - np.log2(1e4 * q * (1 - q) + 1.0) / 32.0) < 1e-14
+    # the threshold is strict and scales with (smallest range + 1): smallest range 2 -> threshold 12
+    t = np.tile(np.array([1000, 1002], np.uint16), 2048)
+    t[3 * 128 + 10] = 1012  # range 12: not a spike
+    t[5 * 128 + 10] = 1013  # range 13: a spike
+    t[9 * 128 + 11] = 1001  # still range 2
+    f = mlp.features(t, 16)[0]
+    assert f[21] == 1.0 / 32.0
+    # 32-bit samples: d = 32 in the variance's scale and in feature 22
+    f = mlp.features(a.astype(np.uint32), 32)[0]
+    assert f[20] == 1.0 / 64.0 and f[22] == 1.0
+
+
+def test_exhaustive_label_sizes_follow_the_closed_form():
+    """The oracle's per-option sizes, on segments whose blocks all have
+    B = 16, equal the closed-form basic stream length of each option's
+    (block length, word size): option o = 2 i + j is block length 128 << i
+    with 32-bit (j = 0) or 64-bit (j = 1) words, p = 7 (w = 32) or 15
+    (w = 64) digits per word.  A swapped option map or a wrong variant fails."""
+    from oracle import mlp
+
+    rng = np.random.default_rng(9)
+    seg = rng.integers(0, 16, 4096 * 2).astype(np.uint16)
+    seg[::128] = 0
+    seg[1::128] = 15  # every block of every option has min 0 and max 15
+    _, sizes = mlp.labels(seg, 0)
+    for o in range(12):
+        L, w = 128 << (o // 2), 32 if o % 2 == 0 else 64
+        p = 7 if w == 32 else 15
+        nb = 4096 // L
+        want = 64 + (nb * 4 + 15) // 16 * 16 + nb * (-(-L // p)) * (w // 8)
+        assert sizes[0, o] == want and sizes[1, o] == want, (o, sizes[0, o], want)

@@ -38,10 +38,38 @@ def test_noalloc_matches_pc_compress_on_consecutive_calls():
         assert torch.equal(out[:k], ref[:k])
 
 
-def test_noalloc_rejects_streams_beyond_its_scratch():
-    p = native.params(native.BASIC, 16, 64, 1)  # one block per sample: many tiles
-    too_many = 40_000_000
-    assert native.workspace_size(p, too_many) > native.NOALLOC_SCRATCH_BYTES
-    fake = 1 << 40  # never dereferenced: the size check comes first
-    st = native.compress_noalloc_raw(fake, too_many, p, fake, native.bound(p, too_many), fake, None)
-    assert st == native.PC_ERR_UNSUPPORTED
+def test_noalloc_near_its_scratch_limit_matches_pc_compress():
+    """A basic uint16 stream at block_len 256 sized a few tiles under the
+    scratch limit, so that the look-back words fill almost all of the static
+    array: the same bytes as pc_compress, and it decodes back exactly."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1805_01844_gb300 as pc
+
+    dev = torch.device("cuda:0")
+    stream = torch.cuda.current_stream(dev).cuda_stream
+    p = native.params(pc.BASIC, 16, 32, 256)
+    lo, hi = 0, 1 << 32
+    while hi - lo > 1:
+        m = (lo + hi) // 2
+        if native.workspace_size(p, m) <= native.NOALLOC_SCRATCH_BYTES:
+            lo = m
+        else:
+            hi = m
+    n = lo - 256 * 40 - 77  # ragged last block, a few tiles under the limit
+    assert native.workspace_size(p, n) > native.NOALLOC_SCRATCH_BYTES * 0.99
+    x = datagen.white_noise_torch(n, dev, 300.0, 5.0, seed=3)
+    codec = pc.Codec(pc.BASIC, 16, 32, 256, max_samples=n, device=dev)
+    ref, ref_n = codec.compress(x)
+    assert codec.device_status() == native.PC_OK
+    out = torch.full((native.bound(p, n),), 0x5A, dtype=torch.uint8, device=dev)
+    nbytes = torch.zeros(1, dtype=torch.int64, device=dev)
+    st = native.compress_noalloc_raw(x.data_ptr(), n, p, out.data_ptr(), out.numel(), nbytes.data_ptr(), stream)
+    assert st == native.PC_OK, native.strerror(st)
+    torch.cuda.synchronize()
+    k = int(ref_n.item())
+    assert int(nbytes.item()) == k
+    assert torch.equal(out[:k], ref[:k])
+    y, n_out = codec.decompress(out, k, n)
+    assert codec.device_status() == native.PC_OK
+    assert int(n_out.item()) == n and torch.equal(y[:n], x)
