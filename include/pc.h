@@ -339,6 +339,85 @@ pc_status pc_segments_features(const pc_segments_info *info, const void *d_plan,
 pc_status pc_compress_segments(const pc_segments_info *info, const void *d_plan, const uint8_t *d_options,
                                void *d_workspace, uint64_t workspace_bytes, pc_stream_t stream);
 
+/* ---- sharding: one stream split into block-aligned shards and stitched --
+ * Blocks are independent (Sec. 3.3, blocked compression), and a block's word
+ * count is a function of its table entry alone, so a stream is "readable by
+ * part" (Sec. 4.3).  One stream of n_samples can therefore be compressed as
+ * K shards of whole blocks (one per GPU, or several on one GPU), each an
+ * ordinary stream from pc_compress, and stitched into exactly the bytes a
+ * single pc_compress call would write:
+ *   pc_shard_range    host: the block-aligned sample range of shard k
+ *   (exchange)        every shard's stream size, 8 bytes per shard, gathered
+ *                     to wherever stitching runs (an all-gather across ranks)
+ *   pc_stitch         device: shard k's table entries and payload copied to
+ *                     their place in the whole stream (the exclusive prefix of
+ *                     the shards' payload sizes), plus the header (shard 0)
+ *                     and the table padding and total size (shard K - 1)
+ *   pc_stitch_layout  host: the same placement as byte ranges, for callers
+ *                     that move the pieces themselves (a collective, a file)
+ * The inverse, pc_slice, cuts the stream of a block range back out of a whole
+ * stream (a scan of the table gives the range's payload offset), so each rank
+ * decompresses its own blocks with pc_decompress. */
+typedef struct {
+    uint64_t total_bytes;    /* size of the whole stream */
+    uint64_t first_block;    /* shard's blocks: [first_block, first_block + n_blocks) */
+    uint64_t n_blocks;
+    uint64_t table_src;      /* shard's table entries: shard stream bytes [table_src, + table_bytes) */
+    uint64_t table_dst;      /*   go to whole-stream bytes [table_dst, + table_bytes) */
+    uint64_t table_bytes;
+    uint64_t payload_src;    /* shard's payload: [payload_src, + payload_bytes) */
+    uint64_t payload_dst;    /*   goes to [payload_dst, + payload_bytes) */
+    uint64_t payload_bytes;
+    uint64_t pad_dst;        /* the whole stream's table padding, zeros: [pad_dst, payload start) */
+    uint64_t payload_start;  /* offset of the whole stream's payload */
+} pc_stitch_region;
+
+/* Shard `shard` of n_shards of a stream of n_samples with *params: whole
+ * blocks, the first n_blocks % n_shards shards one block more than the rest.
+ * *first_sample = its first sample, *n_shard_samples its length (0 for a
+ * shard without blocks).  Host only.  PC_ERR_INVALID_ARG for n_shards = 0,
+ * shard >= n_shards, NULL outputs or bad params. */
+pc_status pc_shard_range(const pc_params *params, uint64_t n_samples, uint32_t n_shards, uint32_t shard,
+                         uint64_t *first_sample, uint64_t *n_shard_samples);
+
+/* Where shard `shard`'s pieces go in the whole stream, given every shard's
+ * stream size shard_bytes[n_shards] (host memory).  Host only.
+ * PC_ERR_CORRUPT if a size cannot be a stream of its shard's blocks. */
+pc_status pc_stitch_layout(const pc_params *params, uint64_t n_samples, uint32_t n_shards, uint32_t shard,
+                           const uint64_t *shard_bytes, pc_stitch_region *region);
+
+/* Copy shard `shard`'s stream d_shard (as pc_compress wrote it for the
+ * samples of pc_shard_range) into its place in the whole stream at d_out.
+ *   d_shard_bytes  device, [n_shards]: every shard's stream size (what each
+ *                  pc_compress wrote to its d_out_bytes, gathered)
+ *   d_out          device, 16-byte aligned, out_capacity >= pc_bound(params,
+ *                  n_samples) (else PC_ERR_CAPACITY); the calls of all shards
+ *                  with one d_out write disjoint bytes and together the whole
+ *                  stream, in any order, on any streams
+ *   d_out_bytes    device, one uint64_t: the whole stream's size, written by
+ *                  the call of shard n_shards - 1 (may be NULL for the others)
+ *   d_workspace    device, >= 64 bytes, 16-byte aligned: status word, read
+ *                  with pc_last_device_status (PC_ERR_CORRUPT if the shard
+ *                  stream's header or a size does not match its shard)
+ * One kernel, no look-back, no allocation. */
+pc_status pc_stitch(const void *d_shard, const uint64_t *d_shard_bytes, uint32_t n_shards, uint32_t shard,
+                    uint64_t n_samples, const pc_params *params, void *d_out, uint64_t out_capacity,
+                    uint64_t *d_out_bytes, void *d_workspace, uint64_t workspace_bytes, pc_stream_t stream);
+
+/* The stream of blocks [first_block, first_block + n_blocks) of the whole
+ * stream d_in (in_bytes bytes, written with *params): a header for those
+ * samples, their table entries and their payload words, i.e. exactly what
+ * pc_compress writes for those samples.  Two kernels: the word counts of the
+ * blocks before and inside the range from the table (a reduction), then the
+ * copy.  d_out: 16-byte aligned, out_capacity >= pc_bound(params, n_blocks *
+ * block_len) (else PC_ERR_CAPACITY); d_out_bytes: device, its size;
+ * d_workspace: >= 64 bytes, 16-byte aligned (pc_last_device_status:
+ * PC_ERR_CORRUPT for a bad header, table entry or payload shorter than the
+ * table implies; PC_ERR_INVALID_ARG for a range past the last block). */
+pc_status pc_slice(const void *d_in, uint64_t in_bytes, const pc_params *params, uint64_t first_block,
+                   uint64_t n_blocks, void *d_out, uint64_t out_capacity, uint64_t *d_out_bytes,
+                   void *d_workspace, uint64_t workspace_bytes, pc_stream_t stream);
+
 /* Compression without any device allocation, for callers that cannot
  * allocate device memory once they run: a data-acquisition loop that must not
  * call cudaMalloc mid-readout (it can fail under memory pressure or

@@ -464,3 +464,52 @@ PCX_HD uint32_t magic_div(uint32_t x, Magic32 mg)
 }
 
 }  // namespace pcx
+
+namespace pcx {
+
+// ---- sharding (Sec. 3.3: blocks are independent) -------------------------
+// Shard k of K of n_blocks blocks: the first n_blocks % K shards get one
+// block more than the others.
+PCX_HD void shard_blocks(uint64_t n_blocks, uint32_t K, uint32_t k, uint64_t &first, uint64_t &count)
+{
+    const uint64_t q = n_blocks / K, r = n_blocks % K;
+    first = (uint64_t)k * q + (k < r ? (uint64_t)k : r);
+    count = q + (k < r ? 1u : 0u);
+}
+
+// Placement of shard k's pieces in the whole stream from every shard's stream
+// size (host or device memory): the exclusive prefix of the shards' payload
+// words.  Returns PC_OK, or PC_ERR_CORRUPT if a size is not a header, a table
+// of that shard's blocks and whole words.
+PCX_HD uint32_t stitch_region(uint32_t d, uint32_t w, uint32_t L, uint64_t n, uint32_t K, uint32_t k,
+                              const uint64_t *shard_bytes, pc_stitch_region &r)
+{
+    const uint64_t NB = ceil_div(n, L), E = 2u * (d / 8u), WBY = w / 8u;
+    uint64_t before = 0, total = 0, mine = 0;
+    for (uint32_t j = 0; j < K; ++j) {
+        uint64_t f, c;
+        shard_blocks(NB, K, j, f, c);
+        const uint64_t head = PC_HEADER_BYTES + table_bytes(c, d), sz = shard_bytes[j];
+        if (sz < head || (sz - head) % WBY != 0) return PC_ERR_CORRUPT;
+        const uint64_t pw = (sz - head) / WBY;
+        if (j < k) before += pw;
+        if (j == k) mine = pw;
+        total += pw;
+    }
+    uint64_t first, count;
+    shard_blocks(NB, K, k, first, count);
+    r.first_block = first;
+    r.n_blocks = count;
+    r.payload_start = PC_HEADER_BYTES + table_bytes(NB, d);
+    r.total_bytes = r.payload_start + total * WBY;
+    r.table_src = PC_HEADER_BYTES;
+    r.table_dst = PC_HEADER_BYTES + first * E;
+    r.table_bytes = count * E;
+    r.payload_src = PC_HEADER_BYTES + table_bytes(count, d);
+    r.payload_dst = r.payload_start + before * WBY;
+    r.payload_bytes = mine * WBY;
+    r.pad_dst = PC_HEADER_BYTES + NB * E;
+    return PC_OK;
+}
+
+}  // namespace pcx

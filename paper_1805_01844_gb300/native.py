@@ -21,7 +21,8 @@ EXPORTS = ("pc_bound", "pc_workspace_size", "pc_compress", "pc_decompress",
            "pc_parse_header", "pc_last_device_status", "pc_selftest_bounded_wait",
            "pc_strerror", "pc_compress_noalloc", "pc_batch_describe", "pc_batch_plan",
            "pc_compress_batch", "pc_segment_features", "pc_mlp_forward", "pc_mlp_grad", "pc_mlp_adam",
-           "pc_segments_describe", "pc_segments_plan", "pc_segments_features", "pc_compress_segments")
+           "pc_segments_describe", "pc_segments_plan", "pc_segments_features", "pc_compress_segments",
+           "pc_shard_range", "pc_stitch_layout", "pc_stitch", "pc_slice")
 SEGMENT_SAMPLES, CHOOSER_FEATURES, CHOOSER_OPTIONS = 4096, 24, 12
 MLP_PARAMS, MLP_WEIGHT_BYTES = 6540, 13360
 NOALLOC_SCRATCH_BYTES = 1 << 20
@@ -60,6 +61,15 @@ class PcSegmentsInfo(ctypes.Structure):
                 ("smem_bytes", ctypes.c_uint32), ("has_totals", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
                 ("n_segments", ctypes.c_uint64), ("seg_stride", ctypes.c_uint64),
                 ("plan_bytes", ctypes.c_uint64), ("workspace_bytes", ctypes.c_uint64)]
+
+
+class PcStitchRegion(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_uint64) for name in (
+        "total_bytes", "first_block", "n_blocks", "table_src", "table_dst", "table_bytes",
+        "payload_src", "payload_dst", "payload_bytes", "pad_dst", "payload_start")]
+
+    def as_dict(self):
+        return {name: int(getattr(self, name)) for name, _ in self._fields_}
 
 
 class PcError(RuntimeError):
@@ -128,6 +138,15 @@ def load(path=LIB_PATH):
     L.pc_segments_features.restype = st
     L.pc_compress_segments.argtypes = [gp, vp, vp, vp, u64, vp]
     L.pc_compress_segments.restype = st
+    rp = ctypes.POINTER(PcStitchRegion)
+    L.pc_shard_range.argtypes = [pp, u64, u32, u32, u64p, u64p]
+    L.pc_shard_range.restype = st
+    L.pc_stitch_layout.argtypes = [pp, u64, u32, u32, u64p, rp]
+    L.pc_stitch_layout.restype = st
+    L.pc_stitch.argtypes = [vp, vp, u32, u32, u64, pp, vp, u64, vp, vp, u64, vp]
+    L.pc_stitch.restype = st
+    L.pc_slice.argtypes = [vp, u64, pp, u64, u64, vp, u64, vp, vp, u64, vp]
+    L.pc_slice.restype = st
     L.pc_strerror.argtypes = [st]
     L.pc_strerror.restype = ctypes.c_char_p
     _lib = L
@@ -246,3 +265,34 @@ def segment_stride(dtype_bits, variant):
     _, info = segments_describe([src], dtype_bits, variant)
     return info.seg_stride
 
+
+
+def shard_range(p, n_samples, n_shards, shard):
+    """(first sample, sample count) of block-aligned shard `shard` of `n_shards`."""
+    f, c = ctypes.c_uint64(0), ctypes.c_uint64(0)
+    _check(load().pc_shard_range(ctypes.byref(p), int(n_samples), int(n_shards), int(shard), ctypes.byref(f),
+                                 ctypes.byref(c)), "pc_shard_range")
+    return int(f.value), int(c.value)
+
+
+def stitch_layout(p, n_samples, n_shards, shard, shard_bytes):
+    """Placement of shard `shard` in the whole stream (dict of byte offsets),
+    from every shard's stream size (host integers)."""
+    arr = (ctypes.c_uint64 * int(n_shards))(*[int(b) for b in shard_bytes])
+    r = PcStitchRegion()
+    _check(load().pc_stitch_layout(ctypes.byref(p), int(n_samples), int(n_shards), int(shard), arr,
+                                   ctypes.byref(r)), "pc_stitch_layout")
+    return r.as_dict()
+
+
+def stitch_raw(d_shard, d_shard_bytes, n_shards, shard, n_samples, p, d_out, out_capacity, d_out_bytes, d_ws,
+               ws_bytes, stream):
+    """pc_stitch on raw device addresses; returns the host status."""
+    return load().pc_stitch(d_shard, d_shard_bytes, int(n_shards), int(shard), int(n_samples), ctypes.byref(p),
+                            d_out, int(out_capacity), d_out_bytes or None, d_ws, int(ws_bytes), stream or None)
+
+
+def slice_raw(d_in, in_bytes, p, first_block, n_blocks, d_out, out_capacity, d_out_bytes, d_ws, ws_bytes, stream):
+    """pc_slice on raw device addresses; returns the host status."""
+    return load().pc_slice(d_in, int(in_bytes), ctypes.byref(p), int(first_block), int(n_blocks), d_out,
+                           int(out_capacity), d_out_bytes, d_ws, int(ws_bytes), stream or None)
