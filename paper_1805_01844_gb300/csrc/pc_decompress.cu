@@ -710,6 +710,10 @@ __device__ __forceinline__ bool decode_basic_group(const typename WordT<T, WB>::
     return bad;
 }
 
+#ifndef PCX_DEC_TAIL3
+#define PCX_DEC_TAIL3 1
+#endif
+
 // Basic words [jb, je) of one block by one warp (src holds them from word jb
 // on): groups of 128 words (four per lane in lockstep), then the rest 32 at
 // a time, so W words cost ceil(W / 32) lane slots rather than a multiple of 4.
@@ -725,6 +729,14 @@ __device__ __forceinline__ bool decode_basic_block(const typename WordT<T, WB>::
     uint32_t j0 = jb;
     for (; j0 + 128 <= je; j0 += 128)
         bad |= decode_basic_group<T, WB, 4, true>(src, jb, ua, junka, j0, je, p, hstar, B, vmin, mg, Dh, MD);
+#if PCX_DEC_TAIL3
+    // 65-96 words left (a block of white noise, L = 1024, w = 64, has ~86):
+    // three words per lane in lockstep instead of three one-word rounds
+    if (je - j0 > 64 && je - j0 <= 96) {
+        bad |= decode_basic_group<T, WB, 3>(src, jb, ua, junka, j0, je, p, hstar, B, vmin, mg, Dh, MD);
+        return bad;
+    }
+#endif
     for (; j0 < je; j0 += 32)
         bad |= decode_basic_group<T, WB, 1>(src, jb, ua, junka, j0, je, p, hstar, B, vmin, mg, Dh, MD);
     return bad;
