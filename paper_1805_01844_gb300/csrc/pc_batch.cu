@@ -227,6 +227,7 @@ __device__ void seg_warp(const T *__restrict__ in, uint32_t n, uint32_t L, uint8
     // 3. lane b: block b's count (Eq. 1-2, or the series table of Sec. 3.2)
     uint32_t W = 0, p = 0, p1 = 0, vmin = 0;
     uint64_t B = 1, K = 0, K2 = 0;
+    PackK pk{0u, 0u, 0u, 0u};
     OrbitView v{};
     if (lane < nblk) {
         B = s_B[lane];
@@ -234,10 +235,9 @@ __device__ void seg_warp(const T *__restrict__ in, uint32_t n, uint32_t L, uint8
         const uint32_t n_b = min(L, n - lane * L);
         if (B > 1) {
             if constexpr (VAR == PC_VARIANT_BASIC) {
-                uint64_t geo;
-                p = basic_p_geo(B, WB, geo);
+                p = basic_p(B, WB);
                 W = (n_b + p - 1) / p;
-                K = geo * vmin;
+                pk = basic_pack_k(B, p, vmin, WB);
             } else {
                 const uint64_t h = orbit_get<WB>(ot, (uint32_t)B, L, ws, limit_ns);  // B <= 65536 for 16-bit data
                 if (h != ~0ull) {
@@ -282,7 +282,9 @@ __device__ void seg_warp(const T *__restrict__ in, uint32_t n, uint32_t L, uint8
         const T *u = reinterpret_cast<const T *>(stage + b * S);
         if (Wb == 0) continue;
         if constexpr (VAR == PC_VARIANT_BASIC) {
-            pack_basic_block<T, WB>(u, Wb, __shfl_sync(0xFFFFFFFFu, p, b), B32, Kb, payload + ob);
+            const PackK pkb{__shfl_sync(0xFFFFFFFFu, pk.D, b), __shfl_sync(0xFFFFFFFFu, pk.Kf, b),
+                            __shfl_sync(0xFFFFFFFFu, pk.Kt, b), __shfl_sync(0xFFFFFFFFu, pk.shape, b)};
+            pack_basic_block<T, WB>(u, Wb, __shfl_sync(0xFFFFFFFFu, p, b), B32, pkb, payload + ob);
         } else {
             OrbitView vb;
             vb.off = __shfl_sync(0xFFFFFFFFu, v.off, b);

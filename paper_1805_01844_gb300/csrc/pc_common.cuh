@@ -151,15 +151,61 @@ struct TileCfg {
     uint32_t smem;        // total dynamic shared memory
 };
 
+// Basic words as 32-bit pieces (compression): a word of p digits is
+// np = ceil(p / p32) pieces of p32 digits, p32 = max{k : B^k <= 2^32 - 1},
+// the top one of t = p - (np - 1) p32 digits, so that each piece is a 32-bit
+// Horner sum and s = ((top D + piece_{np-2}) D + ...) D + piece_0 with
+// D = B^p32.  Pieces are summed over raw samples, so each subtracts
+// vmin (1 + B + ... + B^(len-1)) mod 2^32: Kf for a full piece, Kt for the
+// top one (the true piece is below 2^32, so the difference mod 2^32 is exact).
+// 32-bit words (and B = 2^32) have one piece: p32 = t = p, np = 1.
+struct PackK {
+    uint32_t D, Kf, Kt;
+    uint32_t shape;  // p32 | np << 8 | t << 16
+};
+
+PCX_HD PackK basic_pack_k(uint64_t B, uint32_t p, uint32_t vmin, uint32_t w)
+{
+    PackK r{0u, 0u, 0u, 0u};
+    uint32_t p32 = p, np = 1, t = p;
+    if (w == 64 && B <= 0xFFFFFFFFull) {
+        uint64_t pw = 1;
+        uint32_t g = 0;
+        p32 = 0;
+        while (pw * B <= 0xFFFFFFFFull) {  // pw <= 2^32 - 1 and B < 2^32: no overflow
+            g += (uint32_t)pw;
+            pw *= B;
+            ++p32;
+        }
+        r.D = (uint32_t)pw;
+        r.Kf = vmin * g;
+        np = (p + p32 - 1) / p32;
+        t = p - (np - 1) * p32;
+    }
+    uint32_t g = 0, pw = 1;  // 1 + B + ... + B^(t-1) mod 2^32
+    for (uint32_t i = 0; i < t; ++i) {
+        g += pw;
+        pw *= (uint32_t)B;
+    }
+    r.Kt = vmin * g;
+    r.shape = p32 | (np << 8) | (t << 16);
+    return r;
+}
+
 struct BlockVars {        // per-tile arrays in shared memory
     uint64_t B[kMaxTileBlocks];
     uint32_t vmin[kMaxTileBlocks];
     uint32_t W[kMaxTileBlocks];
     uint32_t woff[kMaxTileBlocks];
     uint32_t p[kMaxTileBlocks];
-    // decoding only: per-block division constants (see k_decode)
-    uint64_t Dh[kMaxTileBlocks];   // B^h*, the largest power of B <= 2^32
-    uint64_t MD[kMaxTileBlocks];   // floor((2^64 - 1) / Dh)
+    union {
+        // decoding only: per-block division constants (see k_decode)
+        struct {
+            uint64_t Dh[kMaxTileBlocks];  // B^h*, the largest power of B <= 2^32
+            uint64_t MD[kMaxTileBlocks];  // floor((2^64 - 1) / Dh)
+        } dec;
+        PackK pk[kMaxTileBlocks];  // compression, basic variant: the 32-bit pieces of its words
+    };
     uint32_t mg_m[kMaxTileBlocks]; // magic reciprocal of B (Magic32)
     uint32_t mg_a[kMaxTileBlocks];
     uint32_t mg_s[kMaxTileBlocks];

@@ -39,59 +39,6 @@ __device__ __forceinline__ void mad64(uint32_t &lo, uint32_t &hi, uint32_t m, ui
     lo = (uint32_t)t;
 }
 
-// Eq. 2, word j of a block: s_j = sum_{i<p} u[j p + i] B^i with u = v - vmin.
-// Evaluated by Horner from the highest digit on the raw samples v, modulo
-// 2^w, minus K = vmin (1 + B + ... + B^(p-1)) mod 2^w: the difference is the
-// true s_j, which is < 2^w.  Padding samples hold vmin, i.e. digit 0.
-template <typename T, uint32_t WB, uint32_t P>
-__device__ __forceinline__ typename WordOf<T, WB>::type horner_k(const T *dg, uint32_t B32)
-{
-    if constexpr (WB == 32) {
-        uint32_t acc = dg[P - 1];
-#pragma unroll
-        for (int k = (int)P - 2; k >= 0; --k) acc = acc * B32 + (uint32_t)dg[k];
-        return acc;
-    } else {
-        uint32_t lo = dg[P - 1], hi = 0;
-#pragma unroll
-        for (int k = (int)P - 2; k >= 0; --k) mad64(lo, hi, B32, (uint32_t)dg[k]);
-        return ((uint64_t)hi << 32) | lo;
-    }
-}
-
-template <typename T, uint32_t WB>
-__device__ __forceinline__ typename WordOf<T, WB>::type
-basic_word(const T *dg, uint32_t p, uint32_t B32, uint64_t K)
-{
-    using Word = typename WordOf<T, WB>::type;
-    Word acc;
-    switch (p) {
-    case 1: acc = horner_k<T, WB, 1>(dg, B32); break;
-    case 2: acc = horner_k<T, WB, 2>(dg, B32); break;
-    case 3: acc = horner_k<T, WB, 3>(dg, B32); break;
-    case 4: acc = horner_k<T, WB, 4>(dg, B32); break;
-    case 5: acc = horner_k<T, WB, 5>(dg, B32); break;
-    case 6: acc = horner_k<T, WB, 6>(dg, B32); break;
-    case 7: acc = horner_k<T, WB, 7>(dg, B32); break;
-    case 8: acc = horner_k<T, WB, 8>(dg, B32); break;
-    case 9: acc = horner_k<T, WB, 9>(dg, B32); break;
-    case 10: acc = horner_k<T, WB, 10>(dg, B32); break;
-    case 11: acc = horner_k<T, WB, 11>(dg, B32); break;
-    case 12: acc = horner_k<T, WB, 12>(dg, B32); break;
-    default:
-        if constexpr (WB == 32) {
-            uint32_t a = dg[p - 1];
-            for (int k = (int)p - 2; k >= 0; --k) a = a * B32 + (uint32_t)dg[k];
-            acc = a;
-        } else {
-            uint32_t lo = dg[p - 1], hi = 0;
-            for (int k = (int)p - 2; k >= 0; --k) mad64(lo, hi, B32, (uint32_t)dg[k]);
-            acc = ((uint64_t)hi << 32) | lo;
-        }
-    }
-    return acc - (Word)K;
-}
-
 // Sec. 3.2, word i of a block:
 //   s_i = r_i + R_i (sum_{k=1}^{p_i} u_{q_i+k} B^{p_i-k} + r'_{i-1} B^{p_i})
 // with the split sample e = u[q_i + p_i], r_i = e mod R_i, and
@@ -229,11 +176,22 @@ __device__ __forceinline__ void adv_words_orbit(const OrbitTable &ot, const Orbi
 
 // Basic words j0 + lane + 32 k (k < NK) of one block by one warp, NK words
 // per lane in lockstep so that their Horner chains are independent for the
-// scheduler.  Lanes past the last word recompute the last word and do not
-// store it.
+// scheduler.  Each word is summed as 32-bit pieces (PackK): one 32-bit
+// multiply-add per digit, one 64-bit multiply-add per piece boundary.  Lanes
+// past the last word recompute the last word and do not store it.
+// 16x2 min/max in the multi-stage basic tiles (measured: +2 % on camera
+// events at L = 1024; in the single-stage tiles, whose short blocks run in
+// 128-thread CTAs, -15 % at L = 256)
+#ifndef PCX_MINMAX_U16X2
+#define PCX_MINMAX_U16X2 1
+#endif
+#ifndef PCX_PACK_UNROLL
+#define PCX_PACK_UNROLL 1
+#endif
+
 template <typename T, uint32_t WB, uint32_t NK, bool FULL = false>
 __device__ __forceinline__ void pack_basic_group(const T *u, uint32_t j0, uint32_t W, uint32_t p, uint32_t B32,
-                                                 uint64_t K, typename WordOf<T, WB>::type *dst)
+                                                 PackK pk, typename WordOf<T, WB>::type *dst)
 {
     using Word = typename WordOf<T, WB>::type;
     const uint32_t lane = threadIdx.x & 31u;
@@ -244,7 +202,7 @@ __device__ __forceinline__ void pack_basic_group(const T *u, uint32_t j0, uint32
         g[k] = u + j * p;
     }
     Word acc[NK];
-    if constexpr (WB == 32) {
+    if constexpr (WB == 32) {  // one piece
         uint32_t a[NK];
 #pragma unroll
         for (uint32_t k = 0; k < NK; ++k) a[k] = g[k][p - 1];
@@ -254,20 +212,42 @@ __device__ __forceinline__ void pack_basic_group(const T *u, uint32_t j0, uint32
             for (uint32_t k = 0; k < NK; ++k) a[k] = a[k] * B32 + (uint32_t)g[k][d];
         }
 #pragma unroll
-        for (uint32_t k = 0; k < NK; ++k) acc[k] = a[k] - (uint32_t)K;
+        for (uint32_t k = 0; k < NK; ++k) acc[k] = a[k] - pk.Kt;
     } else {
-        uint32_t lo[NK], hi[NK];
+        const int p32 = (int)(pk.shape & 0xFFu), t = (int)(pk.shape >> 16);
+        uint32_t a[NK], lo[NK], hi[NK];
+        // the top piece: digits p - 1 down to p - t
+        int d = (int)p - 1;
+#pragma unroll
+        for (uint32_t k = 0; k < NK; ++k) a[k] = g[k][d];
+#if PCX_PACK_UNROLL
+#pragma unroll 2
+#endif
+        for (--d; d >= (int)p - t; --d) {
+#pragma unroll
+            for (uint32_t k = 0; k < NK; ++k) a[k] = a[k] * B32 + (uint32_t)g[k][d];
+        }
 #pragma unroll
         for (uint32_t k = 0; k < NK; ++k) {
-            lo[k] = g[k][p - 1];
+            lo[k] = a[k] - pk.Kt;
             hi[k] = 0;
         }
-        for (int d = (int)p - 2; d >= 0; --d) {
+        // the lower pieces, p32 digits each: d is the top digit of the next one
+        for (; d >= 0; d -= p32) {
 #pragma unroll
-            for (uint32_t k = 0; k < NK; ++k) mad64(lo[k], hi[k], B32, (uint32_t)g[k][d]);
+            for (uint32_t k = 0; k < NK; ++k) a[k] = g[k][d];
+#if PCX_PACK_UNROLL
+#pragma unroll 2
+#endif
+            for (int e = d - 1; e > d - p32; --e) {
+#pragma unroll
+                for (uint32_t k = 0; k < NK; ++k) a[k] = a[k] * B32 + (uint32_t)g[k][e];
+            }
+#pragma unroll
+            for (uint32_t k = 0; k < NK; ++k) mad64(lo[k], hi[k], pk.D, a[k] - pk.Kf);
         }
 #pragma unroll
-        for (uint32_t k = 0; k < NK; ++k) acc[k] = (((uint64_t)hi[k] << 32) | lo[k]) - K;
+        for (uint32_t k = 0; k < NK; ++k) acc[k] = ((uint64_t)hi[k] << 32) | lo[k];
     }
 #pragma unroll
     for (uint32_t k = 0; k < NK; ++k) {
@@ -279,16 +259,16 @@ __device__ __forceinline__ void pack_basic_group(const T *u, uint32_t j0, uint32
 // Basic words of one block by one warp: groups of 128 words (four per lane),
 // then the last 1..127 words in the fewest lockstep slots per lane.
 template <typename T, uint32_t WB>
-__device__ __forceinline__ void pack_basic_block(const T *u, uint32_t W, uint32_t p, uint32_t B32, uint64_t K,
+__device__ __forceinline__ void pack_basic_block(const T *u, uint32_t W, uint32_t p, uint32_t B32, PackK pk,
                                                  typename WordOf<T, WB>::type *dst)
 {
     uint32_t j0 = 0;
-    for (; j0 + 128 <= W; j0 += 128) pack_basic_group<T, WB, 4, true>(u, j0, W, p, B32, K, dst);
+    for (; j0 + 128 <= W; j0 += 128) pack_basic_group<T, WB, 4, true>(u, j0, W, p, B32, pk, dst);
     const uint32_t rest = W - j0;
-    if (rest > 96) pack_basic_group<T, WB, 4>(u, j0, W, p, B32, K, dst);
-    else if (rest > 64) pack_basic_group<T, WB, 3>(u, j0, W, p, B32, K, dst);
-    else if (rest > 32) pack_basic_group<T, WB, 2>(u, j0, W, p, B32, K, dst);
-    else if (rest > 0) pack_basic_group<T, WB, 1>(u, j0, W, p, B32, K, dst);
+    if (rest > 96) pack_basic_group<T, WB, 4>(u, j0, W, p, B32, pk, dst);
+    else if (rest > 64) pack_basic_group<T, WB, 3>(u, j0, W, p, B32, pk, dst);
+    else if (rest > 32) pack_basic_group<T, WB, 2>(u, j0, W, p, B32, pk, dst);
+    else if (rest > 0) pack_basic_group<T, WB, 1>(u, j0, W, p, B32, pk, dst);
 }
 
 // The 64-byte stream header (format version 1, include/pc.h).
@@ -386,7 +366,8 @@ __device__ void compress_tile(const StreamArgs &sa, uint64_t tile, uint8_t *smem
         __syncwarp();
         for (uint32_t b = warp; b < nblk; b += (NT / 32)) {
             const uint32_t n_b = (uint32_t)umin64(L, cnt - (uint64_t)b * L);
-            block_minmax<T>(reinterpret_cast<T *>(smem + (uint64_t)b * cfg.stage_bytes), n_b, &bv.vmin[b], &bv.B[b]);
+            block_minmax<T>(reinterpret_cast<T *>(smem + (uint64_t)b * cfg.stage_bytes), n_b, &bv.vmin[b],
+                                                    &bv.B[b]);
         }
         __syncthreads();
     } else {
@@ -396,7 +377,8 @@ __device__ void compress_tile(const StreamArgs &sa, uint64_t tile, uint8_t *smem
         // 2. min / max per block
         for (uint32_t b = warp; b < nblk; b += (NT / 32)) {
             const uint32_t n_b = (uint32_t)umin64(L, cnt - (uint64_t)b * L);
-            block_minmax<T>(reinterpret_cast<T *>(smem + (uint64_t)b * cfg.stage_bytes), n_b, &bv.vmin[b], &bv.B[b]);
+            block_minmax<T>(reinterpret_cast<T *>(smem + (uint64_t)b * cfg.stage_bytes), n_b, &bv.vmin[b],
+                                                    &bv.B[b]);
         }
         __syncthreads();
     }
@@ -409,11 +391,10 @@ __device__ void compress_tile(const StreamArgs &sa, uint64_t tile, uint8_t *smem
             const uint32_t n_b = (uint32_t)umin64(L, cnt - (uint64_t)lane * L);
             if (B > 1) {
                 if constexpr (VAR == PC_VARIANT_BASIC) {
-                    uint64_t geo;  // 1 + B + ... + B^(p-1), mod 2^64
-                    const uint32_t p = basic_p_geo(B, WB, geo);
+                    const uint32_t p = basic_p(B, WB);
                     bv.p[lane] = p;
                     W = (n_b + p - 1) / p;
-                    bv.K[lane] = geo * bv.vmin[lane];
+                    bv.pk[lane] = basic_pack_k(B, p, bv.vmin[lane], WB);
                 } else if (ORB && B <= kOrbitMaxB) {
                     // the series from the table: O(1) per word
                     const uint64_t h = orbit_get<WB>(sa.ot, (uint32_t)B, L, ws, limit_ns);
@@ -485,7 +466,7 @@ __device__ void compress_tile(const StreamArgs &sa, uint64_t tile, uint8_t *smem
             const uint32_t B32 = (uint32_t)bv.B[b];  // B = 2^32 only with p = 1: never multiplies
             Word *dst = payload + bv.excl + bv.woff[b];
             if constexpr (VAR == PC_VARIANT_BASIC) {
-                pack_basic_block<T, WB>(u, W, bv.p[b], B32, bv.K[b], dst);
+                pack_basic_block<T, WB>(u, W, bv.p[b], B32, bv.pk[b], dst);
             } else {
                 if (ORB && bv.mode[b]) {
                     const OrbitView v{bv.orb_off[b], bv.orb_Q[b], bv.orb_P[b], bv.orb_SQ[b], bv.orb_G[b],
@@ -522,12 +503,11 @@ __device__ void compress_tile(const StreamArgs &sa, uint64_t tile, uint8_t *smem
 constexpr uint32_t kMultiMaxBlocks = 96;  // blocks of one look-back tile
 
 struct MultiVars {  // per-tile arrays, in the BlockVars space of the stage
-    uint64_t B[kMultiMaxBlocks];
-    uint64_t K[kMultiMaxBlocks];
+    PackK pk[kMultiMaxBlocks];     // the 32-bit pieces of the block's words; p in shape bits 24-31
+    uint32_t Bm1[kMultiMaxBlocks];  // B - 1
     uint32_t vmin[kMultiMaxBlocks];
     uint32_t W[kMultiMaxBlocks];
     uint32_t woff[kMultiMaxBlocks];
-    uint32_t p[kMultiMaxBlocks];
     uint64_t excl;
     uint32_t agg;
     uint32_t ok;
@@ -599,8 +579,11 @@ __device__ void compress_tile_multi(const StreamArgs &sa, uint64_t tile, uint8_t
     // 1-2. min / max, stage tile by stage tile over the same slots
     for (uint32_t h = 0; h < nst; ++h) {
         stage(h, h + 1 < nst);
-        for (uint32_t b = warp; b < nh(h); b += NW)
-            block_minmax<T>(slot(b), n_of(h * H + b), &mv.vmin[h * H + b], &mv.B[h * H + b]);
+        for (uint32_t b = warp; b < nh(h); b += NW) {
+            uint64_t Bb;
+            block_minmax<T, PCX_MINMAX_U16X2>(slot(b), n_of(h * H + b), &mv.vmin[h * H + b], &Bb);
+            if (lane == 0) mv.Bm1[h * H + b] = (uint32_t)(Bb - 1);
+        }
     }
     __syncthreads();
 
@@ -611,13 +594,13 @@ __device__ void compress_tile_multi(const StreamArgs &sa, uint64_t tile, uint8_t
             const uint32_t b = b0 + lane;
             uint32_t W = 0;
             if (b < nblk) {
-                const uint64_t B = mv.B[b];
+                const uint64_t B = (uint64_t)mv.Bm1[b] + 1;
                 if (B > 1) {
-                    uint64_t geo;  // 1 + B + ... + B^(p-1), mod 2^64
-                    const uint32_t p = basic_p_geo(B, WB, geo);
-                    mv.p[b] = p;
+                    const uint32_t p = basic_p(B, WB);
                     W = (n_of(b) + p - 1) / p;
-                    mv.K[b] = geo * mv.vmin[b];
+                    PackK pk = basic_pack_k(B, p, mv.vmin[b], WB);
+                    pk.shape |= p << 24;
+                    mv.pk[b] = pk;
                 }
                 mv.W[b] = W;
             }
@@ -643,7 +626,7 @@ __device__ void compress_tile_multi(const StreamArgs &sa, uint64_t tile, uint8_t
     if (mv.ok) {
         for (uint32_t b = threadIdx.x; b < nblk; b += NT) {
             const uint64_t gb = blk0 + b;
-            const uint64_t Bm1 = mv.B[b] - 1;
+            const uint64_t Bm1 = mv.Bm1[b];
             if constexpr (D == 16) {
                 reinterpret_cast<uint32_t *>(sa.out + PC_HEADER_BYTES)[gb] = mv.vmin[b] | ((uint32_t)Bm1 << 16);
             } else {
@@ -665,7 +648,10 @@ __device__ void compress_tile_multi(const StreamArgs &sa, uint64_t tile, uint8_t
                 const uint32_t bb = h * H + b;
                 const uint32_t W = mv.W[bb];
                 if (W == 0) continue;
-                pack_basic_block<T, WB>(slot(b), W, mv.p[bb], (uint32_t)mv.B[bb], mv.K[bb], payload + mv.woff[bb]);
+                PackK pk = mv.pk[bb];
+                const uint32_t p = pk.shape >> 24;
+                pk.shape &= 0xFFFFFFu;
+                pack_basic_block<T, WB>(slot(b), W, p, mv.Bm1[bb] + 1u, pk, payload + mv.woff[bb]);
             }
         }
         if (tile == n_tiles - 1) {

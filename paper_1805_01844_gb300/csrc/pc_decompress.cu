@@ -402,8 +402,8 @@ k_decode(const uint8_t *__restrict__ in, uint32_t L, T *__restrict__ out, uint64
                         ++hs;
                     }
                     bv.hstar[lane] = hs;
-                    bv.Dh[lane] = Dh;
-                    bv.MD[lane] = ~0ull / Dh;
+                    bv.dec.Dh[lane] = Dh;
+                    bv.dec.MD[lane] = ~0ull / Dh;
                     if constexpr (VAR == PC_VARIANT_BASIC) {
                         const uint32_t p = basic_p(B, WB);
                         bv.p[lane] = p;
@@ -457,7 +457,7 @@ k_decode(const uint8_t *__restrict__ in, uint32_t L, T *__restrict__ out, uint64
                 const uint32_t p = bv.p[b];
                 const Magic32 mg{bv.mg_m[b], bv.mg_a[b], bv.mg_s[b]};
                 const uint32_t hstar = bv.hstar[b];
-                const uint64_t Dh = bv.Dh[b], MD = bv.MD[b];
+                const uint64_t Dh = bv.dec.Dh[b], MD = bv.dec.MD[b];
                 // a full word is valid iff its top digit is < B; the last word's
                 // digits past the block (written to the padding) must be 0
                 for (uint32_t j0 = 0; j0 < W; j0 += 32 * KB) {
@@ -507,7 +507,7 @@ k_decode(const uint8_t *__restrict__ in, uint32_t L, T *__restrict__ out, uint64
                                   Magic32{bv.orb_mgm[b], bv.orb_mga[b], bv.orb_mgs[b]}};
                 const Magic32 mg{bv.mg_m[b], bv.mg_a[b], bv.mg_s[b]};
                 const uint32_t hstar = bv.hstar[b];
-                const uint64_t Dh = bv.Dh[b], MD = bv.MD[b];
+                const uint64_t Dh = bv.dec.Dh[b], MD = bv.dec.MD[b];
                 uint32_t cR = 1, cr = 0;  // carry: R and r of the word before this chunk
                 uint32_t qlast = 0, plast = 0;
                 for (uint32_t j0 = 0; j0 < W; j0 += 32) {

@@ -327,11 +327,28 @@ __device__ __forceinline__ void store_tile(T *__restrict__ out, uint64_t g0, uin
     }
 }
 
+// Two 16-bit lanes of a 32-bit register at once (sm_90 and later).
+__device__ __forceinline__ uint32_t min_u16x2(uint32_t a, uint32_t b)
+{
+    uint32_t d;
+    asm("min.u16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+
+__device__ __forceinline__ uint32_t max_u16x2(uint32_t a, uint32_t b)
+{
+    uint32_t d;
+    asm("max.u16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+
 // Sec. 3.1: minimum and maximum of one staged block, by one warp, with
 // 16-byte shared-memory reads, packed 16x2 min/max for uint16 samples and a
 // redux.sync reduction across the warp.  Then the kPad padding samples after
-// the block are set to the minimum (offset 0).
-template <typename T>
+// the block are set to the minimum (offset 0).  PACKED: uint16 pairs by the
+// 16x2 min/max instructions (basic-variant kernels); otherwise the two halves
+// of each 32-bit word are kept apart with plain 32-bit min/max.
+template <typename T, bool PACKED = false>
 __device__ __forceinline__ void block_minmax(T *blk, uint32_t n_b, uint32_t *vmin_out,
                                              uint64_t *B_out)
 {
@@ -340,7 +357,16 @@ __device__ __forceinline__ void block_minmax(T *blk, uint32_t n_b, uint32_t *vmi
     constexpr uint32_t VE = 16 / sizeof(T);
     const uint32_t nvec = n_b / VE;
     const uint4 *v4 = reinterpret_cast<const uint4 *>(blk);
-    if (sizeof(T) == 2) {
+    if (sizeof(T) == 2 && PACKED) {
+        uint32_t pmn = 0xFFFFFFFFu, pmx = 0;
+        for (uint32_t i = lane; i < nvec; i += 32) {
+            const uint4 x = v4[i];
+            pmn = min_u16x2(pmn, min_u16x2(min_u16x2(x.x, x.y), min_u16x2(x.z, x.w)));
+            pmx = max_u16x2(pmx, max_u16x2(max_u16x2(x.x, x.y), max_u16x2(x.z, x.w)));
+        }
+        mn = min(pmn & 0xFFFFu, pmn >> 16);
+        mx = max(pmx & 0xFFFFu, pmx >> 16);
+    } else if (sizeof(T) == 2) {
 #if PCX_MINMAX_PACKED
         uint32_t pmn = 0xFFFFFFFFu, pmx = 0;
         for (uint32_t i = lane; i < nvec; i += 32) {
