@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-cfg1", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-paper-sweeps", action="store_true")
     ap.add_argument("--serve-events", type=int, default=20000)
     return ap.parse_args()
 
@@ -416,6 +417,10 @@ def main():
     if not args.no_batch and rank == 0 and world == 1:
         batch = batch_metrics(dev)
 
+    paper = None
+    if not args.no_paper_sweeps and rank == 0 and world == 1:
+        paper = paper_sweeps(dev, x, sbuf, stream_bytes, L, w, args.variant)
+
     learned, trained = None, None
     if not args.no_learned and rank == 0 and world == 1:
         learned, trained = learned_vs_plain(dev)
@@ -444,10 +449,55 @@ def main():
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                      "alg_bytes_per_launch": alg_bytes, "traffic": recorded_traffic(key)},
         "cpu_baseline": cpu, "cpu_baseline_all_cores": cpu_all, "e2e": e2e, "gpu_launches": 3 * args.steps,
-        "white_noise_2e30": cfg1, "white_noise_65536": small, "batch": batch, "sweep": sweep, "learned": learned, "serving": serving,
+        "white_noise_2e30": cfg1, "white_noise_65536": small, "batch": batch, "sweep": sweep, "paper_sweeps": paper, "learned": learned, "serving": serving,
         "clocks": clk, "wall_s_timed": wall,
     }
     print(json.dumps(line), flush=True)
+
+
+def paper_sweeps(dev, x, sbuf, stream_bytes, L, w, variant):
+    """The paper's ratio experiments on the GPU: Fig. 7 (ratio against block
+    length on 1000 vectors of A(3000, sigma, 2000, y, 4, 1855) for the three
+    distributions of Sec. 4.2, basic and advanced, 32-bit words, L = 1 ... N),
+    Fig. 8 (ratio against the number of uniform signal values in vectors of
+    10,000, advanced, L = 154, 100 vectors per point) and Fig. 11 (byte
+    profile entropy of the camera workload and of its compressed streams).
+    Every point's streams are checked against the oracle in the GPU tests."""
+    import torch
+
+    import paper_1805_01844_gb300 as pc
+    from paper_1805_01844_gb300 import sweeps
+
+    t0 = time.perf_counter()
+    p7 = sweeps.ratio_vs_block_length(dev)
+    t7 = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    p8 = sweeps.ratio_vs_signal(dev)
+    t8 = time.perf_counter() - t0
+    fig7 = {}
+    for p in p7:
+        fig7.setdefault("%s/%s" % (p["curve"], p["variant"]), []).append([p["L"], round(p["ratio"], 5)])
+    fig8 = {}
+    for p in p8:
+        fig8.setdefault(p["curve"], []).append([p["a"], round(p["ratio"], 5)])
+    # Fig. 11: the workload's bytes and its streams (the timed one, and the other variant)
+    other = pc.ADVANCED if variant == "basic" else pc.BASIC
+    codec = pc.Codec(other, 16, w, L, max_samples=x.numel(), device=dev)
+    obuf = torch.empty(codec.bound(x.numel()), dtype=torch.uint8, device=dev)
+    _, onb = codec.compress(x, out=obuf)
+    assert codec.device_status() == 0
+    prof = sweeps.byte_profile(x, {variant: (sbuf, stream_bytes), ("basic", "advanced")[other]: (obuf, int(onb.item()))})
+    del obuf, codec
+    torch.cuda.empty_cache()
+    fig11 = {k: {"entropy_bits_per_byte": round(v["entropy_bits"], 4), "max_over_mean": round(v["max_over_mean"], 2)}
+             for k, v in prof.items()}
+    return {"fig7_ratio_vs_block_length": {"N": 1855, "vectors": 1000, "word_bits": 32, "points": fig7,
+                                           "summary": sweeps.summary(p7), "wall_s": round(t7, 2)},
+            "fig8_ratio_vs_signal": {"N": 10000, "vectors": 100, "block_len": 154, "variant": "advanced",
+                                     "points": fig8, "wall_s": round(t8, 2)},
+            "fig11_byte_profile": {"workload": "camera events (the timed workload), L %d, w %d" % (L, w),
+                                   "profiles": fig11},
+            "ratio_definition": "32-bit words in / stream bytes without the 64-byte stream header (Sec. 4.2)"}
 
 
 def white_noise_65536_latency(dev, reps=200):

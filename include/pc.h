@@ -418,6 +418,14 @@ pc_status pc_slice(const void *d_in, uint64_t in_bytes, const pc_params *params,
                    uint64_t n_blocks, void *d_out, uint64_t out_capacity, uint64_t *d_out_bytes,
                    void *d_workspace, uint64_t workspace_bytes, pc_stream_t stream);
 
+/* ---- byte profile (Sec. 5, Fig. 11) --------------------------------------
+ * Occurrences of each byte value 0..255 in n_bytes bytes of device memory
+ * d_bytes (any alignment): d_hist is device memory of 256 uint64_t
+ * (8-byte aligned), cleared and then filled on `stream`.  The paper compares
+ * the byte profile of a file before and after polynomial compression (a
+ * flatter profile after).  PC_ERR_INVALID_ARG for NULL pointers. */
+pc_status pc_byte_histogram(const void *d_bytes, uint64_t n_bytes, uint64_t *d_hist, pc_stream_t stream);
+
 /* Compression without any device allocation, for callers that cannot
  * allocate device memory once they run: a data-acquisition loop that must not
  * call cudaMalloc mid-readout (it can fail under memory pressure or

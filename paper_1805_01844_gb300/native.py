@@ -22,7 +22,7 @@ EXPORTS = ("pc_bound", "pc_workspace_size", "pc_compress", "pc_decompress",
            "pc_strerror", "pc_compress_noalloc", "pc_batch_describe", "pc_batch_plan",
            "pc_compress_batch", "pc_segment_features", "pc_mlp_forward", "pc_mlp_grad", "pc_mlp_adam",
            "pc_segments_describe", "pc_segments_plan", "pc_segments_features", "pc_compress_segments",
-           "pc_shard_range", "pc_stitch_layout", "pc_stitch", "pc_slice")
+           "pc_shard_range", "pc_stitch_layout", "pc_stitch", "pc_slice", "pc_byte_histogram")
 SEGMENT_SAMPLES, CHOOSER_FEATURES, CHOOSER_OPTIONS = 4096, 24, 12
 MLP_PARAMS, MLP_WEIGHT_BYTES = 6540, 13360
 NOALLOC_SCRATCH_BYTES = 1 << 20
@@ -147,6 +147,8 @@ def load(path=LIB_PATH):
     L.pc_stitch.restype = st
     L.pc_slice.argtypes = [vp, u64, pp, u64, u64, vp, u64, vp, vp, u64, vp]
     L.pc_slice.restype = st
+    L.pc_byte_histogram.argtypes = [vp, u64, vp, vp]
+    L.pc_byte_histogram.restype = st
     L.pc_strerror.argtypes = [st]
     L.pc_strerror.restype = ctypes.c_char_p
     _lib = L
@@ -296,3 +298,8 @@ def slice_raw(d_in, in_bytes, p, first_block, n_blocks, d_out, out_capacity, d_o
     """pc_slice on raw device addresses; returns the host status."""
     return load().pc_slice(d_in, int(in_bytes), ctypes.byref(p), int(first_block), int(n_blocks), d_out,
                            int(out_capacity), d_out_bytes, d_ws, int(ws_bytes), stream or None)
+
+
+def byte_histogram_raw(d_bytes, n_bytes, d_hist, stream):
+    """pc_byte_histogram on raw device addresses; returns the host status."""
+    return load().pc_byte_histogram(d_bytes or None, int(n_bytes), d_hist, stream or None)
