@@ -715,17 +715,23 @@ def learned_vs_plain(dev, train_samples=2 << 30, test_bytes=1 << 30):
 
     t0 = time.perf_counter()
     tr = datagen.chooser_mix_torch(train_samples, dev, seed=11)
-    sizes_tr = ch.exhaustive_sizes(tr)
+    opt_ms = []
+    sizes_tr = ch.exhaustive_sizes(tr, times=opt_ms)
     y = torch.argmin(sizes_tr, dim=1).to(torch.uint8)
+    # a second network trained on labels restricted to options that compress
+    # at least as fast as the plain option (a throughput floor)
+    y_fast = ch.labels_within_time(sizes_tr, opt_ms, opt_ms[ch.PLAIN_OPTION])
     c = ch.Chooser(dev, seed=0)
+    c_fast = ch.Chooser(dev, seed=0)
     Xtr = ch.segment_features(tr)
     del tr, sizes_tr
     torch.cuda.empty_cache()
     hist = c.train(Xtr, y, epochs=8, batch=4096, lr=3e-3)
+    c_fast.train(Xtr, y_fast, epochs=8, batch=4096, lr=3e-3)
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
     n_train = int(Xtr.shape[0])
-    del Xtr, y
+    del Xtr, y, y_fast
     te = datagen.chooser_mix_torch(test_bytes // 2, dev, seed=12)
     sizes_te = ch.exhaustive_sizes(te)
     raw = te.numel() * 2
@@ -757,6 +763,18 @@ def learned_vs_plain(dev, train_samples=2 << 30, test_bytes=1 << 30):
     learned_bytes = seg.total_bytes()
     _, t_plain = timed(plain_path)
     plain_bytes = seg.total_bytes()
+    # the learned path's parts, each timed alone
+    feats, t_feat = timed(seg.features)
+    _, t_mlp = timed(lambda: c.predict(feats))
+    _, t_comp = timed(lambda: seg.compress(pred))
+
+    def fast_path():
+        p = c_fast.predict(seg.features())
+        seg.compress(p)
+        return p
+
+    pred_fast, t_fast = timed(fast_path)
+    fast_bytes = seg.total_bytes()
     assert seg.device_status() == native.PC_OK
     best = int(sizes_te.min(dim=1).values.sum().item())
     agree = float((pred.to(torch.int64) == torch.argmin(sizes_te, dim=1)).float().mean().item())
@@ -777,6 +795,14 @@ def learned_vs_plain(dev, train_samples=2 << 30, test_bytes=1 << 30):
              "ratio_best_fixed_whole_stream": raw / whole[o_best], "best_fixed_option": o_best,
              "label_agreement": agree, "gbs_plain": raw / (t_plain / 1e3) / GB,
              "gbs_learned": raw / (t_learned / 1e3) / GB, "train_s": train_s,
+             "learned_path_ms": {"features": t_feat, "mlp": t_mlp, "compress_learned_options": t_comp,
+                                 "total": t_learned, "compress_plain_option": t_plain},
+             "option_gbs_train": [round(n_train * ch.SEG * 2 / (t / 1e3) / GB, 1) for t in opt_ms],
+             "throughput_floor": {"labels": "smallest option among those at least as fast as the plain one "
+                                            "on the training segments",
+                                  "allowed_options": [o for o, t in enumerate(opt_ms)
+                                                      if t <= opt_ms[ch.PLAIN_OPTION]],
+                                  "ratio": raw / fast_bytes, "gbs": raw / (t_fast / 1e3) / GB},
              "train_loss_first_last": [hist[0], hist[-1]],
              "note": "per-segment v1 streams, all on the device (features, MLP, per-segment compression); "
                      "data: camera events + white noise of varied sigma, train seed 11, test seed 12"},

@@ -141,19 +141,42 @@ def compress_segments(x, options, variant=native.ADVANCED):
     return seg
 
 
-def exhaustive_sizes(x, variant=native.ADVANCED):
+def exhaustive_sizes(x, variant=native.ADVANCED, times=None):
     """Stream size of every segment under every option: [nseg, 12] int64
-    (every segment compressed 12 times on the device)."""
+    (every segment compressed 12 times on the device).  If `times` is a
+    list, the GPU time (ms, CUDA events) of each option's pass over all
+    segments is appended to it."""
     seg = Segments([x], variant)
     nseg = seg.n_segments
     sizes = torch.empty((nseg, OPTIONS), dtype=torch.int64, device=x.device)
     for o in range(OPTIONS):
-        seg.compress(torch.full((nseg,), o, dtype=torch.uint8, device=x.device))
+        opts = torch.full((nseg,), o, dtype=torch.uint8, device=x.device)
+        if times is not None:
+            seg.compress(opts)  # warm-up (the series table of the workspace)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+        seg.compress(opts)
+        if times is not None:
+            e1.record()
         st = seg.device_status()
         if st != native.PC_OK:
             raise native.PcError(st, "pc_compress_segments (device)")
+        if times is not None:
+            times.append(e0.elapsed_time(e1))
         sizes[:, o] = seg.nbytes[0]
     return sizes
+
+
+def labels_within_time(sizes, times, limit):
+    """Minimum-size labels among the options whose pass over the segments
+    took at most `limit` ms (a throughput floor); the fastest option if none
+    qualifies.  sizes: [nseg, 12] device tensor; times: 12 floats."""
+    allowed = torch.tensor([t <= limit for t in times], device=sizes.device)
+    if not bool(allowed.any()):
+        allowed[int(np.argmin(times))] = True
+    big = torch.iinfo(torch.int64).max
+    masked = torch.where(allowed.view(1, -1), sizes, torch.full_like(sizes, big))
+    return torch.argmin(masked, dim=1).to(torch.uint8)
 
 
 class Chooser:
@@ -237,11 +260,15 @@ class Chooser:
                 xb = X[idx].contiguous()
                 yb = y[idx].contiguous()
                 s = _stream(self.device)
-                lib.pc_mlp_grad(self.weights.data_ptr(), xb.data_ptr(), yb.data_ptr(), xb.shape[0],
-                                self.grad.data_ptr(), self.loss.data_ptr(), s)
+                st = lib.pc_mlp_grad(self.weights.data_ptr(), xb.data_ptr(), yb.data_ptr(), xb.shape[0],
+                                     self.grad.data_ptr(), self.loss.data_ptr(), s)
+                if st != native.PC_OK:
+                    raise native.PcError(st, "pc_mlp_grad")
                 self.step += 1
-                lib.pc_mlp_adam(self.master.data_ptr(), self.weights.data_ptr(), self.grad.data_ptr(),
-                                self.m.data_ptr(), self.v.data_ptr(), self.step, lr, s)
+                st = lib.pc_mlp_adam(self.master.data_ptr(), self.weights.data_ptr(), self.grad.data_ptr(),
+                                     self.m.data_ptr(), self.v.data_ptr(), self.step, lr, s)
+                if st != native.PC_OK:
+                    raise native.PcError(st, "pc_mlp_adam")
             history.append(float(self.loss.item()) / n)
         return history
 

@@ -79,6 +79,20 @@ def test_gpu_exhaustive_sizes_match_oracle():
     assert np.array_equal(np.argmin(sizes, axis=1), lab)
 
 
+@pytest.mark.parametrize("variant", [native.BASIC, native.ADVANCED])
+def test_gpu_labels_equal_the_oracle_labels_on_a_thousand_segments(variant):
+    """The training labels the benchmark takes from the GPU's exhaustive
+    search are the CPU oracle's labels: every size of every option, over
+    about 1,300 segments of camera events and white noise of several sigmas
+    with spikes (the chooser's training mix), for both variants."""
+    x = mixed_data(5, n_events=16, noise=12)
+    assert x.size // 4096 >= 1000
+    sizes = ch.exhaustive_sizes(to_dev(x), variant).cpu().numpy()
+    lab, want = mlp.labels(x, variant)
+    assert np.array_equal(sizes, want)
+    assert np.array_equal(np.argmin(sizes, axis=1).astype(np.uint8), lab)
+
+
 def test_trained_chooser_beats_plain_heuristic():
     """Train on oracle labels of configs 1-2 data, evaluate on fresh seeds:
     the learned per-segment options give a smaller total than the plain
