@@ -73,7 +73,8 @@ k_compress_batch(const BatchItemDev *__restrict__ items, const uint64_t *__restr
     uint32_t phase = 0;
     for (;;) {
         if (threadIdx.x == 0) {
-            const uint64_t t = atomicAdd(&ws->ticket, 1u);
+            // a CTA whose staging died takes no further tile
+            const uint64_t t = g_stage_dead ? ~0ull : (uint64_t)atomicAdd(&ws->ticket, 1u);
             uint32_t lo = 0, hi = n_items - 1;  // largest i with prefix[i] <= t
             if (t < total_tiles) {
                 while (lo < hi) {

@@ -292,12 +292,36 @@ __device__ __forceinline__ void write_header(uint8_t *out, uint32_t L, uint64_t 
 
 // One mbarrier per warp for the bulk copies of its blocks (compression tiles).
 __shared__ uint64_t g_stage_bar[kMaxTileBlocks / 4];
+// Set when a staging wait gave up: the CTA issues no more bulk copies and
+// packs nothing more, its tile publishes an error for the look-back of its
+// successors, and it takes no further tile.  A bulk copy that never completes
+// may still write into the stage when the CTA exits.
+__shared__ uint32_t g_stage_dead;
 
 __device__ __forceinline__ void stage_bars_init()
 {
     if (threadIdx.x < kMaxTileBlocks / 4) mbar_init(&g_stage_bar[threadIdx.x], 1);
+    if (threadIdx.x == 0) g_stage_dead = 0;
     mbar_init_fence();
     __syncthreads();
+}
+
+// The staging state of the CTA, as lane 0 of the calling warp sees it.
+__device__ __forceinline__ bool stage_dead()
+{
+    uint32_t d = 0;
+    if ((threadIdx.x & 31u) == 0) d = *reinterpret_cast<volatile uint32_t *>(&g_stage_dead);
+    return __shfl_sync(0xFFFFFFFFu, d, 0) != 0;
+}
+
+// Bounded wait for a warp's staged blocks; on giving up, records the timeout
+// and marks the CTA's staging dead.
+__device__ __forceinline__ void stage_wait(uint32_t warp, uint32_t phase, WsHeader *ws, uint64_t limit_ns)
+{
+    if (!mbar_wait(&g_stage_bar[warp], phase & 1u, limit_ns) && (threadIdx.x & 31u) == 0) {
+        record_error(ws, PC_ERR_TIMEOUT);
+        *reinterpret_cast<volatile uint32_t *>(&g_stage_dead) = 1u;
+    }
 }
 
 // One stream as the compression kernels see it.
@@ -342,7 +366,7 @@ __device__ void compress_tile(const StreamArgs &sa, uint64_t tile, uint8_t *smem
         // block, completing on the warp's mbarrier; the ragged end of the
         // last block comes element by element
         constexpr uint32_t VE = 16 / sizeof(T);
-        if (lane == 0) {
+        if (lane == 0) {  // (a CTA whose staging died takes no further tile, so it never comes here again)
             uint32_t bytes = 0;
             for (uint32_t b = warp; b < nblk; b += (NT / 32))
                 bytes += ((uint32_t)umin64(L, cnt - (uint64_t)b * L) / VE) * 16u;
@@ -361,7 +385,7 @@ __device__ void compress_tile(const StreamArgs &sa, uint64_t tile, uint8_t *smem
             for (uint32_t e = n_b / VE * VE + lane; e < n_b; e += 32)
                 reinterpret_cast<T *>(dst)[e] = in[(blk0 + b) * L + e];
         }
-        if (!mbar_wait(&g_stage_bar[warp], phase & 1u, limit_ns) && lane == 0) record_error(ws, PC_ERR_TIMEOUT);
+        stage_wait(warp, phase, ws, limit_ns);
         ++phase;  // every warp's barrier completed one phase
         __syncwarp();
         for (uint32_t b = warp; b < nblk; b += (NT / 32)) {
@@ -435,9 +459,14 @@ __device__ void compress_tile(const StreamArgs &sa, uint64_t tile, uint8_t *smem
         const uint32_t incl = warp_incl_scan_u32(W);
         if (lane < nblk) bv.woff[lane] = incl - W;
         const uint32_t agg = __shfl_sync(0xFFFFFFFFu, incl, 31);
-        lookback_publish(sa.status, tile, agg);
         uint64_t excl = 0;
-        const bool ok = lookback_complete(sa.status, tile, agg, ws, limit_ns, &excl);
+        bool ok = false;
+        if (stage_dead()) {  // the staged samples are not whole: successors stop on this tile's error
+            if (lane == 0) st_release(&sa.status[tile], kFlagError);
+        } else {
+            lookback_publish(sa.status, tile, agg);
+            ok = lookback_complete(sa.status, tile, agg, ws, limit_ns, &excl);
+        }
         if (lane == 0) {
             bv.agg = agg;
             bv.excl = excl;
@@ -554,7 +583,8 @@ __device__ void compress_tile_multi(const StreamArgs &sa, uint64_t tile, uint8_t
     auto stage = [&](uint32_t h, bool again) {
         const uint32_t m = nh(h);
         __syncwarp();  // the warp's earlier accesses to its slots come first
-        if (lane == 0) {
+        const bool dead = stage_dead();
+        if (lane == 0 && !dead) {
             uint32_t bytes = 0;
             for (uint32_t b = warp; b < m; b += NW) bytes += (n_of(h * H + b) / VE) * 16u;
             const uint64_t policy = again ? l2_policy_evict_last() : l2_policy_evict_first();
@@ -571,7 +601,7 @@ __device__ void compress_tile_multi(const StreamArgs &sa, uint64_t tile, uint8_t
             T *dst = slot(b);
             for (uint32_t e = n_b / VE * VE + lane; e < n_b; e += 32) dst[e] = in[(blk0 + h * H + b) * L + e];
         }
-        if (!mbar_wait(&g_stage_bar[warp], phase & 1u, limit_ns) && lane == 0) record_error(ws, PC_ERR_TIMEOUT);
+        if (!dead) stage_wait(warp, phase, ws, limit_ns);
         ++phase;  // every warp's barrier completed one phase
         __syncwarp();
     };
@@ -609,9 +639,14 @@ __device__ void compress_tile_multi(const StreamArgs &sa, uint64_t tile, uint8_t
             run += __shfl_sync(0xFFFFFFFFu, incl, 31);
         }
         const uint32_t agg = run;
-        lookback_publish(sa.status, tile, agg);
         uint64_t excl = 0;
-        const bool ok = lookback_complete(sa.status, tile, agg, ws, limit_ns, &excl);
+        bool ok = false;
+        if (stage_dead()) {  // the staged samples are not whole: successors stop on this tile's error
+            if (lane == 0) st_release(&sa.status[tile], kFlagError);
+        } else {
+            lookback_publish(sa.status, tile, agg);
+            ok = lookback_complete(sa.status, tile, agg, ws, limit_ns, &excl);
+        }
         if (lane == 0) {
             mv.agg = agg;
             mv.excl = excl;
@@ -637,6 +672,7 @@ __device__ void compress_tile_multi(const StreamArgs &sa, uint64_t tile, uint8_t
         for (uint32_t h = nst; h-- > 0;) {
             if (h + 1 < nst) {
                 stage(h, false);
+                if (stage_dead()) continue;  // this warp's restaged blocks may be incomplete: pack none
                 for (uint32_t b = warp; b < nh(h); b += NW) {  // padding: this stage tile's minimum again
                     T *u = slot(b);
                     const uint32_t n_b = n_of(h * H + b);
@@ -678,13 +714,16 @@ __device__ void write_empty_stream(const StreamArgs &sa)
 // Single-stream compression: a persistent grid, tiles taken in order from an
 // atomic ticket (so a tile only waits on tiles owned by running CTAs).
 // CTAs per SM the register allocation must allow: basic tiles (74 KB of
-// shared memory) fit three to an SM once registers are capped at 85; advanced
-// tiles (100 KB) fit two.
+// shared memory) fit three to an SM once registers are capped at 85; so do
+// advanced tiles of 16-bit data (about 74 KB at L = 1024; measured: at 84
+// registers, which round up past a third of the register file, only two fit
+// and compression ran 24 % slower), while 32-bit advanced tiles that walk
+// their series use up to 100 KB and fit two.
 #ifndef PCX_COMPRESS_MIN_CTAS_BASIC
 #define PCX_COMPRESS_MIN_CTAS_BASIC 3
 #endif
 #ifndef PCX_COMPRESS_MIN_CTAS_ADVANCED
-#define PCX_COMPRESS_MIN_CTAS_ADVANCED 2
+#define PCX_COMPRESS_MIN_CTAS_ADVANCED 3
 #endif
 // 128-thread CTAs (half-size tiles): twice as many per SM.
 template <uint32_t VAR, uint32_t NT>
@@ -706,7 +745,8 @@ k_compress(StreamArgs sa, WsHeader *ws, uint64_t limit_ns)
     stage_bars_init();
     uint32_t phase = 0;
     for (;;) {
-        if (threadIdx.x == 0) s_tile = atomicAdd(&ws->ticket, 1u);
+        // a CTA whose staging died takes no further tile
+        if (threadIdx.x == 0) s_tile = g_stage_dead ? 0xFFFFFFFFu : atomicAdd(&ws->ticket, 1u);
         __syncthreads();
         const uint64_t tile = s_tile;
         __syncthreads();
