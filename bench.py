@@ -45,6 +45,9 @@ def parse():
     ap.add_argument("--block-len", type=int, default=1024)
     ap.add_argument("--word-bits", type=int, default=64, choices=[32, 64])
     ap.add_argument("--events", type=int, default=WORKLOAD["n_events"])
+    ap.add_argument("--white-noise", type=int, default=0,
+                    help="time N samples of the 65,536-sample white-noise workload's generator instead of camera "
+                         "events (no CPU baseline or sweeps then)")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-events", type=int, default=0,
                     help="events in the oracle's CPU sample (0 = sized to ~15 s)")
@@ -61,6 +64,8 @@ def parse():
 
 
 def workload_name(args):
+    if args.white_noise:
+        return "white_noise_N300_5_%d_u16" % args.white_noise
     return "cherenkov_events_%dx%dx%dx%d_u16" % (args.events, WORKLOAD["n_gains"], WORKLOAD["n_time"],
                                                 WORKLOAD["n_pixels"])
 
@@ -318,7 +323,11 @@ def main():
     variant = pc.BASIC if args.variant == "basic" else pc.ADVANCED
     L, w = args.block_len, args.word_bits
 
-    x = datagen.cherenkov_events_torch(args.events, dev, seed=0).reshape(-1)
+    if args.white_noise:
+        x = datagen.white_noise_torch(args.white_noise, dev, mean=300.0, sigma=5.0, seed=0)
+        args.no_cpu_baseline = args.no_sweep = args.no_paper_sweeps = True
+    else:
+        x = datagen.cherenkov_events_torch(args.events, dev, seed=0).reshape(-1)
     n = x.numel()
     raw_bytes = n * 2
     codec = pc.Codec(variant, 16, w, L, max_samples=n, device=dev)
