@@ -826,6 +826,7 @@ __device__ __forceinline__ DecBlock dec_setup(const uint8_t *in, uint64_t gb, ui
             for (uint32_t i = 0; i < r; ++i) d.lim *= d.B;
         }
     } else {
+        d.p = eq1_p(d.B, WB);  // p_1: every word holds p_1 or p_1 - 1 whole samples
         const uint64_t h = orbit_get<WB>(ot, (uint32_t)d.B, L, ws, limit_ns);  // B <= 65536 here
         if (h != ~0ull) {
             d.ov = orbit_view(ot, h);
@@ -929,6 +930,7 @@ k_decode_w(const uint8_t *__restrict__ in, uint32_t L, T *__restrict__ out, uint
                 } else {
                     const Word *src = wsrc;
                     const uint32_t hstar = k.hstar, B32 = (uint32_t)k.B;
+                    const uint32_t p1 = k.p, ns = WB == 64 ? p1 / hstar : 0u, rem0 = p1 - ns * hstar;
                     uint32_t cR = 1, cr = 0, qlast = 0, plast = 0;
                     for (uint32_t j0 = 0; j0 < W; j0 += 32) {
                         const uint32_t i = j0 + lane;
@@ -961,17 +963,24 @@ k_decode_w(const uint8_t *__restrict__ in, uint32_t L, T *__restrict__ out, uint
                         cR = __shfl_sync(0xFFFFFFFFu, e.R, 31);
                         cr = __shfl_sync(0xFFFFFFFFu, r, 31);
                         if (!valid) continue;
+                        // every lane takes p_1 digits, whether its word holds p_1 or p_1 - 1
+                        // samples, so the warp's control flow is the same for all words: a
+                        // word of p_1 - 1 samples puts its top remainder r'_(i-1) in the p_1-th
+                        // digit, stored at u[q_i - 1], the slot its split sample takes below
                         T *last = u + e.q + e.p - 1;
-                        uint32_t rem = e.p;
-                        while (rem >= hstar && (body >> 32) != 0) {
+                        for (uint32_t t = 0; t < ns; ++t) {
                             uint64_t lo;
                             body = divmod_inv64(body, k.Dh, k.MD, lo);
                             rev_exact<T>(last, (uint32_t)lo, hstar, B32, k.mg, vmin);
                             last -= hstar;
-                            rem -= hstar;
                         }
                         bad |= (body >> 32) != 0;
-                        const uint32_t top = rev_quot<T>(last, (uint32_t)body, rem, B32, k.mg, vmin);
+                        const uint32_t qtop = rev_quot<T>(last, (uint32_t)body, rem0, B32, k.mg, vmin);
+                        uint32_t top = qtop;
+                        if (e.p != p1) {
+                            top = (uint32_t)u[e.q - 1] - vmin;
+                            bad |= qtop != 0;
+                        }
                         if (i == 0) {
                             bad |= top != 0;
                         } else {
@@ -1038,6 +1047,7 @@ k_decode_w(const uint8_t *__restrict__ in, uint32_t L, T *__restrict__ out, uint
                                                              k.Dh, k.MD);
                         } else {
                             const uint32_t hstar = k.hstar, B32 = (uint32_t)k.B;
+                            const uint32_t p1 = k.p, ns = WB == 64 ? p1 / hstar : 0u, rem0 = p1 - ns * hstar;
                             for (uint32_t j0 = jb; j0 < je; j0 += 32) {
                                 const uint32_t i = j0 + lane;
                                 const bool valid = i < je;
@@ -1069,17 +1079,24 @@ k_decode_w(const uint8_t *__restrict__ in, uint32_t L, T *__restrict__ out, uint
                                 cR = __shfl_sync(0xFFFFFFFFu, e.R, 31);
                                 cr = __shfl_sync(0xFFFFFFFFu, r, 31);
                                 if (!valid) continue;
+                                // every lane takes p_1 digits, whether its word holds p_1 or p_1 - 1
+                                // samples, so the warp's control flow is the same for all words: a
+                                // word of p_1 - 1 samples puts its top remainder r'_(i-1) in the p_1-th
+                                // digit, stored at u[q_i - 1], the slot its split sample takes below
                                 T *last = u + e.q + e.p - 1;
-                                uint32_t rem = e.p;
-                                while (rem >= hstar && (body >> 32) != 0) {
+                                for (uint32_t t = 0; t < ns; ++t) {
                                     uint64_t lo;
                                     body = divmod_inv64(body, k.Dh, k.MD, lo);
                                     rev_exact<T>(last, (uint32_t)lo, hstar, B32, k.mg, vmin);
                                     last -= hstar;
-                                    rem -= hstar;
                                 }
                                 bad |= (body >> 32) != 0;
-                                const uint32_t top = rev_quot<T>(last, (uint32_t)body, rem, B32, k.mg, vmin);
+                                const uint32_t qtop = rev_quot<T>(last, (uint32_t)body, rem0, B32, k.mg, vmin);
+                                uint32_t top = qtop;
+                                if (e.p != p1) {
+                                    top = (uint32_t)u[e.q - 1] - vmin;
+                                    bad |= qtop != 0;
+                                }
                                 if (i == 0) {
                                     bad |= top != 0;
                                 } else {
