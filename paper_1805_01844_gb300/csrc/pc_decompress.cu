@@ -124,10 +124,37 @@ __device__ __forceinline__ uint32_t put_digits(T *dst, uint32_t x, uint32_t k, u
 // last[0], last[-1], ..., last[-(k-1)] (k - 1 divisions, the top one is x).
 // rev_quot: k divisions; the k digits are written the same way and the
 // remaining quotient is returned.
+#ifndef PCX_REV_EXACT_SPEC
+#define PCX_REV_EXACT_SPEC 1
+#endif
+
+template <typename T, uint32_t K>
+__device__ __forceinline__ void rev_exact_k(T *last, uint32_t x, uint32_t B32, Magic32 mg, uint32_t vmin)
+{
+#pragma unroll
+    for (uint32_t i = 0; i + 1 < K; ++i) {
+        const uint32_t q = magic_div(x, mg);
+        *(last - i) = (T)(x - q * B32 + vmin);
+        x = q;
+    }
+    *(last - (K - 1)) = (T)(x + vmin);
+}
+
+// (k is the same for every lane of the warp: one block's h*)
 template <typename T>
 __device__ __forceinline__ void rev_exact(T *last, uint32_t x, uint32_t k, uint32_t B32, Magic32 mg,
                                           uint32_t vmin)
 {
+#if PCX_REV_EXACT_SPEC
+    switch (k) {
+    case 2: rev_exact_k<T, 2>(last, x, B32, mg, vmin); return;
+    case 3: rev_exact_k<T, 3>(last, x, B32, mg, vmin); return;
+    case 4: rev_exact_k<T, 4>(last, x, B32, mg, vmin); return;
+    case 5: rev_exact_k<T, 5>(last, x, B32, mg, vmin); return;
+    case 6: rev_exact_k<T, 6>(last, x, B32, mg, vmin); return;
+    default: break;
+    }
+#endif
     for (uint32_t i = 0; i + 1 < k; ++i) {
         const uint32_t q = magic_div(x, mg);
         *(last - i) = (T)(x - q * B32 + vmin);
