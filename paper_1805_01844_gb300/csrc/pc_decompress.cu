@@ -199,23 +199,21 @@ __device__ __forceinline__ uint32_t rev_quot(T *last, uint32_t x, uint32_t k, ui
     }
 }
 
-// s = body R + r for R < 2^16 by 16-bit long division with R's magic
-// reciprocal (every partial dividend is < R 2^16 <= 2^32).
+// s = body R + r for R < 2^16 by long division with R's magic reciprocal:
+// the high 32-bit word first (any 32-bit dividend), then two 16-bit steps
+// whose partial dividends r 2^16 + 16 bits stay below R 2^16 <= 2^32.
 __device__ __forceinline__ uint64_t divmod_small64(uint64_t s, uint32_t R, Magic32 mg, uint32_t &r)
 {
-    uint32_t x = (uint32_t)(s >> 48);
-    const uint32_t q3 = magic_div(x, mg);
-    uint32_t rr = x - q3 * R;
-    x = (rr << 16) | ((uint32_t)(s >> 32) & 0xFFFFu);
+    const uint32_t s1 = (uint32_t)(s >> 32), s0 = (uint32_t)s;
+    const uint32_t q1 = magic_div(s1, mg);
+    uint32_t rr = s1 - q1 * R;
+    uint32_t x = (rr << 16) | (s0 >> 16);
     const uint32_t q2 = magic_div(x, mg);
     rr = x - q2 * R;
-    x = (rr << 16) | ((uint32_t)(s >> 16) & 0xFFFFu);
-    const uint32_t q1 = magic_div(x, mg);
-    rr = x - q1 * R;
-    x = (rr << 16) | ((uint32_t)s & 0xFFFFu);
-    const uint32_t q0 = magic_div(x, mg);
-    r = x - q0 * R;
-    return ((uint64_t)q3 << 48) | ((uint64_t)q2 << 32) | ((uint64_t)q1 << 16) | q0;
+    x = (rr << 16) | (s0 & 0xFFFFu);
+    const uint32_t q3 = magic_div(x, mg);
+    r = x - q3 * R;
+    return ((uint64_t)q1 << 32) + ((uint64_t)q2 << 16) + q3;
 }
 
 // Header of a stream, validated by every CTA of the offsets kernel against
