@@ -14,17 +14,22 @@ static cudaError_t launch_compress_t(const LaunchArgs &a)
     // (compress_tile_multi); where a stage budget for four CTAs per SM still
     // gives stage tiles of >= 24 blocks, that smaller stage (measured +2 % at
     // L = 1024; smaller stage tiles lose more than the extra CTA gains)
-    constexpr bool kMultiOk = VAR == PC_VARIANT_BASIC && NT == kThreads;
+    // advanced 16-bit streams (series table) take the same look-back tiles,
+    // with stage tiles of the four-CTA budget so that their larger per-tile
+    // arrays still leave three CTAs per SM
+    constexpr bool kAdvMulti = VAR == PC_VARIANT_ADVANCED && ORB && sizeof(T) == 2 && NT == kThreads;
+    constexpr bool kMultiOk = (VAR == PC_VARIANT_BASIC && NT == kThreads) || kAdvMulti;
     const TileCfg cfg4 = tile_cfg(kKernelCompress, VAR, sizeof(T) * 8, WB, a.L, ORB, NT, kTileBudgetMulti4);
     const bool four = kMultiOk && cfg4.tb >= 24;
     const TileCfg cfgm = four ? cfg4 : cfg1;
     const uint32_t k = multi_k(cfgm.tb);
-    const bool multi = kMultiOk && k >= 2 && a.tb == cfg1.tb && cfgm.tb >= 8 && (a.L * sizeof(T)) % 16 == 0 &&
-                       ceil_div(a.n_blocks, (uint64_t)k * cfgm.tb) >= kSmallTiles;
+    const bool multi = kMultiOk && (!kAdvMulti || four) && k >= 2 && a.tb == cfg1.tb && cfgm.tb >= 8 &&
+                       (a.L * sizeof(T)) % 16 == 0 && ceil_div(a.n_blocks, (uint64_t)k * cfgm.tb) >= kSmallTiles;
     auto kern = !multi ? k_compress<T, WB, VAR, ORB, NT, false, false>
                 : four ? k_compress<T, WB, VAR, ORB, NT, kMultiOk, kMultiOk>
                        : k_compress<T, WB, VAR, ORB, NT, kMultiOk, false>;
-    const TileCfg cfg = multi ? cfgm : cfg1;
+    TileCfg cfg = multi ? cfgm : cfg1;
+    if (multi && kAdvMulti) cfg.smem = multi_smem<VAR>(cfg);
     const uint64_t n_tiles = multi ? ceil_div(a.n_blocks, (uint64_t)k * cfg.tb) : a.n_tiles;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.smem);
     if (e != cudaSuccess) return e;

@@ -17,6 +17,8 @@
 
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "pc_device.cuh"
 #include "pc_kernels.h"
 #include "pc_orbit.cuh"
@@ -543,6 +545,34 @@ struct MultiVars {  // per-tile arrays, in the BlockVars space of the stage
 };
 static_assert(sizeof(MultiVars) <= sizeof(BlockVars), "look-back tile arrays fit the stage tile arrays");
 
+// The advanced variant's per-tile arrays (16-bit data, series table): each
+// block's view of its base's series and the Horner constants of its words;
+// larger than BlockVars, so the launch reserves its size after the stage.
+struct AdvMultiVars {
+    uint64_t K[kMultiMaxBlocks];   // vmin (1 + ... + B^(p_1 - 1)) mod 2^w
+    uint64_t K2[kMultiMaxBlocks];  // the same for p_1 - 1 digits
+    uint32_t Bm1[kMultiMaxBlocks];
+    uint32_t vmin[kMultiMaxBlocks];
+    uint32_t W[kMultiMaxBlocks];
+    uint32_t woff[kMultiMaxBlocks];
+    uint32_t p1[kMultiMaxBlocks];
+    uint32_t off[kMultiMaxBlocks], Q[kMultiMaxBlocks], P[kMultiMaxBlocks], SQ[kMultiMaxBlocks], G[kMultiMaxBlocks];
+    uint32_t mgm[kMultiMaxBlocks], mga[kMultiMaxBlocks], mgs[kMultiMaxBlocks];
+    uint64_t excl;
+    uint32_t agg;
+    uint32_t ok;
+};
+
+template <uint32_t VAR>
+using MultiVarsOf = typename std::conditional<VAR == PC_VARIANT_BASIC, MultiVars, AdvMultiVars>::type;
+
+// Shared memory of a multi-stage tile: the stage, then the per-tile arrays.
+template <uint32_t VAR>
+PCX_HD uint32_t multi_smem(const TileCfg &cfg)
+{
+    return (uint32_t)round_up((uint64_t)cfg.off_blk + sizeof(MultiVarsOf<VAR>), 16);
+}
+
 // Stage tiles per look-back tile for stage tiles of tb blocks.
 #ifndef PCX_MULTI_K_MAX
 #define PCX_MULTI_K_MAX 8
@@ -553,7 +583,7 @@ PCX_HD uint32_t multi_k(uint32_t tb)
     return k > PCX_MULTI_K_MAX ? PCX_MULTI_K_MAX : k;
 }
 
-template <typename T, uint32_t WB, uint32_t NT, bool FOUR>
+template <typename T, uint32_t WB, uint32_t NT, bool FOUR, uint32_t VAR = PC_VARIANT_BASIC>
 __device__ void compress_tile_multi(const StreamArgs &sa, uint64_t tile, uint8_t *smem, WsHeader *ws,
                                     uint64_t limit_ns, uint32_t &phase)
 {
@@ -561,10 +591,11 @@ __device__ void compress_tile_multi(const StreamArgs &sa, uint64_t tile, uint8_t
     constexpr uint32_t D = sizeof(T) * 8;
     constexpr uint32_t VE = 16 / sizeof(T);
     constexpr uint32_t NW = NT / 32;
+    constexpr bool ADV = VAR == PC_VARIANT_ADVANCED;
     const uint32_t L = sa.L;
-    const TileCfg cfg = tile_cfg(kKernelCompress, PC_VARIANT_BASIC, D, WB, L, false, NT, FOUR ? kTileBudgetMulti4 : 0u);
+    const TileCfg cfg = tile_cfg(kKernelCompress, VAR, D, WB, L, ADV, NT, FOUR ? kTileBudgetMulti4 : 0u);
     const uint32_t H = cfg.tb;  // blocks per stage tile; sa.tb = K H
-    MultiVars &mv = *reinterpret_cast<MultiVars *>(smem + cfg.off_blk);
+    MultiVarsOf<VAR> &mv = *reinterpret_cast<MultiVarsOf<VAR> *>(smem + cfg.off_blk);
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
     const T *in = static_cast<const T *>(sa.in);
     const uint64_t n = sa.n, n_blocks = sa.n_blocks, n_tiles = sa.n_tiles;
@@ -611,7 +642,7 @@ __device__ void compress_tile_multi(const StreamArgs &sa, uint64_t tile, uint8_t
         stage(h, h + 1 < nst);
         for (uint32_t b = warp; b < nh(h); b += NW) {
             uint64_t Bb;
-            block_minmax<T, PCX_MINMAX_U16X2>(slot(b), n_of(h * H + b), &mv.vmin[h * H + b], &Bb);
+            block_minmax<T, PCX_MINMAX_U16X2 && !ADV>(slot(b), n_of(h * H + b), &mv.vmin[h * H + b], &Bb);
             if (lane == 0) mv.Bm1[h * H + b] = (uint32_t)(Bb - 1);
         }
     }
@@ -626,11 +657,37 @@ __device__ void compress_tile_multi(const StreamArgs &sa, uint64_t tile, uint8_t
             if (b < nblk) {
                 const uint64_t B = (uint64_t)mv.Bm1[b] + 1;
                 if (B > 1) {
-                    const uint32_t p = basic_p(B, WB);
-                    W = (n_of(b) + p - 1) / p;
-                    PackK pk = basic_pack_k(B, p, mv.vmin[b], WB);
-                    pk.shape |= p << 24;
-                    mv.pk[b] = pk;
+                    if constexpr (!ADV) {
+                        const uint32_t p = basic_p(B, WB);
+                        W = (n_of(b) + p - 1) / p;
+                        PackK pk = basic_pack_k(B, p, mv.vmin[b], WB);
+                        pk.shape |= p << 24;
+                        mv.pk[b] = pk;
+                    } else {  // the series from the table (16-bit data: every base is in it)
+                        const uint64_t hd = orbit_get<WB>(sa.ot, (uint32_t)B, L, ws, limit_ns);
+                        if (hd != ~0ull) {
+                            const OrbitView v = orbit_view(sa.ot, hd);
+                            W = orbit_words_cached(sa.ot, v, n_of(b), L);
+                            mv.off[b] = v.off;
+                            mv.Q[b] = v.Q;
+                            mv.P[b] = v.P;
+                            mv.SQ[b] = v.SQ;
+                            mv.G[b] = v.G;
+                            mv.mgm[b] = v.mgP.m;
+                            mv.mga[b] = v.mgP.a;
+                            mv.mgs[b] = v.mgP.s;
+                            const uint32_t p1 = eq1_p(B, WB);
+                            uint64_t geo = 0, pw = 1, geo0 = 0;  // 1 + B + ... + B^(p-1)
+                            for (uint32_t kk = 0; kk < p1; ++kk) {
+                                geo0 = geo;
+                                geo += pw;
+                                pw *= B;
+                            }
+                            mv.p1[b] = p1;
+                            mv.K[b] = geo * mv.vmin[b];
+                            mv.K2[b] = geo0 * mv.vmin[b];
+                        }
+                    }
                 }
                 mv.W[b] = W;
             }
@@ -684,10 +741,17 @@ __device__ void compress_tile_multi(const StreamArgs &sa, uint64_t tile, uint8_t
                 const uint32_t bb = h * H + b;
                 const uint32_t W = mv.W[bb];
                 if (W == 0) continue;
-                PackK pk = mv.pk[bb];
-                const uint32_t p = pk.shape >> 24;
-                pk.shape &= 0xFFFFFFu;
-                pack_basic_block<T, WB>(slot(b), W, p, mv.Bm1[bb] + 1u, pk, payload + mv.woff[bb]);
+                if constexpr (!ADV) {
+                    PackK pk = mv.pk[bb];
+                    const uint32_t p = pk.shape >> 24;
+                    pk.shape &= 0xFFFFFFu;
+                    pack_basic_block<T, WB>(slot(b), W, p, mv.Bm1[bb] + 1u, pk, payload + mv.woff[bb]);
+                } else {
+                    const OrbitView v{mv.off[bb], mv.Q[bb], mv.P[bb], mv.SQ[bb], mv.G[bb],
+                                      Magic32{mv.mgm[bb], mv.mga[bb], mv.mgs[bb]}};
+                    adv_words_orbit<T, WB>(sa.ot, v, slot(b), W, mv.Bm1[bb] + 1u, mv.vmin[bb], mv.p1[bb], mv.K[bb],
+                                           mv.K2[bb], payload + mv.woff[bb]);
+                }
             }
         }
         if (tile == n_tiles - 1) {
@@ -695,7 +759,7 @@ __device__ void compress_tile_multi(const StreamArgs &sa, uint64_t tile, uint8_t
             const uint64_t tend = PC_HEADER_BYTES + n_blocks * 2u * (D / 8);
             for (uint64_t o = tend + threadIdx.x; o < payload_off; o += NT) sa.out[o] = 0;
             if (threadIdx.x == 0) {
-                write_header<D, WB, PC_VARIANT_BASIC>(sa.out, L, n, n_blocks, payload_words);
+                write_header<D, WB, VAR>(sa.out, L, n, n_blocks, payload_words);
                 *sa.out_bytes = payload_off + payload_words * (WB / 8);
             }
         }
@@ -733,7 +797,7 @@ constexpr int kCompressMinCtas =
 // MULTI: look-back tiles of several stage tiles (compress_tile_multi); FOUR:
 // its stage tiles sized for four CTAs per SM (registers capped at 64).
 template <typename T, uint32_t WB, uint32_t VAR, bool ORB, uint32_t NT, bool MULTI = false, bool FOUR = false>
-__global__ void __launch_bounds__(NT, FOUR ? 4 : kCompressMinCtas<VAR, NT>)
+__global__ void __launch_bounds__(NT, FOUR && VAR == PC_VARIANT_BASIC ? 4 : kCompressMinCtas<VAR, NT>)
 k_compress(StreamArgs sa, WsHeader *ws, uint64_t limit_ns)
 {
     extern __shared__ __align__(16) uint8_t smem[];
@@ -751,7 +815,7 @@ k_compress(StreamArgs sa, WsHeader *ws, uint64_t limit_ns)
         const uint64_t tile = s_tile;
         __syncthreads();
         if (tile >= sa.n_tiles) break;
-        if constexpr (MULTI) compress_tile_multi<T, WB, NT, FOUR>(sa, tile, smem, ws, limit_ns, phase);
+        if constexpr (MULTI) compress_tile_multi<T, WB, NT, FOUR, VAR>(sa, tile, smem, ws, limit_ns, phase);
         else compress_tile<T, WB, VAR, ORB, NT>(sa, tile, smem, ws, limit_ns, phase);
     }
 }

@@ -19,6 +19,7 @@ import paper_1805_01844_gb300 as pc  # noqa: E402
 from paper_1805_01844_gb300 import datagen, native  # noqa: E402
 
 FULL_TILES = 2432 * 32  # blocks above which no configuration halves its tiles
+MULTI_TILES = 2432 * 96  # blocks above which 16-bit streams take look-back tiles of several stage tiles
 
 
 def input_with_wide_blocks(n, L, d, seed, spike_every, spike):
@@ -32,8 +33,12 @@ def input_with_wide_blocks(n, L, d, seed, spike_every, spike):
     return x
 
 
-@pytest.mark.parametrize("d,L,w,extra", [(16, 1024, 64, 13), (16, 4096, 32, 5), (32, 1024, 64, 29)])
+@pytest.mark.parametrize("d,L,w,extra", [(16, 1024, 64, 13), (16, 4096, 32, 5), (32, 1024, 64, 29),
+                                         (16, 1024, 64, MULTI_TILES - FULL_TILES + 37),
+                                         (16, 512, 32, MULTI_TILES - FULL_TILES + 70)])
 def test_advanced_full_tiles_match_oracle_twice_on_one_workspace(d, L, w, extra):
+    """The last two cases are long enough for look-back tiles of four stage
+    tiles of 24 blocks (the last look-back tile partial)."""
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     dev = torch.device("cuda:0")
