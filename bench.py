@@ -269,7 +269,7 @@ def run_reference(args):
     if rank != 0:
         return
     variant = 0 if args.variant == "basic" else 1
-    n_ev = args.cpu_events or 8
+    n_ev = args.cpu_events or 16
     x = datagen.cherenkov_events(n_ev, seed=0)
     import oracle
 
@@ -289,7 +289,9 @@ def run_reference(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u16",
         "data": "synthetic", "ratio": per_step / len(s),
         "config": {"workload": workload_name(args), "variant": args.variant,
-                   "block_len": args.block_len, "word_bits": args.word_bits},
+                   "block_len": args.block_len, "word_bits": args.word_bits,
+                   "sample": "each step compresses and decompresses the first %d events (%.1f MB) of this "
+                             "workload (the same generator and seed), single thread" % (n_ev, per_step / 1e6)},
         "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle",
                          "sample": "first %d events (%.1f MB) of the workload, generated on the host"
                                    % (n_ev, per_step / 1e6)},
