@@ -199,6 +199,85 @@ __device__ __forceinline__ uint32_t rev_quot(T *last, uint32_t x, uint32_t k, ui
     }
 }
 
+// Two advanced words of one lane in lockstep (independent division
+// chains for the scheduler): rev_exact and rev_quot on (last0, x0) and
+// (last1, x1) at once; k is the same for both (and for the whole warp).
+template <typename T, uint32_t K>
+__device__ __forceinline__ void rev_exact2_k(T *l0, uint32_t x0, T *l1, uint32_t x1, uint32_t B32, Magic32 mg,
+                                             uint32_t vmin)
+{
+#pragma unroll
+    for (uint32_t i = 0; i + 1 < K; ++i) {
+        const uint32_t q0 = magic_div(x0, mg), q1 = magic_div(x1, mg);
+        *(l0 - i) = (T)(x0 - q0 * B32 + vmin);
+        *(l1 - i) = (T)(x1 - q1 * B32 + vmin);
+        x0 = q0;
+        x1 = q1;
+    }
+    *(l0 - (K - 1)) = (T)(x0 + vmin);
+    *(l1 - (K - 1)) = (T)(x1 + vmin);
+}
+
+template <typename T>
+__device__ __forceinline__ void rev_exact2(T *l0, uint32_t x0, T *l1, uint32_t x1, uint32_t k, uint32_t B32,
+                                           Magic32 mg, uint32_t vmin)
+{
+    switch (k) {
+    case 2: rev_exact2_k<T, 2>(l0, x0, l1, x1, B32, mg, vmin); return;
+    case 3: rev_exact2_k<T, 3>(l0, x0, l1, x1, B32, mg, vmin); return;
+    case 4: rev_exact2_k<T, 4>(l0, x0, l1, x1, B32, mg, vmin); return;
+    case 5: rev_exact2_k<T, 5>(l0, x0, l1, x1, B32, mg, vmin); return;
+    case 6: rev_exact2_k<T, 6>(l0, x0, l1, x1, B32, mg, vmin); return;
+    default: break;
+    }
+    for (uint32_t i = 0; i + 1 < k; ++i) {
+        const uint32_t q0 = magic_div(x0, mg), q1 = magic_div(x1, mg);
+        *(l0 - i) = (T)(x0 - q0 * B32 + vmin);
+        *(l1 - i) = (T)(x1 - q1 * B32 + vmin);
+        x0 = q0;
+        x1 = q1;
+    }
+    *(l0 - (k - 1)) = (T)(x0 + vmin);
+    *(l1 - (k - 1)) = (T)(x1 + vmin);
+}
+
+template <typename T, uint32_t K>
+__device__ __forceinline__ void rev_quot2_k(T *l0, uint32_t &x0, T *l1, uint32_t &x1, uint32_t B32, Magic32 mg,
+                                            uint32_t vmin)
+{
+#pragma unroll
+    for (uint32_t i = 0; i < K; ++i) {
+        const uint32_t q0 = magic_div(x0, mg), q1 = magic_div(x1, mg);
+        *(l0 - i) = (T)(x0 - q0 * B32 + vmin);
+        *(l1 - i) = (T)(x1 - q1 * B32 + vmin);
+        x0 = q0;
+        x1 = q1;
+    }
+}
+
+// k digits of each, the quotients left in x0 and x1.
+template <typename T>
+__device__ __forceinline__ void rev_quot2(T *l0, uint32_t &x0, T *l1, uint32_t &x1, uint32_t k, uint32_t B32,
+                                          Magic32 mg, uint32_t vmin)
+{
+    switch (k) {
+    case 0: return;
+    case 1: rev_quot2_k<T, 1>(l0, x0, l1, x1, B32, mg, vmin); return;
+    case 2: rev_quot2_k<T, 2>(l0, x0, l1, x1, B32, mg, vmin); return;
+    case 3: rev_quot2_k<T, 3>(l0, x0, l1, x1, B32, mg, vmin); return;
+    case 4: rev_quot2_k<T, 4>(l0, x0, l1, x1, B32, mg, vmin); return;
+    case 5: rev_quot2_k<T, 5>(l0, x0, l1, x1, B32, mg, vmin); return;
+    default: break;
+    }
+    for (uint32_t i = 0; i < k; ++i) {
+        const uint32_t q0 = magic_div(x0, mg), q1 = magic_div(x1, mg);
+        *(l0 - i) = (T)(x0 - q0 * B32 + vmin);
+        *(l1 - i) = (T)(x1 - q1 * B32 + vmin);
+        x0 = q0;
+        x1 = q1;
+    }
+}
+
 // s = body R + r for R < 2^16 by long division with R's magic reciprocal:
 // the high 32-bit word first (any 32-bit dividend), then two 16-bit steps
 // whose partial dividends r 2^16 + 16 bits stay below R 2^16 <= 2^32.
@@ -811,6 +890,177 @@ __device__ __forceinline__ void store_rec(uint8_t *recs, const DecBlock &d, uint
     for (uint32_t i = 0; i < NV; ++i) dst[i] = v[i];
 }
 
+// Advanced words [jb, je) of one block by one warp (src holds them from word
+// jb on), two words per lane in lockstep (words j0 + lane and j0 + 32 +
+// lane) while more than 32 are left, then one: each word divided by its R_i, R_{i-1} and r_{i-1} taken from the
+// word before (the carry cR, cr for the first), then p_1 digits of every
+// word whatever its digit count (see below), the split sample re-joined.
+// Lanes past the range write into the junk slots.  qlast / plast: q and p of
+// word W - 1 when it is in the range.  Returns true for an invalid word.
+template <typename T, uint32_t WB>
+__device__ __forceinline__ bool adv_decode_words(const OrbitTable &ot, const DecBlock &k,
+                                                 const typename WordT<T, WB>::type *src, uint32_t jb, uint32_t je,
+                                                 uint32_t W, T *u, T *junk, uint32_t vmin, uint32_t n_b,
+                                                 uint32_t &cR, uint32_t &cr, uint32_t &qlast, uint32_t &plast)
+{
+    constexpr uint32_t FULLM = 0xFFFFFFFFu;
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t hstar = k.hstar, B32 = (uint32_t)k.B, p1 = k.p;
+    const uint32_t ns = WB == 64 ? p1 / hstar : 0u, rem0 = p1 - ns * hstar;
+    bool bad = false;
+    uint32_t j0 = jb;
+    for (; j0 + 32 < je; j0 += 64) {
+        const uint32_t i0 = j0 + lane, i1 = i0 + 32;
+        const bool v0 = i0 < je, v1 = i1 < je;
+        const SeriesEntry dummy{1u, p1, 0u, Magic32{0xFFFFFFFFu, 0xFFFFFFFFu, 0u}};  // R = 1: divides by one
+        SeriesEntry e0 = dummy, e1 = dummy;
+        uint64_t s0 = 0, s1 = 0;
+        if (v0) {
+            e0 = orbit_entry(ot, k.ov, i0);
+            s0 = src[i0 - jb];
+        }
+        if (v1) {
+            e1 = orbit_entry(ot, k.ov, i1);
+            s1 = src[i1 - jb];
+        }
+        uint32_t r0, r1;
+        uint64_t b0, b1;
+        if constexpr (WB == 32) {
+            const uint32_t q0 = magic_div((uint32_t)s0, e0.mgR), q1 = magic_div((uint32_t)s1, e1.mgR);
+            r0 = (uint32_t)s0 - q0 * e0.R;
+            r1 = (uint32_t)s1 - q1 * e1.R;
+            b0 = q0;
+            b1 = q1;
+        } else {
+            b0 = divmod_small64(s0, e0.R, e0.mgR, r0);
+            b1 = divmod_small64(s1, e1.R, e1.mgR, r1);
+        }
+        // R_{i-1} and r_{i-1}: the lane before, the last lane of the group
+        // before for word j0 + 32, the carry for word j0
+        uint32_t Rp0 = __shfl_up_sync(FULLM, e0.R, 1), rp0 = __shfl_up_sync(FULLM, r0, 1);
+        uint32_t Rp1 = __shfl_up_sync(FULLM, e1.R, 1), rp1 = __shfl_up_sync(FULLM, r1, 1);
+        const uint32_t R31 = __shfl_sync(FULLM, e0.R, 31), r31 = __shfl_sync(FULLM, r0, 31);
+        if (lane == 0) {
+            Rp0 = cR;
+            rp0 = cr;
+            Rp1 = R31;
+            rp1 = r31;
+        }
+        cR = __shfl_sync(FULLM, e1.R, 31);
+        cr = __shfl_sync(FULLM, r1, 31);
+        // every lane takes p_1 digits, whether its word holds p_1 or p_1 - 1
+        // samples, so the warp's control flow is the same for all words: a
+        // word of p_1 - 1 samples puts its top remainder r'_(i-1) in the p_1-th
+        // digit, stored at u[q_i - 1], the slot its split sample takes below
+        T *l0 = v0 ? u + e0.q + e0.p - 1 : junk + p1 - 1;
+        T *l1 = v1 ? u + e1.q + e1.p - 1 : junk + p1 - 1;
+        if constexpr (WB == 64) {
+            for (uint32_t t = 0; t < ns; ++t) {
+                uint64_t lo0, lo1;
+                b0 = divmod_inv64(b0, k.Dh, k.MD, lo0);
+                b1 = divmod_inv64(b1, k.Dh, k.MD, lo1);
+                rev_exact2<T>(l0, (uint32_t)lo0, l1, (uint32_t)lo1, hstar, B32, k.mg, vmin);
+                l0 -= hstar;
+                l1 -= hstar;
+            }
+            bad |= (v0 && (b0 >> 32) != 0) || (v1 && (b1 >> 32) != 0);
+        }
+        uint32_t x0 = (uint32_t)b0, x1 = (uint32_t)b1;
+        rev_quot2<T>(l0, x0, l1, x1, rem0, B32, k.mg, vmin);
+        if (v0) {
+            uint32_t top = x0;
+            if (e0.p != p1) {
+                top = (uint32_t)u[e0.q - 1] - vmin;
+                bad |= x0 != 0;
+            }
+            if (i0 == 0) {
+                bad |= top != 0;
+            } else {
+                const uint64_t val = (uint64_t)top * Rp0 + rp0;
+                bad |= val >= k.B;
+                u[e0.q - 1] = (T)(val + vmin);
+            }
+            if (e0.q + e0.p >= n_b) bad |= r0 != 0;
+            if (i0 == W - 1) {
+                qlast = e0.q;
+                plast = e0.p;
+            }
+        }
+        if (v1) {
+            uint32_t top = x1;
+            if (e1.p != p1) {
+                top = (uint32_t)u[e1.q - 1] - vmin;
+                bad |= x1 != 0;
+            }
+            const uint64_t val = (uint64_t)top * Rp1 + rp1;  // word j0 + 32 + lane is never word 0
+            bad |= val >= k.B;
+            u[e1.q - 1] = (T)(val + vmin);
+            if (e1.q + e1.p >= n_b) bad |= r1 != 0;
+            if (i1 == W - 1) {
+                qlast = e1.q;
+                plast = e1.p;
+            }
+        }
+    }
+    if (j0 < je) {  // 1-32 words left: one word per lane
+        const uint32_t i = j0 + lane;
+        const bool v = i < je;
+        SeriesEntry e{1u, p1, 0u, Magic32{0xFFFFFFFFu, 0xFFFFFFFFu, 0u}};
+        uint64_t sw = 0;
+        if (v) {
+            e = orbit_entry(ot, k.ov, i);
+            sw = src[i - jb];
+        }
+        uint32_t r;
+        uint64_t body;
+        if constexpr (WB == 32) {
+            const uint32_t q = magic_div((uint32_t)sw, e.mgR);
+            r = (uint32_t)sw - q * e.R;
+            body = q;
+        } else {
+            body = divmod_small64(sw, e.R, e.mgR, r);
+        }
+        uint32_t Rp = __shfl_up_sync(FULLM, e.R, 1), rp = __shfl_up_sync(FULLM, r, 1);
+        if (lane == 0) {
+            Rp = cR;
+            rp = cr;
+        }
+        cR = __shfl_sync(FULLM, e.R, 31);
+        cr = __shfl_sync(FULLM, r, 31);
+        if (v) {
+            T *last = u + e.q + e.p - 1;
+            if constexpr (WB == 64) {
+                for (uint32_t t = 0; t < ns; ++t) {
+                    uint64_t lo;
+                    body = divmod_inv64(body, k.Dh, k.MD, lo);
+                    rev_exact<T>(last, (uint32_t)lo, hstar, B32, k.mg, vmin);
+                    last -= hstar;
+                }
+                bad |= (body >> 32) != 0;
+            }
+            const uint32_t qtop = rev_quot<T>(last, (uint32_t)body, rem0, B32, k.mg, vmin);
+            uint32_t top = qtop;
+            if (e.p != p1) {
+                top = (uint32_t)u[e.q - 1] - vmin;
+                bad |= qtop != 0;
+            }
+            if (i == 0) {
+                bad |= top != 0;
+            } else {
+                const uint64_t val = (uint64_t)top * Rp + rp;
+                bad |= val >= k.B;
+                u[e.q - 1] = (T)(val + vmin);
+            }
+            if (e.q + e.p >= n_b) bad |= r != 0;
+            if (i == W - 1) {
+                qlast = e.q;
+                plast = e.p;
+            }
+        }
+    }
+    return bad;
+}
+
 template <uint32_t WB, uint32_t VAR, bool ORB>
 __device__ __forceinline__ DecBlock dec_setup(const uint8_t *in, uint64_t gb, uint32_t n_b, uint32_t L,
                                               const OrbitTable &ot,
@@ -953,72 +1203,9 @@ k_decode_w(const uint8_t *__restrict__ in, uint32_t L, T *__restrict__ out, uint
                     bad |= decode_basic_block<T, WB>(wsrc, u, u + L + kPad, 0, W, p, k.hstar, k.B, vmin, k.mg, k.Dh, k.MD);
                     if (k.lim != 0) bad |= (uint64_t)wsrc[W - 1] >= k.lim;
                 } else {
-                    const Word *src = wsrc;
-                    const uint32_t hstar = k.hstar, B32 = (uint32_t)k.B;
-                    const uint32_t p1 = k.p, ns = WB == 64 ? p1 / hstar : 0u, rem0 = p1 - ns * hstar;
                     uint32_t cR = 1, cr = 0, qlast = 0, plast = 0;
-                    for (uint32_t j0 = 0; j0 < W; j0 += 32) {
-                        const uint32_t i = j0 + lane;
-                        const bool valid = i < W;
-                        SeriesEntry e;
-                        uint64_t s = 0;
-                        if (valid) {
-                            e = orbit_entry(ot, k.ov, i);
-                            s = src[i];
-                        } else {
-                            e = SeriesEntry{1u, 0u, 0u, Magic32{0xFFFFFFFFu, 0xFFFFFFFFu, 0u}};
-                        }
-                        uint32_t r = 0;
-                        uint64_t body = 0;
-                        if (valid) {
-                            if constexpr (WB == 32) {
-                                const uint32_t q32 = magic_div((uint32_t)s, e.mgR);
-                                r = (uint32_t)s - q32 * e.R;
-                                body = q32;
-                            } else {
-                                body = divmod_small64(s, e.R, e.mgR, r);
-                            }
-                        }
-                        uint32_t Rp = __shfl_up_sync(0xFFFFFFFFu, e.R, 1);
-                        uint32_t rp = __shfl_up_sync(0xFFFFFFFFu, r, 1);
-                        if (lane == 0) {
-                            Rp = cR;
-                            rp = cr;
-                        }
-                        cR = __shfl_sync(0xFFFFFFFFu, e.R, 31);
-                        cr = __shfl_sync(0xFFFFFFFFu, r, 31);
-                        if (!valid) continue;
-                        // every lane takes p_1 digits, whether its word holds p_1 or p_1 - 1
-                        // samples, so the warp's control flow is the same for all words: a
-                        // word of p_1 - 1 samples puts its top remainder r'_(i-1) in the p_1-th
-                        // digit, stored at u[q_i - 1], the slot its split sample takes below
-                        T *last = u + e.q + e.p - 1;
-                        for (uint32_t t = 0; t < ns; ++t) {
-                            uint64_t lo;
-                            body = divmod_inv64(body, k.Dh, k.MD, lo);
-                            rev_exact<T>(last, (uint32_t)lo, hstar, B32, k.mg, vmin);
-                            last -= hstar;
-                        }
-                        bad |= (body >> 32) != 0;
-                        const uint32_t qtop = rev_quot<T>(last, (uint32_t)body, rem0, B32, k.mg, vmin);
-                        uint32_t top = qtop;
-                        if (e.p != p1) {
-                            top = (uint32_t)u[e.q - 1] - vmin;
-                            bad |= qtop != 0;
-                        }
-                        if (i == 0) {
-                            bad |= top != 0;
-                        } else {
-                            const uint64_t val = (uint64_t)top * Rp + rp;
-                            bad |= val >= k.B;
-                            u[e.q - 1] = (T)(val + vmin);
-                        }
-                        if (e.q + e.p >= n_b) bad |= r != 0;
-                        if (i == W - 1) {
-                            qlast = e.q;
-                            plast = e.p;
-                        }
-                    }
+                    bad |= adv_decode_words<T, WB>(ot, k, wsrc, 0, W, W, u, u + L + kPad, vmin, n_b, cR, cr, qlast,
+                                                   plast);
                     __syncwarp();
                     const uint32_t src_lane = (W - 1) & 31u;
                     qlast = __shfl_sync(0xFFFFFFFFu, qlast, src_lane);
@@ -1071,70 +1258,8 @@ k_decode_w(const uint8_t *__restrict__ in, uint32_t L, T *__restrict__ out, uint
                             bad |= decode_basic_block<T, WB>(wsrc, u, u + L + kPad, jb, je, k.p, k.hstar, k.B, vmin, k.mg,
                                                              k.Dh, k.MD);
                         } else {
-                            const uint32_t hstar = k.hstar, B32 = (uint32_t)k.B;
-                            const uint32_t p1 = k.p, ns = WB == 64 ? p1 / hstar : 0u, rem0 = p1 - ns * hstar;
-                            for (uint32_t j0 = jb; j0 < je; j0 += 32) {
-                                const uint32_t i = j0 + lane;
-                                const bool valid = i < je;
-                                SeriesEntry e;
-                                uint64_t s = 0;
-                                if (valid) {
-                                    e = orbit_entry(ot, k.ov, i);
-                                    s = wsrc[i - jb];
-                                } else {
-                                    e = SeriesEntry{1u, 0u, 0u, Magic32{0xFFFFFFFFu, 0xFFFFFFFFu, 0u}};
-                                }
-                                uint32_t r = 0;
-                                uint64_t body = 0;
-                                if (valid) {
-                                    if constexpr (WB == 32) {
-                                        const uint32_t q32 = magic_div((uint32_t)s, e.mgR);
-                                        r = (uint32_t)s - q32 * e.R;
-                                        body = q32;
-                                    } else {
-                                        body = divmod_small64(s, e.R, e.mgR, r);
-                                    }
-                                }
-                                uint32_t Rp = __shfl_up_sync(0xFFFFFFFFu, e.R, 1);
-                                uint32_t rp = __shfl_up_sync(0xFFFFFFFFu, r, 1);
-                                if (lane == 0) {
-                                    Rp = cR;
-                                    rp = cr;
-                                }
-                                cR = __shfl_sync(0xFFFFFFFFu, e.R, 31);
-                                cr = __shfl_sync(0xFFFFFFFFu, r, 31);
-                                if (!valid) continue;
-                                // every lane takes p_1 digits, whether its word holds p_1 or p_1 - 1
-                                // samples, so the warp's control flow is the same for all words: a
-                                // word of p_1 - 1 samples puts its top remainder r'_(i-1) in the p_1-th
-                                // digit, stored at u[q_i - 1], the slot its split sample takes below
-                                T *last = u + e.q + e.p - 1;
-                                for (uint32_t t = 0; t < ns; ++t) {
-                                    uint64_t lo;
-                                    body = divmod_inv64(body, k.Dh, k.MD, lo);
-                                    rev_exact<T>(last, (uint32_t)lo, hstar, B32, k.mg, vmin);
-                                    last -= hstar;
-                                }
-                                bad |= (body >> 32) != 0;
-                                const uint32_t qtop = rev_quot<T>(last, (uint32_t)body, rem0, B32, k.mg, vmin);
-                                uint32_t top = qtop;
-                                if (e.p != p1) {
-                                    top = (uint32_t)u[e.q - 1] - vmin;
-                                    bad |= qtop != 0;
-                                }
-                                if (i == 0) {
-                                    bad |= top != 0;
-                                } else {
-                                    const uint64_t val = (uint64_t)top * Rp + rp;
-                                    bad |= val >= k.B;
-                                    u[e.q - 1] = (T)(val + vmin);
-                                }
-                                if (e.q + e.p >= n_b) bad |= r != 0;
-                                if (i == W - 1) {
-                                    qlast = e.q;
-                                    plast = e.p;
-                                }
-                            }
+                            bad |= adv_decode_words<T, WB>(ot, k, wsrc, jb, je, W, u, u + L + kPad, vmin, n_b, cR, cr,
+                                                           qlast, plast);
                         }
                         __syncwarp();  // the buffer is free for the chunk after next
                         slot ^= 1u;
