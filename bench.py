@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--white-noise", type=int, default=0,
                     help="time N samples of the 65,536-sample white-noise workload's generator instead of camera "
                          "events (no CPU baseline or sweeps then)")
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=6)
     ap.add_argument("--cpu-events", type=int, default=0,
                     help="events in the oracle's CPU sample (0 = sized to ~15 s)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -861,7 +861,7 @@ def end_to_end(codec, x, n, steps, dev):
     sbuf = torch.empty(codec.bound(n), dtype=torch.uint8, device=dev)
     ybuf = torch.empty(n, dtype=torch.int16, device=dev)
 
-    def one():
+    def one():  # one step at a time: upload, compress, download the stream, decompress, download
         xin.copy_(host_in, non_blocking=True)
         _, nb = codec.compress(xin, out=sbuf)
         nbytes = int(nb.item())
@@ -880,8 +880,31 @@ def end_to_end(codec, x, n, steps, dev):
     dt = time.perf_counter() - t0
     assert torch.equal(host_out, host_in)
     raw = n * 2
+    seq = raw * steps / dt / GB
+    # the same round trips pipelined over consecutive steps (the package's
+    # RoundTrip): a step's upload overlaps the previous step's downloads
+    from paper_1805_01844_gb300.pipeline import RoundTrip
+
+    p = codec.params
+    rt = RoundTrip(p.variant, p.dtype_bits, p.word_bits, p.block_len, n, device=dev)
+    rt.submit(host_in)
+    rt.drain()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        rt.submit(host_in)
+    rt.drain()
+    dt = time.perf_counter() - t0
+    done = rt.completed()
+    for b in range(2):
+        assert torch.equal(rt.host_out[b], host_in)
+    nb = done[-1][1]
+    assert torch.equal(rt.host_stream[done[-1][0]][:nb], host_stream[:nb])
     return {"value": raw * steps / dt / GB, "unit": "GB/s", "h2d_bytes_per_step": raw,
-            "d2h_bytes_per_step": tot_stream // steps + raw + 8}
+            "d2h_bytes_per_step": tot_stream // steps + raw,
+            "pipelined": "consecutive steps overlap (an upload with the previous step's downloads), "
+                         "through paper_1805_01844_gb300.pipeline.RoundTrip",
+            "sequential_gbs": seq}
 
 
 if __name__ == "__main__":
