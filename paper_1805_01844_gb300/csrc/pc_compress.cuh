@@ -187,6 +187,9 @@ __device__ __forceinline__ void adv_words_orbit(const OrbitTable &ot, const Orbi
 #ifndef PCX_MINMAX_U16X2
 #define PCX_MINMAX_U16X2 1
 #endif
+#ifndef PCX_PACK_FLAT
+#define PCX_PACK_FLAT 1
+#endif
 #ifndef PCX_PACK_UNROLL
 #define PCX_PACK_UNROLL 1
 #endif
@@ -255,6 +258,52 @@ __device__ __forceinline__ void pack_basic_group(const T *u, uint32_t j0, uint32
     for (uint32_t k = 0; k < NK; ++k) {
         const uint32_t j = j0 + lane + 32 * k;
         if (FULL || j < W) dst[j] = acc[k];
+    }
+}
+
+// One basic word (as in pack_basic_group, for one lane): digits dg[0..p) of
+// raw samples, summed as 32-bit pieces (PackK).
+template <typename T, uint32_t WB>
+__device__ __forceinline__ typename WordOf<T, WB>::type basic_word_pk(const T *dg, uint32_t p, uint32_t B32,
+                                                                     PackK pk)
+{
+    uint32_t a = dg[p - 1];
+    if constexpr (WB == 32) {
+        for (int d = (int)p - 2; d >= 0; --d) a = a * B32 + (uint32_t)dg[d];
+        return a - pk.Kt;
+    } else {
+        const int p32 = (int)(pk.shape & 0xFFu), t = (int)(pk.shape >> 16);
+        int d = (int)p - 2;
+        for (; d >= (int)p - t; --d) a = a * B32 + (uint32_t)dg[d];
+        uint32_t lo = a - pk.Kt, hi = 0;
+        for (; d >= 0; d -= p32) {
+            a = dg[d];
+            for (int e = d - 1; e > d - p32; --e) a = a * B32 + (uint32_t)dg[e];
+            mad64(lo, hi, pk.D, a - pk.Kf);
+        }
+        return ((uint64_t)hi << 32) | lo;
+    }
+}
+
+// Basic words of a whole tile with few words per block (short blocks): the
+// tile's words taken as one sequence, a lane per word, so lanes do not idle
+// on blocks of fewer than 32 words.  Word g belongs to the last block b with
+// woff[b] <= g (a block without words shares its offset with the next).
+template <typename T, uint32_t WB, uint32_t NT>
+__device__ __forceinline__ void pack_basic_flat(const uint8_t *stage, uint32_t stage_bytes, const uint32_t *woff,
+                                                const uint32_t *p_of, const uint64_t *B_of, const PackK *pk_of,
+                                                uint32_t nblk, uint32_t agg, typename WordOf<T, WB>::type *dst)
+{
+    for (uint32_t g = threadIdx.x; g < agg; g += NT) {
+        uint32_t lo = 0, hi = nblk - 1;
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi + 1) >> 1;
+            if (woff[mid] <= g) lo = mid;
+            else hi = mid - 1;
+        }
+        const uint32_t p = p_of[lo];
+        const T *dg = reinterpret_cast<const T *>(stage + (uint64_t)lo * stage_bytes) + (g - woff[lo]) * p;
+        dst[g] = basic_word_pk<T, WB>(dg, p, (uint32_t)B_of[lo], pk_of[lo]);
     }
 }
 
@@ -489,7 +538,14 @@ __device__ void compress_tile(const StreamArgs &sa, uint64_t tile, uint8_t *smem
             }
         }
         Word *payload = reinterpret_cast<Word *>(sa.out + payload_off);
-        for (uint32_t b = warp; b < nblk; b += (NT / 32)) {
+        // short basic blocks (fewer than 16 words on average): a lane per word
+        // over the whole tile instead of a warp per block (measured at 2^30
+        // white-noise samples, w = 64: L = 64 +14 %, L = 128 +8 %)
+        const bool flat = VAR == PC_VARIANT_BASIC && PCX_PACK_FLAT && bv.agg < 16u * nblk;
+        if (flat)
+            pack_basic_flat<T, WB, NT>(smem, cfg.stage_bytes, bv.woff, bv.p, bv.B, bv.pk, nblk, bv.agg,
+                                       payload + bv.excl);
+        for (uint32_t b = warp; b < nblk && !flat; b += (NT / 32)) {
             const uint32_t W = bv.W[b];
             if (W == 0) continue;
             const T *u = reinterpret_cast<const T *>(smem + (uint64_t)b * cfg.stage_bytes);

@@ -160,3 +160,23 @@ def test_launch_configuration_independence():
     for _ in range(3):
         got, _, _ = gpu_compress(x, 0, 64, 1024)
         assert got == want
+
+
+@pytest.mark.parametrize("variant,w", CONFIGS)
+@pytest.mark.parametrize("dtype", [np.uint16, np.uint32])
+@pytest.mark.parametrize("L", [32, 64, 128, 256])
+def test_short_blocks_with_constant_blocks_among_them(variant, w, dtype, L):
+    """Short blocks (a few words each, packed a lane per word across the
+    tile's blocks), one in three constant (no words) and some wide, over many
+    tiles with a ragged last block."""
+    rng = np.random.default_rng(L + w + 3 * variant)
+    n_blocks = 32 * 40 + 7
+    hi = np.iinfo(dtype).max
+    x = np.clip(rng.normal(900, 30, n_blocks * L), 0, hi).astype(dtype)
+    for b in range(n_blocks):
+        r = int(rng.integers(0, 6))
+        if r < 2:
+            x[b * L:(b + 1) * L] = int(rng.integers(0, hi))
+        elif r == 2:
+            x[b * L + int(rng.integers(0, L))] = hi
+    check(x[: n_blocks * L - L // 2 + 1], variant, w, L)
