@@ -417,13 +417,18 @@ __device__ void compress_tile(const StreamArgs &sa, uint64_t tile, uint8_t *smem
         // block, completing on the warp's mbarrier; the ragged end of the
         // last block comes element by element
         constexpr uint32_t VE = 16 / sizeof(T);
-        if (lane == 0) {  // (a CTA whose staging died takes no further tile, so it never comes here again)
+        {  // (a CTA whose staging died takes no further tile, so it never comes here again)
+            // lane i issues the copy of the warp's i-th block (blocks warp,
+            // warp + NT / 32, ...), once lane 0 has set the expected bytes
+            constexpr uint32_t NW = NT / 32;
             uint32_t bytes = 0;
-            for (uint32_t b = warp; b < nblk; b += (NT / 32))
+            for (uint32_t b = warp + lane * NW; b < nblk; b += 32 * NW)
                 bytes += ((uint32_t)umin64(L, cnt - (uint64_t)b * L) / VE) * 16u;
+            bytes = __reduce_add_sync(0xFFFFFFFFu, bytes);
             fence_proxy_async_smem();  // the stage's earlier generic accesses before the async writes
-            mbar_arrive_expect_tx(&g_stage_bar[warp], bytes);
-            for (uint32_t b = warp; b < nblk; b += (NT / 32)) {
+            if (lane == 0) mbar_arrive_expect_tx(&g_stage_bar[warp], bytes);
+            __syncwarp();
+            for (uint32_t b = warp + lane * NW; b < nblk; b += 32 * NW) {
                 const uint32_t nb16 = ((uint32_t)umin64(L, cnt - (uint64_t)b * L) / VE) * 16u;
                 if (nb16)
                     bulk_copy_g2s(smem + (uint64_t)b * cfg.stage_bytes, in + (blk0 + b) * L, nb16,
@@ -670,14 +675,16 @@ __device__ void compress_tile_multi(const StreamArgs &sa, uint64_t tile, uint8_t
     auto stage = [&](uint32_t h, bool again) {
         const uint32_t m = nh(h);
         __syncwarp();  // the warp's earlier accesses to its slots come first
-        const bool dead = stage_dead();
-        if (lane == 0 && !dead) {
+        const bool dead = __any_sync(0xFFFFFFFFu, stage_dead());
+        if (!dead) {  // lane i copies the warp's i-th block, once lane 0 has set the expected bytes
             uint32_t bytes = 0;
-            for (uint32_t b = warp; b < m; b += NW) bytes += (n_of(h * H + b) / VE) * 16u;
+            for (uint32_t b = warp + lane * NW; b < m; b += 32 * NW) bytes += (n_of(h * H + b) / VE) * 16u;
+            bytes = __reduce_add_sync(0xFFFFFFFFu, bytes);
             const uint64_t policy = again ? l2_policy_evict_last() : l2_policy_evict_first();
             fence_proxy_async_smem();
-            mbar_arrive_expect_tx(&g_stage_bar[warp], bytes);
-            for (uint32_t b = warp; b < m; b += NW) {
+            if (lane == 0) mbar_arrive_expect_tx(&g_stage_bar[warp], bytes);
+            __syncwarp();
+            for (uint32_t b = warp + lane * NW; b < m; b += 32 * NW) {
                 const uint32_t nb16 = (n_of(h * H + b) / VE) * 16u;
                 if (nb16)
                     bulk_copy_g2s_hint(slot(b), in + (blk0 + h * H + b) * L, nb16, &g_stage_bar[warp], policy);
