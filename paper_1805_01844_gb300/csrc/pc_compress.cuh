@@ -435,11 +435,11 @@ __device__ void compress_tile(const StreamArgs &sa, uint64_t tile, uint8_t *smem
                                   &g_stage_bar[warp]);
             }
         }
-        for (uint32_t b = warp; b < nblk; b += (NT / 32)) {
-            const uint32_t n_b = (uint32_t)umin64(L, cnt - (uint64_t)b * L);
-            uint8_t *dst = smem + (uint64_t)b * cfg.stage_bytes;
-            for (uint32_t e = n_b / VE * VE + lane; e < n_b; e += 32)
-                reinterpret_cast<T *>(dst)[e] = in[(blk0 + b) * L + e];
+        if (cnt % VE != 0 && (nblk - 1) % (NT / 32) == warp) {  // only the stream's last block can be ragged
+            const uint32_t b = nblk - 1;
+            const uint32_t n_b = (uint32_t)(cnt - (uint64_t)b * L);
+            T *dst = reinterpret_cast<T *>(smem + (uint64_t)b * cfg.stage_bytes);
+            for (uint32_t e = n_b / VE * VE + lane; e < n_b; e += 32) dst[e] = in[(blk0 + b) * L + e];
         }
         stage_wait(warp, phase, ws, limit_ns);
         ++phase;  // every warp's barrier completed one phase
@@ -690,7 +690,8 @@ __device__ void compress_tile_multi(const StreamArgs &sa, uint64_t tile, uint8_t
                     bulk_copy_g2s_hint(slot(b), in + (blk0 + h * H + b) * L, nb16, &g_stage_bar[warp], policy);
             }
         }
-        for (uint32_t b = warp; b < m; b += NW) {
+        if (n % VE != 0 && blk0 + h * H + m == n_blocks && (m - 1) % NW == warp) {  // the stream's ragged last block
+            const uint32_t b = m - 1;
             const uint32_t n_b = n_of(h * H + b);
             T *dst = slot(b);
             for (uint32_t e = n_b / VE * VE + lane; e < n_b; e += 32) dst[e] = in[(blk0 + h * H + b) * L + e];
