@@ -11,6 +11,9 @@ Functions and the passage each follows:
   adv_schedule     Sec. 3.2, the split-base series (p_i, R_i, R'_i, q_i)
   adv_pack/...     Sec. 3.2, word s_i of the series and its inverse
   compress/...     Sec. 3.3 blocked compression, Fig. 2 block header
+  compress_v2/...  the same with (L, w) chosen per segment of the data, one
+                   code byte each (format version 2; the block-size choice of
+                   Sec. 3.3 and Sec. 4.2, Fig. 7)
 """
 import ctypes
 
@@ -63,6 +66,12 @@ def lib():
         L.po_compress.restype = ctypes.c_int
         L.po_decompress.argtypes = [vp, u64, vp, u64, _u64p]
         L.po_decompress.restype = ctypes.c_int
+        L.po_bound_v2.argtypes = [uint, uint, u64, u64, _u64p]
+        L.po_bound_v2.restype = ctypes.c_int
+        L.po_compress_v2.argtypes = [vp, u64, uint, uint, u64, vp, vp, u64, _u64p]
+        L.po_compress_v2.restype = ctypes.c_int
+        L.po_decompress_v2.argtypes = [vp, u64, vp, u64, _u64p]
+        L.po_decompress_v2.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -173,4 +182,62 @@ def decompress(stream, capacity=None):
                              out.ctypes.data, capacity, ctypes.byref(n_out))
     if st != OK:
         raise OracleError(st, "decompress")
+    return out[:n_out.value].copy()
+
+
+def v2_code(block_len, word_bits):
+    """Format-2 code byte of a segment: log2(L) | (w == 64) << 7."""
+    k = int(block_len).bit_length() - 1
+    if block_len != 1 << k or k > 13 or word_bits not in (32, 64):
+        raise ValueError("block length must be a power of two <= 8192, words 32 or 64 bits")
+    return k | (0x80 if word_bits == 64 else 0)
+
+
+def bound_v2(variant, dtype_bits, seg_len, n):
+    out = ctypes.c_uint64(0)
+    st = lib().po_bound_v2(variant, dtype_bits, seg_len, n, ctypes.byref(out))
+    if st != OK:
+        raise OracleError(st, "bound_v2")
+    return int(out.value)
+
+
+def compress_v2(x, variant, seg_len, codes):
+    """Format-2 stream of x: segment s of seg_len samples compressed with the
+    (L, w) of codes[s] (see v2_code)."""
+    x = np.ascontiguousarray(x)
+    d = {np.dtype(np.uint16): 16, np.dtype(np.uint32): 32}[x.dtype]
+    codes = np.ascontiguousarray(np.asarray(codes, dtype=np.uint8))
+    n_seg = -(-x.size // seg_len)
+    if codes.size < n_seg:
+        raise ValueError("one code per segment")
+    cap = bound_v2(variant, d, seg_len, x.size)
+    out = np.zeros(cap, dtype=np.uint8)
+    nbytes = ctypes.c_uint64(0)
+    st = lib().po_compress_v2(x.ctypes.data, x.size, variant, d, seg_len, codes.ctypes.data if codes.size else None,
+                              out.ctypes.data, cap, ctypes.byref(nbytes))
+    if st != OK:
+        raise OracleError(st, "compress_v2")
+    return out[:nbytes.value].tobytes()
+
+
+def header_v2(stream):
+    b = bytes(stream[:HEADER_BYTES])
+    return dict(magic=b[0:4], version=int.from_bytes(b[4:6], "little"), variant=b[6], dtype_bits=b[7],
+                seg_len=int.from_bytes(b[12:16], "little"), n_samples=int.from_bytes(b[16:24], "little"),
+                n_segments=int.from_bytes(b[24:32], "little"), body_bytes=int.from_bytes(b[32:40], "little"))
+
+
+def decompress_v2(stream, capacity=None):
+    """Inverse of compress_v2; raises OracleError on a corrupt stream."""
+    buf = np.frombuffer(bytes(stream), dtype=np.uint8)
+    h = header_v2(stream) if len(buf) >= HEADER_BYTES else dict(dtype_bits=16, n_samples=0)
+    dt = np.uint32 if h["dtype_bits"] == 32 else np.uint16
+    if capacity is None:
+        capacity = h["n_samples"] if h["n_samples"] < (1 << 34) else 0
+    out = np.zeros(max(capacity, 1), dtype=dt)
+    n_out = ctypes.c_uint64(0)
+    st = lib().po_decompress_v2(buf.ctypes.data if len(buf) else None, len(buf), out.ctypes.data, capacity,
+                                ctypes.byref(n_out))
+    if st != OK:
+        raise OracleError(st, "decompress_v2")
     return out[:n_out.value].copy()

@@ -24,6 +24,10 @@
  *   po_compress /
  *   po_decompress   -- Sec. 3.3 (blocked compression) and Fig. 2 (minimum
  *                      then base stored once per block, then the packed data).
+ *   po_*_v2         -- the same blocked compression with the block length
+ *                      and word size chosen per segment of the data (the
+ *                      block-size choice of Sec. 3.3 and Sec. 4.2, Fig. 7),
+ *                      one code byte per segment (format version 2).
  *
  * Readings where the paper is silent or garbled (each is listed in the design
  * notes of the repository):
@@ -510,6 +514,198 @@ int po_decompress(const uint8_t *in, uint64_t in_bytes, void *out, uint64_t cap,
     }
     free(u_buf);
     free(w_buf);
+    *n_out = n;
+    return PO_OK;
+}
+
+/* --------------------------- segmented stream (format version 2) ----- */
+
+/* The block length is the parameter the paper tunes by hand from ratio
+ * curves (Sec. 3.3, Sec. 4.2 Fig. 7).  A version-2 stream lets that choice
+ * change along the data: the samples are cut into segments of seg_len
+ * samples, and each segment is compressed blockwise (as above) with its own
+ * block length L and word size w, recorded in one code byte.  Layout (all
+ * little-endian):
+ *   header, 64 bytes:  "PCMP", u16 version = 2, u8 variant, u8 dtype_bits,
+ *                      4 zero bytes, u32 seg_len, u64 n_samples,
+ *                      u64 n_segments, u64 body_bytes, 24 zero bytes
+ *   codes:             one byte per segment, log2(L) | (w == 64) << 7, L a
+ *                      power of two in [1, 8192]; zero-padded to a multiple
+ *                      of 8 bytes
+ *   bodies:            per segment in order: its block table (vmin, B - 1),
+ *                      zero-padded to a multiple of 8 bytes, then its packed
+ *                      words, zero-padded to a multiple of 8 bytes
+ * A segment's body size follows from its table alone (its word counts), so
+ * a reader finds segment k by summing the bodies before it. */
+
+#define PO_V2_MAX_LOG2_L 13u
+
+static uint64_t po_round8(uint64_t x) { return (x + 7) / 8 * 8; }
+
+static int po_v2_code_ok(unsigned code)
+{
+    return (code & 0x60u) == 0 && (code & 0x1Fu) <= PO_V2_MAX_LOG2_L;
+}
+
+static uint64_t po_v2_L(unsigned code) { return (uint64_t)1 << (code & 0x1Fu); }
+static unsigned po_v2_w(unsigned code) { return (code & 0x80u) ? 64u : 32u; }
+
+/* Largest body of a segment of n_s samples under code `code`: its table
+ * plus the largest word count of the blocked bound above. */
+static uint64_t po_v2_body_bound(unsigned variant, unsigned d, unsigned code, uint64_t n_s)
+{
+    uint64_t L = po_v2_L(code), v1;
+    unsigned w = po_v2_w(code);
+    uint64_t nb = (n_s + L - 1) / L;
+    po_bound(variant, d, w, L, n_s, &v1);
+    uint64_t word_bytes = v1 - PO_HEADER_BYTES - po_table_bytes(nb, d);
+    return po_round8(nb * 2 * (d / 8)) + po_round8(word_bytes);
+}
+
+/* Worst-case size of a version-2 stream of n samples, over every code. */
+int po_bound_v2(unsigned variant, unsigned d, uint64_t seg_len, uint64_t n, uint64_t *max_bytes)
+{
+    if (!po_params_ok(variant, d, 32, seg_len)) return PO_ERR_INVALID_ARG;
+    uint64_t n_seg = (n + seg_len - 1) / seg_len;
+    uint64_t total = PO_HEADER_BYTES + po_round8(n_seg);
+    for (int last = 0; last < 2; ++last) {
+        uint64_t ns, count;
+        if (n_seg == 0) break;
+        if (!last) { ns = seg_len; count = n_seg - 1; }
+        else { ns = n - (n_seg - 1) * seg_len; count = 1; }
+        if (count == 0) continue;
+        uint64_t worst = 0;
+        for (unsigned k = 0; k <= PO_V2_MAX_LOG2_L; ++k)
+            for (unsigned wide = 0; wide < 2; ++wide) {
+                uint64_t b = po_v2_body_bound(variant, d, k | (wide << 7), ns);
+                if (b > worst) worst = b;
+            }
+        total += count * worst;
+    }
+    *max_bytes = total;
+    return PO_OK;
+}
+
+/* Each segment compressed alone by po_compress with its (L, w); its table
+ * entries and words then move into the segment's body. */
+int po_compress_v2(const void *in, uint64_t n, unsigned variant, unsigned d, uint64_t seg_len,
+                   const uint8_t *codes, uint8_t *out, uint64_t cap, uint64_t *out_bytes)
+{
+    if (!po_params_ok(variant, d, 32, seg_len)) return PO_ERR_INVALID_ARG;
+    uint64_t n_seg = (n + seg_len - 1) / seg_len;
+    for (uint64_t s = 0; s < n_seg; ++s)
+        if (!po_v2_code_ok(codes[s])) return PO_ERR_INVALID_ARG;
+    unsigned db = d / 8;
+    uint64_t pos = PO_HEADER_BYTES + po_round8(n_seg);
+    if (cap < pos) return PO_ERR_CAPACITY;
+    memset(out, 0, pos);
+    for (uint64_t s = 0; s < n_seg; ++s) out[PO_HEADER_BYTES + s] = codes[s];
+    for (uint64_t s = 0; s < n_seg; ++s) {
+        uint64_t start = s * seg_len;
+        uint64_t n_s = n - start < seg_len ? n - start : seg_len;
+        uint64_t L = po_v2_L(codes[s]);
+        unsigned w = po_v2_w(codes[s]), wb = w / 8;
+        uint64_t v1cap, v1bytes;
+        po_bound(variant, d, w, L, n_s, &v1cap);
+        uint8_t *v1 = (uint8_t *)malloc(v1cap);
+        if (!v1) return PO_ERR_INVALID_ARG;
+        const uint8_t *src = (const uint8_t *)in + start * db;
+        int st = po_compress(src, n_s, variant, d, w, L, v1, v1cap, &v1bytes);
+        if (st != PO_OK) { free(v1); return st; }
+        uint64_t nb = get_le(v1 + 24, 8), pw = get_le(v1 + 32, 8);
+        uint64_t tb = nb * 2 * db, body = po_round8(tb) + po_round8(pw * wb);
+        if (cap - pos < body) { free(v1); return PO_ERR_CAPACITY; }
+        memset(out + pos, 0, body);
+        memcpy(out + pos, v1 + PO_HEADER_BYTES, tb);
+        memcpy(out + pos + po_round8(tb), v1 + PO_HEADER_BYTES + po_table_bytes(nb, d), pw * wb);
+        pos += body;
+        free(v1);
+    }
+    memcpy(out, "PCMP", 4);
+    put_le(out + 4, 2, 2);
+    out[6] = (uint8_t)variant;
+    out[7] = (uint8_t)d;
+    put_le(out + 12, seg_len, 4);
+    put_le(out + 16, n, 8);
+    put_le(out + 24, n_seg, 8);
+    put_le(out + 32, pos - PO_HEADER_BYTES - po_round8(n_seg), 8);
+    *out_bytes = pos;
+    return PO_OK;
+}
+
+static int po_zero(const uint8_t *p, uint64_t n)
+{
+    for (uint64_t i = 0; i < n; ++i) if (p[i] != 0) return 0;
+    return 1;
+}
+
+int po_decompress_v2(const uint8_t *in, uint64_t in_bytes, void *out, uint64_t cap, uint64_t *n_out)
+{
+    *n_out = 0;
+    if (in_bytes < PO_HEADER_BYTES) return PO_ERR_CORRUPT;
+    if (memcmp(in, "PCMP", 4) != 0 || get_le(in + 4, 2) != 2) return PO_ERR_CORRUPT;
+    unsigned variant = in[6], d = in[7];
+    uint64_t seg_len = get_le(in + 12, 4), n = get_le(in + 16, 8);
+    uint64_t n_seg = get_le(in + 24, 8), body_bytes = get_le(in + 32, 8);
+    if (!po_zero(in + 8, 4) || !po_zero(in + 40, 24)) return PO_ERR_CORRUPT;
+    if (!po_params_ok(variant, d, 32, seg_len)) return PO_ERR_CORRUPT;
+    if (n_seg != (n + seg_len - 1) / seg_len) return PO_ERR_CORRUPT;
+    /* codes and bodies must lie inside the buffer */
+    if (n_seg > in_bytes - PO_HEADER_BYTES) return PO_ERR_CORRUPT;
+    uint64_t pos = PO_HEADER_BYTES + po_round8(n_seg);
+    if (pos > in_bytes || body_bytes > in_bytes - pos) return PO_ERR_CORRUPT;
+    uint64_t end = pos + body_bytes;
+    if (!po_zero(in + PO_HEADER_BYTES + n_seg, pos - PO_HEADER_BYTES - n_seg)) return PO_ERR_CORRUPT;
+    if (n > cap) return PO_ERR_CAPACITY;
+    unsigned db = d / 8;
+    uint64_t dmax = d == 16 ? 0xFFFFull : 0xFFFFFFFFull;
+    for (uint64_t s = 0; s < n_seg; ++s) {
+        unsigned code = in[PO_HEADER_BYTES + s];
+        if (!po_v2_code_ok(code)) return PO_ERR_CORRUPT;
+        uint64_t start = s * seg_len;
+        uint64_t n_s = n - start < seg_len ? n - start : seg_len;
+        uint64_t L = po_v2_L(code);
+        unsigned w = po_v2_w(code), wb = w / 8;
+        uint64_t nb = (n_s + L - 1) / L, tb = nb * 2 * db;
+        if (po_round8(tb) > end - pos) return PO_ERR_CORRUPT;
+        const uint8_t *table = in + pos;
+        if (!po_zero(table + tb, po_round8(tb) - tb)) return PO_ERR_CORRUPT;
+        uint64_t W = 0;
+        for (uint64_t b = 0; b < nb; ++b) {
+            uint64_t n_b = n_s - b * L < L ? n_s - b * L : L;
+            uint64_t vmin = get_le(table + b * 2 * db, db), Bm1 = get_le(table + b * 2 * db + db, db);
+            if (vmin + Bm1 > dmax) return PO_ERR_CORRUPT;
+            W += po_count(variant, Bm1 + 1, w, n_b);
+        }
+        uint64_t words_at = pos + po_round8(tb);
+        if (W > (end - words_at) / wb || po_round8(W * wb) > end - words_at) return PO_ERR_CORRUPT;
+        if (!po_zero(in + words_at + W * wb, po_round8(W * wb) - W * wb)) return PO_ERR_CORRUPT;
+        /* the blocks of the segment, as in po_decompress */
+        uint64_t *u_buf = (uint64_t *)malloc((L + 2) * sizeof(uint64_t));
+        uint64_t *w_buf = (uint64_t *)malloc((L + 2) * sizeof(uint64_t));
+        if (!u_buf || !w_buf) { free(u_buf); free(w_buf); return PO_ERR_INVALID_ARG; }
+        uint64_t off = 0;
+        for (uint64_t b = 0; b < nb; ++b) {
+            uint64_t n_b = n_s - b * L < L ? n_s - b * L : L;
+            uint64_t vmin = get_le(table + b * 2 * db, db);
+            uint64_t B = get_le(table + b * 2 * db + db, db) + 1;
+            uint64_t Wb = po_count(variant, B, w, n_b);
+            for (uint64_t j = 0; j < Wb; ++j) w_buf[j] = get_le(in + words_at + (off + j) * wb, wb);
+            int st = variant == 0 ? po_basic_unpack(B, w, w_buf, Wb, n_b, u_buf)
+                                  : po_adv_unpack(B, w, w_buf, Wb, n_b, u_buf);
+            if (st != PO_OK) { free(u_buf); free(w_buf); return st; }
+            for (uint64_t i = 0; i < n_b; ++i) {
+                uint64_t v = u_buf[i] + vmin, k = start + b * L + i;
+                if (d == 16) ((uint16_t *)out)[k] = (uint16_t)v;
+                else ((uint32_t *)out)[k] = (uint32_t)v;
+            }
+            off += Wb;
+        }
+        free(u_buf);
+        free(w_buf);
+        pos = words_at + po_round8(W * wb);
+    }
+    if (pos != end) return PO_ERR_CORRUPT;
     *n_out = n;
     return PO_OK;
 }

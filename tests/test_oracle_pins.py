@@ -431,3 +431,78 @@ def test_exhaustive_label_sizes_follow_the_closed_form():
         nb = 4096 // L
         want = 64 + (nb * 4 + 15) // 16 * 16 + nb * (-(-L // p)) * (w // 8)
         assert sizes[0, o] == want and sizes[1, o] == want, (o, sizes[0, o], want)
+
+
+# --------------------------------------- segmented streams (format 2)
+
+
+def test_segmented_stream_worked_example(golden_dir):
+    """Per-segment (L, w) codes in one stream, worked by hand byte by byte."""
+    g = _read_golden(golden_dir, "segmented_stream_worked_example.txt")
+    vals = np.array([int(t) for t in g["values"].split()], dtype=np.uint16)
+    seg_len = int(g["seg_len"])
+    codes = [oracle.v2_code(int(a), int(b)) for a, b in (t.split(":") for t in g["segments"].split())]
+    assert codes == [int(t, 16) for t in g["codes"].split()]
+    stream = oracle.compress_v2(vals, 0, seg_len, codes)
+    assert stream == bytes.fromhex(g["stream_hex"])
+    assert np.array_equal(oracle.decompress_v2(stream), vals)
+
+
+def _v2_size_closed_form(x, variant, seg_len, codes):
+    """Size of a format-2 stream from Eq. 1-2's word counts per block."""
+    d = x.dtype.itemsize * 8
+    n_seg = -(-x.size // seg_len)
+    total = 64 + -(-n_seg // 8) * 8
+    for s in range(n_seg):
+        seg = x[s * seg_len:(s + 1) * seg_len].astype(np.int64)
+        L, w = 1 << (codes[s] & 0x1F), 64 if codes[s] & 0x80 else 32
+        nb = -(-seg.size // L)
+        W = 0
+        for b in range(nb):
+            blk = seg[b * L:(b + 1) * L]
+            B = int(blk.max() - blk.min() + 1)
+            if B > 1:
+                if variant == 0:
+                    p = 0
+                    while B ** (p + 1) <= 2 ** w - 1:
+                        p += 1
+                    W += -(-blk.size // max(p, 1))
+                else:
+                    W += oracle.pack_count(1, B, w, blk.size)
+        total += -(-nb * 2 * (d // 8) // 8) * 8 + -(-W * (w // 8) // 8) * 8
+    return total
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("dtype", [np.uint16, np.uint32])
+def test_segmented_stream_sizes_and_round_trip(variant, dtype):
+    """Every segment with its own code (all 28 codes, ragged last segment):
+    the size is the closed form of the per-block word counts plus the 8-byte
+    paddings, the stream decodes back exactly, and a format-1 reader rejects
+    it."""
+    rng = np.random.default_rng(5 + variant)
+    seg_len = 700
+    x = np.clip(rng.normal(3000, 40, 28 * seg_len + 123), 0, np.iinfo(dtype).max).astype(dtype)
+    x[rng.integers(0, x.size, 30)] = np.iinfo(dtype).max // 3
+    codes = [k | (0x80 if wide else 0) for k in range(14) for wide in (0, 1)] + [0x87]
+    s = oracle.compress_v2(x, variant, seg_len, codes)
+    assert len(s) == _v2_size_closed_form(x, variant, seg_len, codes)
+    assert len(s) <= oracle.bound_v2(variant, x.dtype.itemsize * 8, seg_len, x.size)
+    assert np.array_equal(oracle.decompress_v2(s), x)
+    with pytest.raises(oracle.OracleError):
+        oracle.decompress(s)
+
+
+def test_segmented_stream_rejects_bad_codes_and_bytes():
+    x = np.arange(40, dtype=np.uint16) * 7
+    s = bytearray(oracle.compress_v2(x, 1, 16, [0x84, 0x03, 0x8D]))
+    assert np.array_equal(oracle.decompress_v2(bytes(s)), x)
+    for pos, val in [(64, 0x0E), (64, 0x24), (67, 1), (8, 1), (4, 1), (len(s) - 1, 0xFF)]:
+        bad = bytearray(s)
+        bad[pos] = val if bad[pos] != val else val ^ 1
+        with pytest.raises(oracle.OracleError):
+            oracle.decompress_v2(bytes(bad))
+    with pytest.raises(oracle.OracleError):
+        oracle.decompress_v2(bytes(s[:-8]))
+    with pytest.raises(ValueError):
+        oracle.v2_code(96, 32)
