@@ -532,11 +532,15 @@ int po_decompress(const uint8_t *in, uint64_t in_bytes, void *out, uint64_t cap,
  *   codes:             one byte per segment, log2(L) | (w == 64) << 7, L a
  *                      power of two in [1, 8192]; zero-padded to a multiple
  *                      of 8 bytes
+ *   sizes:             per segment, u32 body size in units of 8 bytes;
+ *                      zero-padded to a multiple of 8 bytes
  *   bodies:            per segment in order: its block table (vmin, B - 1),
  *                      zero-padded to a multiple of 8 bytes, then its packed
  *                      words, zero-padded to a multiple of 8 bytes
- * A segment's body size follows from its table alone (its word counts), so
- * a reader finds segment k by summing the bodies before it. */
+ * A segment's body size also follows from its table alone (its word
+ * counts); it is stored so that a reader finds every segment from a prefix
+ * sum of the sizes, without walking the bodies one after another, and a
+ * stored size that disagrees with the table is a corrupt stream. */
 
 #define PO_V2_MAX_LOG2_L 13u
 
@@ -567,7 +571,7 @@ int po_bound_v2(unsigned variant, unsigned d, uint64_t seg_len, uint64_t n, uint
 {
     if (!po_params_ok(variant, d, 32, seg_len)) return PO_ERR_INVALID_ARG;
     uint64_t n_seg = (n + seg_len - 1) / seg_len;
-    uint64_t total = PO_HEADER_BYTES + po_round8(n_seg);
+    uint64_t total = PO_HEADER_BYTES + po_round8(n_seg) + po_round8(4 * n_seg);
     for (int last = 0; last < 2; ++last) {
         uint64_t ns, count;
         if (n_seg == 0) break;
@@ -596,7 +600,8 @@ int po_compress_v2(const void *in, uint64_t n, unsigned variant, unsigned d, uin
     for (uint64_t s = 0; s < n_seg; ++s)
         if (!po_v2_code_ok(codes[s])) return PO_ERR_INVALID_ARG;
     unsigned db = d / 8;
-    uint64_t pos = PO_HEADER_BYTES + po_round8(n_seg);
+    uint64_t sizes_at = PO_HEADER_BYTES + po_round8(n_seg);
+    uint64_t bodies_at = sizes_at + po_round8(4 * n_seg), pos = bodies_at;
     if (cap < pos) return PO_ERR_CAPACITY;
     memset(out, 0, pos);
     for (uint64_t s = 0; s < n_seg; ++s) out[PO_HEADER_BYTES + s] = codes[s];
@@ -618,6 +623,8 @@ int po_compress_v2(const void *in, uint64_t n, unsigned variant, unsigned d, uin
         memset(out + pos, 0, body);
         memcpy(out + pos, v1 + PO_HEADER_BYTES, tb);
         memcpy(out + pos + po_round8(tb), v1 + PO_HEADER_BYTES + po_table_bytes(nb, d), pw * wb);
+        if (body / 8 > 0xFFFFFFFFull) { free(v1); return PO_ERR_UNSUPPORTED; }
+        put_le(out + sizes_at + 4 * s, body / 8, 4);
         pos += body;
         free(v1);
     }
@@ -628,7 +635,7 @@ int po_compress_v2(const void *in, uint64_t n, unsigned variant, unsigned d, uin
     put_le(out + 12, seg_len, 4);
     put_le(out + 16, n, 8);
     put_le(out + 24, n_seg, 8);
-    put_le(out + 32, pos - PO_HEADER_BYTES - po_round8(n_seg), 8);
+    put_le(out + 32, pos - bodies_at, 8);
     *out_bytes = pos;
     return PO_OK;
 }
@@ -651,11 +658,13 @@ int po_decompress_v2(const uint8_t *in, uint64_t in_bytes, void *out, uint64_t c
     if (!po_params_ok(variant, d, 32, seg_len)) return PO_ERR_CORRUPT;
     if (n_seg != (n + seg_len - 1) / seg_len) return PO_ERR_CORRUPT;
     /* codes and bodies must lie inside the buffer */
-    if (n_seg > in_bytes - PO_HEADER_BYTES) return PO_ERR_CORRUPT;
-    uint64_t pos = PO_HEADER_BYTES + po_round8(n_seg);
+    if (n_seg > (in_bytes - PO_HEADER_BYTES) / 5) return PO_ERR_CORRUPT;
+    uint64_t sizes_at = PO_HEADER_BYTES + po_round8(n_seg);
+    uint64_t pos = sizes_at + po_round8(4 * n_seg);
     if (pos > in_bytes || body_bytes > in_bytes - pos) return PO_ERR_CORRUPT;
     uint64_t end = pos + body_bytes;
-    if (!po_zero(in + PO_HEADER_BYTES + n_seg, pos - PO_HEADER_BYTES - n_seg)) return PO_ERR_CORRUPT;
+    if (!po_zero(in + PO_HEADER_BYTES + n_seg, sizes_at - PO_HEADER_BYTES - n_seg)) return PO_ERR_CORRUPT;
+    if (!po_zero(in + sizes_at + 4 * n_seg, pos - sizes_at - 4 * n_seg)) return PO_ERR_CORRUPT;
     if (n > cap) return PO_ERR_CAPACITY;
     unsigned db = d / 8;
     uint64_t dmax = d == 16 ? 0xFFFFull : 0xFFFFFFFFull;
@@ -703,7 +712,9 @@ int po_decompress_v2(const uint8_t *in, uint64_t in_bytes, void *out, uint64_t c
         }
         free(u_buf);
         free(w_buf);
-        pos = words_at + po_round8(W * wb);
+        uint64_t next = words_at + po_round8(W * wb);
+        if (get_le(in + sizes_at + 4 * s, 4) * 8 != next - pos) return PO_ERR_CORRUPT;
+        pos = next;
     }
     if (pos != end) return PO_ERR_CORRUPT;
     *n_out = n;

@@ -452,7 +452,7 @@ def _v2_size_closed_form(x, variant, seg_len, codes):
     """Size of a format-2 stream from Eq. 1-2's word counts per block."""
     d = x.dtype.itemsize * 8
     n_seg = -(-x.size // seg_len)
-    total = 64 + -(-n_seg // 8) * 8
+    total = 64 + -(-n_seg // 8) * 8 + -(-4 * n_seg // 8) * 8
     for s in range(n_seg):
         seg = x[s * seg_len:(s + 1) * seg_len].astype(np.int64)
         L, w = 1 << (codes[s] & 0x1F), 64 if codes[s] & 0x80 else 32
@@ -497,7 +497,7 @@ def test_segmented_stream_rejects_bad_codes_and_bytes():
     x = np.arange(40, dtype=np.uint16) * 7
     s = bytearray(oracle.compress_v2(x, 1, 16, [0x84, 0x03, 0x8D]))
     assert np.array_equal(oracle.decompress_v2(bytes(s)), x)
-    for pos, val in [(64, 0x0E), (64, 0x24), (67, 1), (8, 1), (4, 1), (len(s) - 1, 0xFF)]:
+    for pos, val in [(64, 0x0E), (64, 0x24), (67, 1), (8, 1), (4, 1), (72, 9), (79, 1), (len(s) - 1, 0xFF)]:
         bad = bytearray(s)
         bad[pos] = val if bad[pos] != val else val ^ 1
         with pytest.raises(oracle.OracleError):
