@@ -772,8 +772,29 @@ def learned_vs_plain(dev, train_samples=2 << 30, test_bytes=1 << 30):
 
     pred, t_learned = timed(learned_path)
     learned_bytes = seg.total_bytes()
+    # the learned options' segments as ONE version-2 stream (a code byte and a
+    # size per segment instead of a 64-byte header), decoded back on the GPU
+    v2buf, v2nb = seg.assemble_v2(0)
+    v2ws = seg._v2_ws
+
+    def learned_path_v2():
+        p = learned_path()
+        seg.assemble_v2(0, out=v2buf, out_bytes=v2nb, workspace=v2ws)
+        return p
+
+    _, t_learned_v2 = timed(learned_path_v2)
+    assert seg.v2_status() == native.PC_OK
+    learned_v2_bytes = int(v2nb.item())
+    yv2, nv2, wsd = ch.decompress_v2(v2buf, learned_v2_bytes, native.ADVANCED, 16, te.numel())
+    _, t_dec_v2 = timed(lambda: ch.decompress_v2(v2buf, learned_v2_bytes, native.ADVANCED, 16, te.numel(), out=yv2,
+                                                 workspace=wsd))
+    v2_exact = (native.last_device_status(wsd.data_ptr(), torch.cuda.current_stream().cuda_stream) == native.PC_OK
+                and int(nv2.item()) == te.numel() and bool(torch.equal(yv2[:te.numel()], te)))
+    del yv2, wsd
     _, t_plain = timed(plain_path)
     plain_bytes = seg.total_bytes()
+    seg.assemble_v2(0, out=v2buf, out_bytes=v2nb, workspace=v2ws)
+    plain_v2_bytes = int(v2nb.item())
     # the learned path's parts, each timed alone
     feats, t_feat = timed(seg.features)
     _, t_mlp = timed(lambda: c.predict(feats))
@@ -801,6 +822,9 @@ def learned_vs_plain(dev, train_samples=2 << 30, test_bytes=1 << 30):
     return ({"train_segments": n_train, "test_segments": int(nseg), "test_bytes": raw,
              "segment_samples": ch.SEG, "variant": "advanced",
              "ratio_plain": raw / plain_bytes, "ratio_learned": raw / learned_bytes,
+             "ratio_learned_v2": raw / learned_v2_bytes, "ratio_plain_v2": raw / plain_v2_bytes,
+             "gbs_learned_v2": raw / (t_learned_v2 / 1e3) / GB,
+             "v2_decompress_gbs": raw / (t_dec_v2 / 1e3) / GB, "v2_round_trip_exact": v2_exact,
              "ratio_exhaustive": raw / best, "learned_vs_exhaustive_loss": learned_bytes / best - 1.0,
              "ratio_plain_whole_stream": raw / whole[ch.PLAIN_OPTION],
              "ratio_best_fixed_whole_stream": raw / whole[o_best], "best_fixed_option": o_best,
@@ -815,7 +839,9 @@ def learned_vs_plain(dev, train_samples=2 << 30, test_bytes=1 << 30):
                                                       if t <= opt_ms[ch.PLAIN_OPTION]],
                                   "ratio": raw / fast_bytes, "gbs": raw / (t_fast / 1e3) / GB},
              "train_loss_first_last": [hist[0], hist[-1]],
-             "note": "per-segment v1 streams, all on the device (features, MLP, per-segment compression); "
+             "note": "per-segment v1 streams (ratio_learned, ratio_plain) and the same segments as one "
+                     "version-2 stream (_v2), all on the device (features, MLP, per-segment compression, "
+                     "assembly); "
                      "data: camera events + white noise of varied sigma, train seed 11, test seed 12"},
             c)
 

@@ -426,6 +426,59 @@ pc_status pc_slice(const void *d_in, uint64_t in_bytes, const pc_params *params,
  * flatter profile after).  PC_ERR_INVALID_ARG for NULL pointers. */
 pc_status pc_byte_histogram(const void *d_bytes, uint64_t n_bytes, uint64_t *d_hist, pc_stream_t stream);
 
+/* ---- format version 2: block length and word size per segment ---------
+ * The paper picks the block length by hand from ratio curves (Sec. 3.3;
+ * Sec. 4.2, Fig. 7; Sec. 4.3.2, Fig. 10).  A version-2 stream records that
+ * choice per segment of the data in one stream: samples are cut into
+ * segments of seg_len samples (the last may be shorter), and each segment is
+ * compressed blockwise with its own (L, w), L a power of two <= 8192.
+ * Layout, little-endian:
+ *   header, 64 bytes: "PCMP", u16 version = 2, u8 variant, u8 dtype_bits,
+ *     4 zero bytes, u32 seg_len, u64 n_samples, u64 n_segments,
+ *     u64 body_bytes, 24 zero bytes;
+ *   codes: one byte per segment, log2(L) | (w == 64) << 7, zero-padded to a
+ *     multiple of 8 bytes;
+ *   sizes: per segment, u32 body size in units of 8 bytes, zero-padded to a
+ *     multiple of 8 bytes (every segment is found by a prefix sum);
+ *   bodies: per segment, its block table (vmin, B - 1), zero-padded to 8
+ *     bytes, then its packed words, zero-padded to 8 bytes.
+ * A segment's body holds the same table entries and words as the version-1
+ * stream of that segment alone; 64 bytes of header per segment become 5.
+ *
+ * pc_bound_v2: worst-case stream size over every code (host only).
+ * pc_assemble_v2: one version-2 stream from the version-1 streams of
+ *   n_segments consecutive segments, segment j at d_slots + j * seg_stride
+ *   (16-byte aligned, seg_stride a multiple of 16: the slots that
+ *   pc_compress_segments writes for one source, seg_len =
+ *   PC_SEGMENT_SAMPLES).  Each slot's header must name this variant and
+ *   dtype, a power-of-two block length <= 8192 and the segment's sample
+ *   count, and fit its slot; otherwise PC_ERR_INVALID_ARG is recorded in the
+ *   workspace status and the segment gets an empty body.  A body that would
+ *   pass out_capacity records PC_ERR_CAPACITY (out_capacity >=
+ *   pc_bound_v2 always suffices).  *d_out_bytes gets the stream size.
+ *   Workspace: pc_assemble_v2_workspace_size bytes, 16-byte aligned.
+ * pc_decompress_v2: the samples of a version-2 stream of this variant, dtype
+ *   and seg_len (all checked against its header) into d_out (capacity in
+ *   samples); *d_n_samples gets the count.  Corrupt streams (header, codes,
+ *   paddings, stored sizes that disagree with the tables, invalid words) are
+ *   recorded as PC_ERR_CORRUPT in the workspace status, read by
+ *   pc_last_device_status.  PC_ERR_UNSUPPORTED for advanced 32-bit data
+ *   (bases above 65536 need the serial series walk; the CPU reference decodes
+ *   them).  Workspace: pc_decompress_v2_workspace_size bytes for the
+ *   capacity, 16-byte aligned.
+ * Bounded waits and host-side error returns as for pc_compress. */
+pc_status pc_bound_v2(uint32_t variant, uint32_t dtype_bits, uint32_t seg_len, uint64_t n_samples,
+                      uint64_t *max_bytes);
+pc_status pc_assemble_v2_workspace_size(uint64_t n_segments, uint64_t *bytes);
+pc_status pc_assemble_v2(const void *d_slots, uint64_t seg_stride, uint64_t n_segments, uint64_t n_samples,
+                         uint32_t seg_len, uint32_t dtype_bits, uint32_t variant, void *d_out, uint64_t out_capacity,
+                         uint64_t *d_out_bytes, void *d_workspace, uint64_t workspace_bytes, pc_stream_t stream);
+pc_status pc_decompress_v2_workspace_size(uint32_t variant, uint32_t dtype_bits, uint32_t seg_len,
+                                          uint64_t capacity_samples, uint64_t *bytes);
+pc_status pc_decompress_v2(const void *d_in, uint64_t in_bytes, uint32_t variant, uint32_t dtype_bits,
+                           uint32_t seg_len, void *d_out, uint64_t out_capacity_samples, uint64_t *d_n_samples,
+                           void *d_workspace, uint64_t workspace_bytes, pc_stream_t stream);
+
 /* Compression without any device allocation, for callers that cannot
  * allocate device memory once they run: a data-acquisition loop that must not
  * call cudaMalloc mid-readout (it can fail under memory pressure or

@@ -14,7 +14,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libpc.so")
-SOURCES = ["pc_api.cu", "pc_compress.cu", "pc_decompress.cu", "pc_noalloc.cu", "pc_batch.cu", "pc_learn.cu", "pc_shard.cu", "pc_stats.cu"]
+SOURCES = ["pc_api.cu", "pc_compress.cu", "pc_decompress.cu", "pc_noalloc.cu", "pc_batch.cu", "pc_learn.cu", "pc_shard.cu", "pc_stats.cu", "pc_segmented.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -4,8 +4,10 @@ include/pc.h): marshalling of the library's feature, MLP and batch kernels.
 Per segment of 4096 samples an MLP picks one of 12 options (block length
 128..4096 x word size 32/64).  The options only change the parameters of each
 segment's stream; every segment is an ordinary version-1 stream, compressed
-in one batch launch, so the format and losslessness are untouched.  The plain
-heuristic (one fixed option for every segment) is the fallback.
+in one batch launch, so losslessness is untouched; assemble_v2 then joins a
+source's segments into one version-2 stream, which records each segment's
+(L, w) in a code byte instead of a 64-byte header.  The plain heuristic (one
+fixed option for every segment) is the fallback.
 """
 import numpy as np
 import torch
@@ -128,6 +130,58 @@ class Segments:
 
     def total_bytes(self):
         return int(sum(int(nb.sum().item()) for nb in self.nbytes))
+
+    def assemble_v2(self, i, out=None, out_bytes=None, workspace=None):
+        """Source i's segment streams as one version-2 stream (per-segment
+        (L, w) codes instead of a 64-byte header per segment; pc_assemble_v2).
+        Returns (uint8 device buffer, int64 device tensor [1] of its size);
+        no host synchronisation."""
+        n = self.sources[i].numel()
+        cap = native.bound_v2(self.variant, self.dtype_bits, SEG, n)
+        if out is None:
+            out = torch.empty((cap + 15) // 16 * 16, dtype=torch.uint8, device=self.device)
+        if out_bytes is None:
+            out_bytes = torch.zeros(1, dtype=torch.int64, device=self.device)
+        wsb = native.assemble_v2_workspace_size(self.counts[i])
+        if workspace is None or workspace.numel() < wsb:
+            workspace = torch.empty((wsb + 15) // 16 * 16, dtype=torch.uint8, device=self.device)
+        st = native.assemble_v2_raw(self.outs[i].data_ptr() if n else None, self.stride, self.counts[i], n, SEG,
+                                    self.dtype_bits, self.variant, out.data_ptr(), out.numel(), out_bytes.data_ptr(),
+                                    workspace.data_ptr(), workspace.numel(), self._handle())
+        if st != native.PC_OK:
+            raise native.PcError(st, "pc_assemble_v2")
+        self._v2_ws = workspace
+        return out, out_bytes
+
+    def v2_status(self):
+        """Device status of the last assemble_v2 (synchronises)."""
+        return native.last_device_status(self._v2_ws.data_ptr(), self._handle())
+
+
+def v2_code(o):
+    """Format-2 code byte of chooser option o: log2(L) | (w == 64) << 7."""
+    return (7 + o // 2) | (0x80 if o % 2 else 0)
+
+
+def decompress_v2(buf, in_bytes, variant, dtype_bits, capacity, seg_len=SEG, out=None, workspace=None,
+                  stream=None):
+    """Samples of a version-2 stream (pc_decompress_v2).  Returns (samples,
+    int64 device count, workspace); check native.last_device_status on the
+    workspace for corrupt streams."""
+    dev = buf.device
+    dt = torch.int16 if dtype_bits == 16 else torch.int32
+    if out is None:
+        out = torch.empty(max(capacity, 8), dtype=dt, device=dev)
+    n_out = torch.zeros(1, dtype=torch.int64, device=dev)
+    wsb = native.decompress_v2_workspace_size(variant, dtype_bits, seg_len, capacity)
+    if workspace is None or workspace.numel() < wsb:
+        workspace = torch.empty((wsb + 15) // 16 * 16, dtype=torch.uint8, device=dev)
+    s = (stream or torch.cuda.current_stream(dev)).cuda_stream
+    st = native.decompress_v2_raw(buf.data_ptr(), in_bytes, variant, dtype_bits, seg_len, out.data_ptr(), capacity,
+                                  n_out.data_ptr(), workspace.data_ptr(), workspace.numel(), s)
+    if st != native.PC_OK:
+        raise native.PcError(st, "pc_decompress_v2")
+    return out, n_out, workspace
 
 
 def compress_segments(x, options, variant=native.ADVANCED):

@@ -430,6 +430,59 @@ PCX_HD uint64_t table_bytes(uint64_t n_blocks, uint32_t d)
     return round_up(n_blocks * 2u * (d / 8u), 16);
 }
 
+// ---- format version 2: segmented streams --------------------------------
+// The block length and word size change along the data: segments of seg_len
+// samples, each compressed blockwise with its own (L, w).  After the 64-byte
+// header (version 2; u32 seg_len at byte 12, then u64 n_samples, n_segments,
+// body_bytes) come one code byte per segment (log2 L | (w == 64) << 7), then
+// one u32 body size per segment in units of 8 bytes, each array zero-padded
+// to a multiple of 8 bytes, then the bodies: the segment's block table
+// (vmin, B - 1) zero-padded to 8 bytes, then its packed words zero-padded to
+// 8 bytes.  The stored sizes let every segment be found by a prefix sum.
+constexpr uint32_t kV2MaxLog2L = 13;     // L <= 8192
+constexpr uint32_t kV2TileSegs = 256;    // segments per look-back tile of the v2 kernels
+constexpr uint64_t kOrbitTagV2 = 0x4F52424954330000ull;  // two tables (w = 32, 64): v2 decoding
+
+PCX_HD uint64_t round8(uint64_t x) { return (x + 7) / 8 * 8; }
+PCX_HD bool v2_code_ok(uint32_t c) { return (c & 0x60u) == 0 && (c & 0x1Fu) <= kV2MaxLog2L; }
+PCX_HD uint32_t v2_L(uint32_t c) { return 1u << (c & 0x1Fu); }
+PCX_HD uint32_t v2_w(uint32_t c) { return (c & 0x80u) ? 64u : 32u; }
+
+struct V2Geom {
+    uint64_t sizes_at, bodies_at;
+};
+PCX_HD V2Geom v2_geom(uint64_t n_seg)
+{
+    V2Geom g;
+    g.sizes_at = PC_HEADER_BYTES + round8(n_seg);
+    g.bodies_at = g.sizes_at + round8(4 * n_seg);
+    return g;
+}
+
+// Workspace of the v2 kernels: the header, (advanced decoding) two series
+// tables laid out as a batch's, look-back words per tile of kV2TileSegs
+// segments, and (decoding) one body offset per segment.
+struct V2Layout {
+    uint64_t off_flags32, off_flags64, off_hdr32, off_slots32, off_hdr64, off_slots64;
+    uint64_t off_status, n_status, off_offsets, n_offsets, bytes;
+};
+PCX_HD V2Layout v2_layout(bool tables, bool offsets, uint64_t max_segments)
+{
+    V2Layout l;
+    l.off_flags32 = sizeof(WsHeader);
+    l.off_flags64 = l.off_flags32 + (tables ? kOrbitFlagsBytes : 0);
+    l.off_hdr32 = l.off_flags64 + (tables ? kOrbitFlagsBytes : 0);
+    l.off_slots32 = l.off_hdr32 + (tables ? kOrbitHdrBytes : 0);
+    l.off_hdr64 = l.off_slots32 + (tables ? kOrbitSlotBytes : 0);
+    l.off_slots64 = l.off_hdr64 + (tables ? kOrbitHdrBytes : 0);
+    l.off_status = l.off_slots64 + (tables ? kOrbitSlotBytes : 0);
+    l.n_status = (max_segments + kV2TileSegs - 1) / kV2TileSegs + 1;
+    l.off_offsets = l.off_status + 8 * l.n_status;
+    l.n_offsets = offsets ? max_segments + 1 : 0;
+    l.bytes = round_up(l.off_offsets + 8 * l.n_offsets, 16);
+    return l;
+}
+
 // Segments path (learned chooser): the device copy of a pc_source plus the
 // index of its first segment among all sources' segments.  An empty source
 // owns no segment.

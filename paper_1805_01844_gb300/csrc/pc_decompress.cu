@@ -1061,23 +1061,14 @@ __device__ __forceinline__ bool adv_decode_words(const OrbitTable &ot, const Dec
     return bad;
 }
 
+// A block's record from its table entry (vmin, B - 1), range-checked by the
+// caller.
 template <uint32_t WB, uint32_t VAR, bool ORB>
-__device__ __forceinline__ DecBlock dec_setup(const uint8_t *in, uint64_t gb, uint32_t n_b, uint32_t L,
-                                              const OrbitTable &ot,
-                                              WsHeader *ws, uint64_t limit_ns, uint32_t D)
+__device__ __forceinline__ DecBlock dec_setup_entry(uint64_t vmin, uint64_t Bm1, uint32_t n_b, uint32_t L,
+                                                    const OrbitTable &ot, WsHeader *ws, uint64_t limit_ns)
 {
     DecBlock d{};
-    uint64_t vmin, Bm1;
-    if (D == 16) {
-        const uint32_t e = reinterpret_cast<const uint32_t *>(in + PC_HEADER_BYTES)[gb];
-        vmin = e & 0xFFFFu;
-        Bm1 = e >> 16;
-    } else {
-        const uint64_t e = reinterpret_cast<const uint64_t *>(in + PC_HEADER_BYTES)[gb];
-        vmin = e & 0xFFFFFFFFull;
-        Bm1 = e >> 32;
-    }
-    d.B = Bm1 + 1;  // entries were range-checked by the offsets kernel
+    d.B = Bm1 + 1;
     d.vmin = (uint32_t)vmin;
     d.n_b = n_b;
     if (d.B <= 1) return d;
@@ -1109,6 +1100,25 @@ __device__ __forceinline__ DecBlock dec_setup(const uint8_t *in, uint64_t gb, ui
         }
     }
     return d;
+}
+
+template <uint32_t WB, uint32_t VAR, bool ORB>
+__device__ __forceinline__ DecBlock dec_setup(const uint8_t *in, uint64_t gb, uint32_t n_b, uint32_t L,
+                                              const OrbitTable &ot,
+                                              WsHeader *ws, uint64_t limit_ns, uint32_t D)
+{
+    uint64_t vmin, Bm1;
+    if (D == 16) {
+        const uint32_t e = reinterpret_cast<const uint32_t *>(in + PC_HEADER_BYTES)[gb];
+        vmin = e & 0xFFFFu;
+        Bm1 = e >> 16;
+    } else {
+        const uint64_t e = reinterpret_cast<const uint64_t *>(in + PC_HEADER_BYTES)[gb];
+        vmin = e & 0xFFFFFFFFull;
+        Bm1 = e >> 32;
+    }
+    // entries were range-checked by the offsets kernel
+    return dec_setup_entry<WB, VAR, ORB>(vmin, Bm1, n_b, L, ot, ws, limit_ns);
 }
 
 // Warp-granular decoding (basic, and advanced with the series table on 16-bit
@@ -1374,6 +1384,361 @@ cudaError_t launch_decompress(const LaunchArgs &a)
     case 6: return launch_decompress_t<uint32_t, 64, 0, false>(a);
     default: return a.orbit ? launch_decompress_t<uint32_t, 64, 1, true>(a) : launch_decompress_t<uint32_t, 64, 1, false>(a);
     }
+}
+
+// ---- format version 2 (segmented streams) --------------------------------
+
+// Body offsets of a version-2 stream: every CTA checks the header; one thread
+// per segment reads its code and stored body size; a block-wide scan and the
+// bounded look-back over tiles of kV2TileSegs segments give every body's
+// offset.  The last tile checks that the sizes add up to the header's
+// body_bytes and that the two arrays' paddings are zero.
+template <uint32_t NT>
+__global__ void __launch_bounds__(NT)
+k_v2_offsets(const uint8_t *__restrict__ in, uint64_t in_bytes, uint32_t variant, uint32_t d, uint32_t seg_len,
+             uint64_t cap, uint64_t max_segments, uint64_t *__restrict__ n_out, WsHeader *ws, uint64_t *status,
+             uint64_t *offsets, uint64_t limit_ns)
+{
+    constexpr uint32_t NW = NT / 32;
+    __shared__ uint64_t hdr[3];
+    __shared__ uint64_t warp_tot[NW];
+    __shared__ uint64_t s_excl;
+    __shared__ uint32_t s_code, s_tile, s_ok;
+    const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+    if (threadIdx.x == 0) {  // the host checked in_bytes >= PC_HEADER_BYTES
+        const uint32_t *h = reinterpret_cast<const uint32_t *>(in);
+        const uint64_t *h64 = reinterpret_cast<const uint64_t *>(in);
+        const uint64_t n = h64[2], n_seg = h64[3], body = h64[4];
+        uint32_t code = PC_OK;
+        if (h[0] != 0x504D4350u || h[1] != (2u | (variant << 16) | (d << 24)) || h[2] != 0 || h[3] != seg_len ||
+            h64[5] != 0 || h64[6] != 0 || h64[7] != 0 || n_seg != ceil_div(n, seg_len))
+            code = PC_ERR_CORRUPT;
+        else if (n > cap || n_seg > max_segments)
+            code = PC_ERR_CAPACITY;
+        else {
+            const V2Geom g = v2_geom(n_seg);
+            if (g.bodies_at > in_bytes || body > in_bytes - g.bodies_at) code = PC_ERR_CORRUPT;
+        }
+        hdr[0] = n;
+        hdr[1] = n_seg;
+        hdr[2] = body;
+        s_code = code;
+    }
+    __syncthreads();
+    if (s_code != PC_OK) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) record_error(ws, s_code);
+        return;
+    }
+    const uint64_t n = hdr[0], n_seg = hdr[1], body_bytes = hdr[2];
+    const V2Geom g = v2_geom(n_seg);
+    const uint32_t *sizes = reinterpret_cast<const uint32_t *>(in + g.sizes_at);
+    const uint64_t n_tiles = ceil_div(n_seg, kV2TileSegs);
+    if (n_tiles == 0) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            if (body_bytes != 0) record_error(ws, PC_ERR_CORRUPT);
+            offsets[0] = 0;
+            *n_out = 0;
+        }
+        return;
+    }
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = atomicAdd(&ws->ticket, 1u);
+        __syncthreads();
+        const uint64_t tile = s_tile;
+        if (tile >= n_tiles) break;
+        uint64_t v = 0;  // this thread's segments' sizes (kV2TileSegs / NT of them), bytes
+        uint64_t mine[kV2TileSegs / NT];
+#pragma unroll
+        for (uint32_t i = 0; i < kV2TileSegs / NT; ++i) {
+            const uint64_t sg = tile * kV2TileSegs + threadIdx.x * (kV2TileSegs / NT) + i;
+            mine[i] = 0;
+            if (sg < n_seg) {
+                if (!v2_code_ok(in[PC_HEADER_BYTES + sg])) record_error(ws, PC_ERR_CORRUPT);
+                mine[i] = 8ull * sizes[sg];
+            }
+            v += mine[i];
+        }
+        // block-wide exclusive scan of v (64-bit: up to 2^35 bytes per thread)
+        uint64_t incl = v;
+#pragma unroll
+        for (uint32_t o = 1; o < 32; o <<= 1) {
+            const uint64_t t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (lane == 31) warp_tot[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            const uint64_t t = lane < NW ? warp_tot[lane] : 0ull;
+            uint64_t ti = t;
+#pragma unroll
+            for (uint32_t o = 1; o < 32; o <<= 1) {
+                const uint64_t u = __shfl_up_sync(0xFFFFFFFFu, ti, o);
+                if (lane >= o) ti += u;
+            }
+            if (lane < NW) warp_tot[lane] = ti - t;
+            const uint64_t agg = __shfl_sync(0xFFFFFFFFu, ti, 31);
+            uint64_t excl = 0;
+            const bool ok = lookback_warp(status, tile, agg, ws, limit_ns, &excl);
+            if (lane == 0) {
+                s_excl = excl;
+                s_ok = ok ? 1u : 0u;
+            }
+        }
+        __syncthreads();
+        if (s_ok) {
+            uint64_t off = s_excl + warp_tot[warp] + (incl - v);
+#pragma unroll
+            for (uint32_t i = 0; i < kV2TileSegs / NT; ++i) {
+                const uint64_t sg = tile * kV2TileSegs + threadIdx.x * (kV2TileSegs / NT) + i;
+                if (sg < n_seg) {
+                    offsets[sg] = off;
+                    if (sg == n_seg - 1) {
+                        offsets[n_seg] = off + mine[i];
+                        if (off + mine[i] != body_bytes) record_error(ws, PC_ERR_CORRUPT);
+                        for (uint64_t o = PC_HEADER_BYTES + n_seg; o < g.sizes_at; ++o)
+                            if (in[o] != 0) record_error(ws, PC_ERR_CORRUPT);
+                        for (uint64_t o = g.sizes_at + 4 * n_seg; o < g.bodies_at; ++o)
+                            if (in[o] != 0) record_error(ws, PC_ERR_CORRUPT);
+                        *n_out = n;
+                    }
+                }
+                off += mine[i];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// One segment of a version-2 stream by one warp: its blocks' word counts
+// (lane per block, 32 at a time) must give the stored body size; then the
+// blocks are set up 32 at a time (records in the warp's shared memory) and
+// decoded one by one as k_decode_w decodes a chunked block: words staged
+// kDecChunk at a time, digits into the warp's sample slot, samples out.
+// Returns true if the segment is corrupt.
+template <typename T, uint32_t WB, uint32_t VAR>
+__device__ bool v2_segment(const uint8_t *body, uint64_t size, uint32_t n_s, uint32_t L, uint32_t slot_elems,
+                           T *__restrict__ out, uint8_t *wsm, const OrbitTable &ot, WsHeader *ws, uint64_t limit_ns)
+{
+    using Word = typename WordT<T, WB>::type;
+    constexpr uint32_t D = sizeof(T) * 8, DB = D / 8;
+    constexpr uint64_t kDmax = D == 16 ? 0xFFFFull : 0xFFFFFFFFull;
+    constexpr uint32_t kRec = VAR == PC_VARIANT_BASIC ? kDecRecBasic : kDecRecAdvanced;
+    const uint32_t lane = threadIdx.x & 31u;
+    T *u = reinterpret_cast<T *>(wsm);
+    T *junk = u + slot_elems - kPad;
+    const uint32_t slot_bytes = (uint32_t)round_up((uint64_t)slot_elems * sizeof(T), 16);
+    Word *wbuf = reinterpret_cast<Word *>(wsm + slot_bytes);
+    uint8_t *recs = wsm + slot_bytes + kDecChunk * sizeof(Word);
+    auto rec = [&](uint32_t b) -> const DecBlock & { return *reinterpret_cast<const DecBlock *>(recs + b * kRec); };
+
+    const uint32_t nb = (n_s + L - 1) / L;
+    const uint64_t tb = (uint64_t)nb * 2 * DB, words_at = round8(tb);
+    if (words_at > size) return true;
+    auto entry = [&](uint32_t b, uint64_t &vmin, uint64_t &Bm1) {
+        if constexpr (D == 16) {
+            const uint32_t e = reinterpret_cast<const uint32_t *>(body)[b];
+            vmin = e & 0xFFFFu;
+            Bm1 = e >> 16;
+        } else {
+            const uint64_t e = reinterpret_cast<const uint64_t *>(body)[b];
+            vmin = e & 0xFFFFFFFFull;
+            Bm1 = e >> 32;
+        }
+    };
+    // 1. word counts: the stored size must be the table's
+    bool bad = false;
+    uint64_t total = 0;
+    for (uint32_t b0 = 0; b0 < nb; b0 += 32) {
+        const uint32_t b = b0 + lane;
+        uint32_t W = 0;
+        if (b < nb) {
+            uint64_t vmin, Bm1;
+            entry(b, vmin, Bm1);
+            if (vmin + Bm1 > kDmax) {
+                bad = true;
+                Bm1 = 0;
+            }
+            W = block_words<WB, VAR, true>(Bm1 + 1, min(L, n_s - b * L), L, ot, ws, limit_ns);
+        }
+        total += warp_sum_u64(W);
+    }
+    if (__any_sync(0xFFFFFFFFu, bad) || words_at + round8(total * (WB / 8)) != size) return true;
+    for (uint64_t o = tb + lane; o < words_at; o += 32) bad |= body[o] != 0;
+    for (uint64_t o = words_at + total * (WB / 8) + lane; o < size; o += 32) bad |= body[o] != 0;
+    const Word *words = reinterpret_cast<const Word *>(body + words_at);
+
+    // 2. blocks, 32 records at a time
+    uint64_t run = 0;  // words of the earlier rounds
+    for (uint32_t b0 = 0; b0 < nb; b0 += 32) {
+        const uint32_t m = min(32u, nb - b0);
+        DecBlock mine{};
+        if (lane < m) {
+            uint64_t vmin, Bm1;
+            entry(b0 + lane, vmin, Bm1);
+            mine = dec_setup_entry<WB, VAR, true>(vmin, Bm1, min(L, n_s - (b0 + lane) * L), L, ot, ws, limit_ns);
+        }
+        const uint32_t incl = warp_incl_scan_u32(mine.W);
+        mine.woff = incl - mine.W;
+        __syncwarp();  // the previous round's records are read
+        if (lane < m) store_rec<VAR>(recs, mine, lane);
+        __syncwarp();
+        for (uint32_t b = 0; b < m; ++b) {
+            const DecBlock &k = rec(b);
+            const uint32_t vmin = k.vmin, W = k.W, n_b = k.n_b;
+            if (W == 0) {
+                for (uint32_t i = lane; i < n_b; i += 32) u[i] = (T)vmin;
+            } else {
+                const uint32_t nch = (W + kDecChunk - 1) / kDecChunk;
+                uint32_t cR = 1, cr = 0, qlast = 0, plast = 0;  // advanced: carries across words
+                for (uint32_t c = 0; c < nch; ++c) {
+                    const uint32_t jb = c * kDecChunk, je = min(W, jb + kDecChunk);
+                    const Word *g = words + run + k.woff + jb;
+                    for (uint32_t j = lane; j < je - jb; j += 32) wbuf[j] = g[j];
+                    __syncwarp();
+                    if constexpr (VAR == PC_VARIANT_BASIC) {
+                        bad |= decode_basic_block<T, WB>(wbuf, u, junk, jb, je, k.p, k.hstar, k.B, vmin, k.mg, k.Dh,
+                                                         k.MD);
+                    } else {
+                        bad |= adv_decode_words<T, WB>(ot, k, wbuf, jb, je, W, u, junk, vmin, n_b, cR, cr, qlast,
+                                                       plast);
+                    }
+                    __syncwarp();  // the buffer is free for the next chunk
+                }
+                // digits past the block's end must be padding (offset 0)
+                uint32_t end;
+                if constexpr (VAR == PC_VARIANT_BASIC) {
+                    end = W * k.p;
+                } else {
+                    const uint32_t src_lane = (W - 1) & 31u;
+                    qlast = __shfl_sync(0xFFFFFFFFu, qlast, src_lane);
+                    plast = __shfl_sync(0xFFFFFFFFu, plast, src_lane);
+                    end = qlast + plast;
+                }
+                for (uint32_t i = n_b + lane; i < end; i += 32) bad |= (uint32_t)u[i] != vmin;
+            }
+            __syncwarp();
+            T *dst = out + (uint64_t)(b0 + b) * L;
+            for (uint32_t i = lane; i < n_b; i += 32) dst[i] = u[i];
+            __syncwarp();
+        }
+        run += __shfl_sync(0xFFFFFFFFu, incl, 31);
+    }
+    return __any_sync(0xFFFFFFFFu, bad);
+}
+
+// Shared memory of one warp of k_v2_decode: the sample slot of the longest
+// block (at most the segment), one chunk of words, 32 block records.
+PCX_HD uint32_t v2_slot_elems(uint32_t seg_len)
+{
+    return (seg_len < (1u << kV2MaxLog2L) ? seg_len : (1u << kV2MaxLog2L)) + 2 * kPad;
+}
+PCX_HD uint32_t v2_warp_bytes(uint32_t variant, uint32_t d, uint32_t seg_len)
+{
+    return (uint32_t)(round_up((uint64_t)v2_slot_elems(seg_len) * (d / 8), 16) + kDecChunk * 8ull +
+                      32ull * (variant == PC_VARIANT_BASIC ? kDecRecBasic : kDecRecAdvanced));
+}
+
+// Decoding of a version-2 stream: a warp per segment, round-robin; the
+// segment's code picks the word size.
+template <typename T, uint32_t VAR>
+__global__ void __launch_bounds__(kDecWarpsMax * 32)
+k_v2_decode(const uint8_t *__restrict__ in, uint32_t seg_len, T *__restrict__ out, WsHeader *ws,
+            const uint64_t *__restrict__ offsets, OrbitTable ot32, OrbitTable ot64, uint64_t limit_ns,
+            uint32_t warp_bytes)
+{
+    extern __shared__ __align__(16) uint8_t smem[];
+    const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+    if (*reinterpret_cast<volatile uint32_t *>(&ws->status) != PC_OK) return;
+    const uint64_t *h64 = reinterpret_cast<const uint64_t *>(in);
+    const uint64_t n = h64[2], n_seg = h64[3];
+    const V2Geom g = v2_geom(n_seg);
+    const uint32_t *sizes = reinterpret_cast<const uint32_t *>(in + g.sizes_at);
+    uint8_t *wsm = smem + warp * warp_bytes;
+    const uint32_t nwarps = blockDim.x >> 5;
+    const uint32_t slot_elems = v2_slot_elems(seg_len);
+    bool bad = false;
+    for (uint64_t sg = (uint64_t)blockIdx.x * nwarps + warp; sg < n_seg; sg += (uint64_t)gridDim.x * nwarps) {
+        const uint32_t code = in[PC_HEADER_BYTES + sg];
+        if (!v2_code_ok(code)) {  // recorded by the offsets kernel
+            bad = true;
+            continue;
+        }
+        const uint32_t L = v2_L(code);
+        const uint32_t n_s = (uint32_t)umin64(seg_len, n - sg * seg_len);
+        const uint8_t *body = in + g.bodies_at + offsets[sg];
+        const uint64_t size = 8ull * sizes[sg];
+        T *dst = out + sg * seg_len;
+        if (v2_w(code) == 64) bad |= v2_segment<T, 64, VAR>(body, size, n_s, L, slot_elems, dst, wsm, ot64, ws, limit_ns);
+        else bad |= v2_segment<T, 32, VAR>(body, size, n_s, L, slot_elems, dst, wsm, ot32, ws, limit_ns);
+    }
+    if (__any_sync(0xFFFFFFFFu, bad) && lane == 0) record_error(ws, PC_ERR_CORRUPT);
+}
+
+template <typename T, uint32_t VAR>
+static cudaError_t launch_v2_decode_t(const V2DecodeArgs &a)
+{
+    cudaError_t e;
+    int dev = 0, sms = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    uint8_t *base = static_cast<uint8_t *>(a.workspace);
+    WsHeader *ws = reinterpret_cast<WsHeader *>(base);
+    const V2Layout lay = v2_layout(VAR == PC_VARIANT_ADVANCED, true, a.max_segments);
+    uint64_t *status = reinterpret_cast<uint64_t *>(base + lay.off_status);
+    uint64_t *offsets = reinterpret_cast<uint64_t *>(base + lay.off_offsets);
+    const OrbitTable ot32{reinterpret_cast<uint32_t *>(base + lay.off_flags32),
+                          reinterpret_cast<uint64_t *>(base + lay.off_hdr32),
+                          reinterpret_cast<ulonglong2 *>(base + lay.off_slots32), &ws->orbit_cursor};
+    const OrbitTable ot64{reinterpret_cast<uint32_t *>(base + lay.off_flags64),
+                          reinterpret_cast<uint64_t *>(base + lay.off_hdr64),
+                          reinterpret_cast<ulonglong2 *>(base + lay.off_slots64), &ws->reserved_cursor64};
+    if ((e = cudaMemsetAsync(base, 0, VAR == PC_VARIANT_ADVANCED ? 12 : 32, a.stream)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(status, 0, 8 * lay.n_status, a.stream)) != cudaSuccess) return e;
+    if constexpr (VAR == PC_VARIANT_ADVANCED) {
+        if ((e = launch_orbit_prepare(ws, ot32.flags, 2 * kOrbitFlagsBytes, &ws->orbit_cursor,
+                                      &ws->reserved_cursor64, kOrbitTagV2, a.stream)) != cudaSuccess)
+            return e;
+    }
+    {
+        auto kern = k_v2_offsets<kThreads>;
+        int per_sm = 0;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, 0)) != cudaSuccess) return e;
+        if (per_sm < 1) return cudaErrorInvalidConfiguration;
+        uint64_t grid = (uint64_t)per_sm * sms;
+        if (lay.n_status < grid) grid = lay.n_status;
+        kern<<<(unsigned)grid, kThreads, 0, a.stream>>>(static_cast<const uint8_t *>(a.in), a.in_bytes, VAR,
+                                                        sizeof(T) * 8, a.seg_len, a.cap, a.max_segments, a.n_out, ws,
+                                                        status, offsets, a.limit_ns);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    {
+        auto kern = k_v2_decode<T, VAR>;
+        const uint32_t wb = v2_warp_bytes(VAR, sizeof(T) * 8, a.seg_len);
+        const uint32_t smem = kDecWarpsMax * wb;
+        if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+            return e;
+        int per_sm = 0;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kDecWarpsMax * 32, smem)) !=
+            cudaSuccess)
+            return e;
+        if (per_sm < 1) return cudaErrorInvalidConfiguration;
+        uint64_t grid = (uint64_t)per_sm * sms;
+        const uint64_t need = ceil_div(a.max_segments, kDecWarpsMax);
+        if (need < grid) grid = need;
+        if (grid < 1) grid = 1;
+        kern<<<(unsigned)grid, kDecWarpsMax * 32, smem, a.stream>>>(static_cast<const uint8_t *>(a.in), a.seg_len,
+                                                                    static_cast<T *>(a.out), ws, offsets, ot32, ot64,
+                                                                    a.limit_ns, wb);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_v2_decode(const V2DecodeArgs &a)
+{
+    if (a.d == 16) return a.variant ? launch_v2_decode_t<uint16_t, 1>(a) : launch_v2_decode_t<uint16_t, 0>(a);
+    if (a.variant == 0) return launch_v2_decode_t<uint32_t, 0>(a);
+    return cudaErrorNotSupported;  // 32-bit advanced: bases above the series table need the serial walk
 }
 
 // Self-test of the bounded wait: tile 1 looks back at tile 0, which nothing

@@ -41,4 +41,34 @@ cudaError_t launch_orbit_prepare(WsHeader *ws, uint32_t *flags, uint64_t flag_by
 cudaError_t launch_decompress(const LaunchArgs &a);
 cudaError_t launch_selftest_wait(WsHeader *ws, uint64_t *status, uint64_t limit_ns, cudaStream_t stream);
 
+// Decoding of a version-2 (segmented) stream: workspace laid out by
+// v2_layout(advanced, true, max_segments).
+struct V2DecodeArgs {
+    const void *in;
+    uint64_t in_bytes;
+    uint32_t variant, d, seg_len;
+    uint64_t cap;           // sample capacity of out
+    uint64_t max_segments;  // ceil(cap / seg_len): offsets in the workspace
+    void *out;
+    uint64_t *n_out;
+    void *workspace;
+    uint64_t limit_ns;
+    cudaStream_t stream;
+};
+cudaError_t launch_v2_decode(const V2DecodeArgs &a);
+
+// Assembly of a version-2 stream from per-segment version-1 streams.
+struct V2AssembleArgs {
+    const void *slots;
+    uint64_t seg_stride, n_segments, n;
+    uint32_t seg_len, d, variant;
+    void *out;
+    uint64_t out_capacity;
+    uint64_t *out_bytes;
+    void *workspace;
+    uint64_t limit_ns;
+    cudaStream_t stream;
+};
+cudaError_t launch_v2_assemble(const V2AssembleArgs &a);
+
 }  // namespace pcx

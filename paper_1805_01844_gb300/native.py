@@ -22,7 +22,9 @@ EXPORTS = ("pc_bound", "pc_workspace_size", "pc_compress", "pc_decompress",
            "pc_strerror", "pc_compress_noalloc", "pc_batch_describe", "pc_batch_plan",
            "pc_compress_batch", "pc_segment_features", "pc_mlp_forward", "pc_mlp_grad", "pc_mlp_adam",
            "pc_segments_describe", "pc_segments_plan", "pc_segments_features", "pc_compress_segments",
-           "pc_shard_range", "pc_stitch_layout", "pc_stitch", "pc_slice", "pc_byte_histogram")
+           "pc_shard_range", "pc_stitch_layout", "pc_stitch", "pc_slice", "pc_byte_histogram",
+           "pc_bound_v2", "pc_assemble_v2_workspace_size", "pc_assemble_v2", "pc_decompress_v2_workspace_size",
+           "pc_decompress_v2")
 SEGMENT_SAMPLES, CHOOSER_FEATURES, CHOOSER_OPTIONS = 4096, 24, 12
 MLP_PARAMS, MLP_WEIGHT_BYTES = 6540, 13360
 NOALLOC_SCRATCH_BYTES = 1 << 20
@@ -149,6 +151,16 @@ def load(path=LIB_PATH):
     L.pc_slice.restype = st
     L.pc_byte_histogram.argtypes = [vp, u64, vp, vp]
     L.pc_byte_histogram.restype = st
+    L.pc_bound_v2.argtypes = [u32, u32, u32, u64, u64p]
+    L.pc_bound_v2.restype = st
+    L.pc_assemble_v2_workspace_size.argtypes = [u64, u64p]
+    L.pc_assemble_v2_workspace_size.restype = st
+    L.pc_assemble_v2.argtypes = [vp, u64, u64, u64, u32, u32, u32, vp, u64, vp, vp, u64, vp]
+    L.pc_assemble_v2.restype = st
+    L.pc_decompress_v2_workspace_size.argtypes = [u32, u32, u32, u64, u64p]
+    L.pc_decompress_v2_workspace_size.restype = st
+    L.pc_decompress_v2.argtypes = [vp, u64, u32, u32, u32, vp, u64, vp, vp, u64, vp]
+    L.pc_decompress_v2.restype = st
     L.pc_strerror.argtypes = [st]
     L.pc_strerror.restype = ctypes.c_char_p
     _lib = L
@@ -303,3 +315,37 @@ def slice_raw(d_in, in_bytes, p, first_block, n_blocks, d_out, out_capacity, d_o
 def byte_histogram_raw(d_bytes, n_bytes, d_hist, stream):
     """pc_byte_histogram on raw device addresses; returns the host status."""
     return load().pc_byte_histogram(d_bytes or None, int(n_bytes), d_hist, stream or None)
+
+
+def bound_v2(variant, dtype_bits, seg_len, n):
+    out = ctypes.c_uint64(0)
+    _check(load().pc_bound_v2(variant, dtype_bits, seg_len, int(n), ctypes.byref(out)), "pc_bound_v2")
+    return int(out.value)
+
+
+def assemble_v2_workspace_size(n_segments):
+    out = ctypes.c_uint64(0)
+    _check(load().pc_assemble_v2_workspace_size(int(n_segments), ctypes.byref(out)),
+           "pc_assemble_v2_workspace_size")
+    return int(out.value)
+
+
+def decompress_v2_workspace_size(variant, dtype_bits, seg_len, capacity):
+    out = ctypes.c_uint64(0)
+    _check(load().pc_decompress_v2_workspace_size(variant, dtype_bits, seg_len, int(capacity), ctypes.byref(out)),
+           "pc_decompress_v2_workspace_size")
+    return int(out.value)
+
+
+def assemble_v2_raw(d_slots, seg_stride, n_segments, n, seg_len, dtype_bits, variant, d_out, out_capacity,
+                    d_out_bytes, d_ws, ws_bytes, stream):
+    """pc_assemble_v2 on raw device addresses; returns the host status."""
+    return load().pc_assemble_v2(d_slots or None, int(seg_stride), int(n_segments), int(n), seg_len, dtype_bits,
+                                 variant, d_out, int(out_capacity), d_out_bytes, d_ws, int(ws_bytes),
+                                 stream or None)
+
+
+def decompress_v2_raw(d_in, in_bytes, variant, dtype_bits, seg_len, d_out, cap, d_n, d_ws, ws_bytes, stream):
+    """pc_decompress_v2 on raw device addresses; returns the host status."""
+    return load().pc_decompress_v2(d_in, int(in_bytes), variant, dtype_bits, seg_len, d_out or None, int(cap), d_n,
+                                   d_ws, int(ws_bytes), stream or None)
