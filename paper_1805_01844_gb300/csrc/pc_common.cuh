@@ -278,13 +278,16 @@ PCX_HD TileCfg tile_cfg(uint32_t kind, uint32_t variant, uint32_t d, uint32_t w,
 }
 
 // Threads per CTA of the single-stream compression kernel: 128-thread CTAs
-// (half-size tiles, more CTAs per SM) for short basic blocks, where the per-
-// tile work is small; 256 otherwise (measured on the camera workload).
+// (half-size tiles, more CTAs per SM) for basic blocks of <= 128 samples,
+// where the per-tile work is small; 256 otherwise, which also gives long
+// streams the look-back tiles of several stage tiles (measured on camera
+// events, w = 64: L = 512 +25 %, L = 256 +3 % over 128 threads; L = 128 -9 %
+// on white noise).
 PCX_HD uint32_t compress_threads(uint32_t variant, uint32_t d, uint32_t w, uint32_t L)
 {
     (void)d;
     (void)w;
-    return variant == PC_VARIANT_BASIC && L <= 512 ? 128u : 256u;
+    return variant == PC_VARIANT_BASIC && L <= 128 ? 128u : 256u;
 }
 
 // Blocks per tile of the decompression offsets kernel (one thread per block).

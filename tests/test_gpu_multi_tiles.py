@@ -29,14 +29,15 @@ def stage_tiles_per_lookback(tb):
 
 
 @pytest.mark.parametrize("d,L,w,extra_blocks", [(16, 1024, 64, 70), (16, 1024, 64, 5), (16, 1024, 32, 40),
-                                                 (16, 4096, 64, 9), (32, 1024, 64, 50)])
+                                                 (16, 4096, 64, 9), (32, 1024, 64, 50), (16, 512, 64, 7),
+                                                 (16, 256, 32, 50), (16, 256, 64, 33)])
 def test_multi_stage_tiles_match_oracle(d, L, w, extra_blocks):
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     dev = torch.device("cuda:0")
     tb = stage_blocks(L, d)
     n_blocks = stage_tiles_per_lookback(tb) * tb * SMALL_TILES + extra_blocks
-    n = (n_blocks - 1) * L + 777  # ragged last block
+    n = (n_blocks - 1) * L + min(777, L - 5)  # ragged last block
     dt = np.uint16 if d == 16 else np.uint32
     x = datagen.white_noise(n, 300.0 if d == 16 else 70000.0, 5.0, seed=L + w + extra_blocks, dtype=dt)
     # a few wide blocks so that several bases occur
