@@ -890,6 +890,10 @@ __device__ __forceinline__ void store_rec(uint8_t *recs, const DecBlock &d, uint
     for (uint32_t i = 0; i < NV; ++i) dst[i] = v[i];
 }
 
+#ifndef PCX_ADV_SPLIT_R32
+#define PCX_ADV_SPLIT_R32 1
+#endif
+
 // Advanced words [jb, je) of one block by one warp (src holds them from word
 // jb on), two words per lane in lockstep (words j0 + lane and j0 + 32 +
 // lane) while more than 32 are left, then one: each word divided by its R_i, R_{i-1} and r_{i-1} taken from the
@@ -956,10 +960,21 @@ __device__ __forceinline__ bool adv_decode_words(const OrbitTable &ot, const Dec
         T *l1 = v1 ? u + e1.q + e1.p - 1 : junk + p1 - 1;
         if constexpr (WB == 64) {
             for (uint32_t t = 0; t < ns; ++t) {
-                uint64_t lo0, lo1;
-                b0 = divmod_inv64(b0, k.Dh, k.MD, lo0);
-                b1 = divmod_inv64(b1, k.Dh, k.MD, lo1);
-                rev_exact2<T>(l0, (uint32_t)lo0, l1, (uint32_t)lo1, hstar, B32, k.mg, vmin);
+                uint32_t lo0, lo1;
+#if PCX_ADV_SPLIT_R32
+                if (k.Dh <= 0x80000000ull) {  // remainders formed in 32 bits (as the basic decoder's splits)
+                    b0 = divmod_inv64_r32(b0, (uint32_t)k.Dh, k.MD, lo0);
+                    b1 = divmod_inv64_r32(b1, (uint32_t)k.Dh, k.MD, lo1);
+                } else
+#endif
+                {
+                    uint64_t w0, w1;
+                    b0 = divmod_inv64(b0, k.Dh, k.MD, w0);
+                    b1 = divmod_inv64(b1, k.Dh, k.MD, w1);
+                    lo0 = (uint32_t)w0;
+                    lo1 = (uint32_t)w1;
+                }
+                rev_exact2<T>(l0, lo0, l1, lo1, hstar, B32, k.mg, vmin);
                 l0 -= hstar;
                 l1 -= hstar;
             }
@@ -1031,9 +1046,18 @@ __device__ __forceinline__ bool adv_decode_words(const OrbitTable &ot, const Dec
             T *last = u + e.q + e.p - 1;
             if constexpr (WB == 64) {
                 for (uint32_t t = 0; t < ns; ++t) {
-                    uint64_t lo;
-                    body = divmod_inv64(body, k.Dh, k.MD, lo);
-                    rev_exact<T>(last, (uint32_t)lo, hstar, B32, k.mg, vmin);
+                    uint32_t lo;
+#if PCX_ADV_SPLIT_R32
+                    if (k.Dh <= 0x80000000ull) {
+                        body = divmod_inv64_r32(body, (uint32_t)k.Dh, k.MD, lo);
+                    } else
+#endif
+                    {
+                        uint64_t w;
+                        body = divmod_inv64(body, k.Dh, k.MD, w);
+                        lo = (uint32_t)w;
+                    }
+                    rev_exact<T>(last, lo, hstar, B32, k.mg, vmin);
                     last -= hstar;
                 }
                 bad |= (body >> 32) != 0;
