@@ -662,11 +662,36 @@ def batch_metrics(dev, n_streams=64, reps=20):
     torch.cuda.synchronize()
     t_each = med(one_by_one)
     same = all(torch.equal(b.outs[k][:sizes[k]], outs[k][:sizes[k]]) for k in range(len(xs)))
+    # each stream alone through the single-stream kernel, timed one by one (no
+    # launch gaps counted): what the batch launch is measured against
+    t_alone = 0.0
+    for c, x, o in zip(codecs, xs, outs):
+        t_alone += med(lambda: c.compress(x, out=o))
+    by_len = {}
+    for x, p in zip(xs, params):
+        k = "L%d" % p.block_len
+        by_len[k] = by_len.get(k, 0.0) + x.numel() * x.element_size() / raw
+    # the same streams autotuned with time as well as size: only the
+    # candidates within 50 % of the fastest one's time compete on size
+    params_fast = [pcb.autotune(x, variant=pc.BASIC, time_slack=0.5) for x in xs]
+    nt_f, _ = pcb.autotune_threads(xs, params_fast)
+    bf = pcb.Batch(xs, params_fast, cta_threads=nt_f)
+    gf = bf.capture()
+    gf.replay()
+    torch.cuda.synchronize()
+    t_fast = med(gf.replay)
+    assert bf.device_status() == 0
+    sizes_f = bf.nbytes.cpu().tolist()
     return {"streams": len(xs), "input_bytes": raw, "ratio": raw / sum(sizes),
             "gbs_one_graph_launch": raw / (t_batch / 1e3) / GB, "gbs_one_call_per_stream": raw / (t_each / 1e3) / GB,
+            "gbs_each_stream_alone_summed": raw / (t_alone / 1e3) / GB,
+            "input_share_by_block_len": {k: round(v, 4) for k, v in sorted(by_len.items())},
             "autotune_s": tune_s, "identical_to_single_stream": same, "cta_threads": nt,
             "ms_by_cta_threads": nt_ms,
-            "params": sorted(set("L%d_w%d" % (p.block_len, p.word_bits) for p in params))}
+            "params": sorted(set("L%d_w%d" % (p.block_len, p.word_bits) for p in params)),
+            "time_aware_autotune": {"time_slack": 0.5, "ratio": raw / sum(sizes_f),
+                                    "gbs_one_graph_launch": raw / (t_fast / 1e3) / GB, "cta_threads": nt_f,
+                                    "params": sorted(set("L%d_w%d" % (p.block_len, p.word_bits) for p in params_fast))}}
 
 
 def sweep_params(x, n, dev, steps=5):

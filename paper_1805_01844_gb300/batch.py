@@ -80,24 +80,43 @@ LENGTHS = (128, 256, 512, 1024, 2048, 4096)
 WORDS = (32, 64)
 
 
-def autotune(x, variant=native.BASIC, sample=1 << 18, lengths=LENGTHS, words=WORDS):
+def autotune(x, variant=native.BASIC, sample=1 << 18, lengths=LENGTHS, words=WORDS, time_slack=None,
+             time_sample=1 << 22, reps=3):
     """Block length and word size for stream `x`: every candidate compresses
     the first `sample` samples with the library; the smallest stream wins, a
-    tie going to the longer block (fewer blocks, less per-block work)."""
+    tie going to the longer block (fewer blocks, less per-block work).  With
+    `time_slack`, every candidate is also timed (CUDA events, `reps`
+    compressions of the first `time_sample` samples after a warm-up) and only
+    the candidates within (1 + time_slack) of the fastest one's time compete
+    on size: short blocks compress markedly slower, and a slightly smaller
+    stream rarely pays for that."""
     from . import Codec
 
     d = _dtype_bits(x)
     head = x[:sample].contiguous()
-    best = None
+    cands = []
     for w in words:
         for L in lengths:
-            codec = Codec(variant, d, w, L, max_samples=head.numel(), device=x.device)
+            codec = Codec(variant, d, w, L, max_samples=max(head.numel(), min(x.numel(), time_sample)),
+                          device=x.device)
             _, nb = codec.compress(head)
-            size = int(nb.item())
-            key = (size, -L, -w)
-            if best is None or key < best[0]:
-                best = (key, native.params(variant, d, w, L))
-    return best[1]
+            t = 0.0
+            if time_slack is not None:
+                th = x[:time_sample].contiguous()
+                out = torch.empty(codec.bound(th.numel()), dtype=torch.uint8, device=x.device)
+                codec.compress(th, out=out)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                for _ in range(reps):
+                    codec.compress(th, out=out)
+                e1.record()
+                torch.cuda.synchronize(x.device)
+                t = e0.elapsed_time(e1) / reps
+            cands.append((int(nb.item()), -L, -w, t, native.params(variant, d, w, L)))
+    if time_slack is not None:
+        t_min = min(c[3] for c in cands)
+        cands = [c for c in cands if c[3] <= (1.0 + time_slack) * t_min]
+    return min(cands, key=lambda c: c[:3])[4]
 
 
 def autotune_threads(tensors, params, candidates=(128, 256), reps=5):

@@ -94,3 +94,17 @@ def test_autotune_threads_returns_a_candidate():
     nt, times = autotune_threads(tensors, params, reps=2)
     assert nt in (128, 256) and set(times) == {128, 256} and times[nt] == min(times.values())
 
+
+
+def test_time_aware_autotune_stays_within_the_size_rule():
+    """With a time slack the choice is still a candidate of the oracle's
+    size table, and with an unbounded slack it is the smallest one."""
+    sp = datagen.batched_stream_specs(1, min_bytes=400000, max_bytes=400001, seed=6)[0]
+    x = datagen.batched_stream(sp)
+    head = x[: 1 << 16]
+    sizes = {(L, w): len(oracle.compress(head, 0, w, L)) for L in (128, 256, 512, 1024, 2048, 4096)
+             for w in (32, 64)}
+    p = autotune(to_dev(x), sample=1 << 16, time_slack=0.5, time_sample=1 << 17)
+    assert (p.block_len, p.word_bits) in sizes
+    q = autotune(to_dev(x), sample=1 << 16, time_slack=1e9, time_sample=1 << 17)
+    assert sizes[(q.block_len, q.word_bits)] == min(sizes.values())
