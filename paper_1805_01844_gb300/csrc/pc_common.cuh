@@ -341,13 +341,34 @@ PCX_HD uint32_t dec_words_bytes(uint32_t variant, uint32_t d, uint32_t w, uint32
     return (uint32_t)round_up(2 * (uint64_t)dec_chunk_words(variant, d, w, L) * (w / 8), 16);
 }
 
-// Shared memory of one warp of the warp decoder: a block's sample slot, two
-// word buffers, the records of a tile of up to `recs` blocks.
+// Short basic blocks are decoded a lane per word across the warp's whole tile
+// (k_decode_w's flat path): the tile's samples are assembled in shared
+// memory and leave in one run of 16-byte stores.
+#ifndef PCX_DEC_FLAT_MAXL
+#define PCX_DEC_FLAT_MAXL 128
+#endif
+PCX_HD bool dec_flat(uint32_t variant, uint32_t d, uint32_t w, uint32_t L)
+{
+    return variant == PC_VARIANT_BASIC && !dec_chunked(variant, d, w, L) && L <= PCX_DEC_FLAT_MAXL &&
+           (L * (d / 8)) % 16 == 0;
+}
+
+// Shared memory of one warp of the warp decoder before its block records: a
+// block's sample slot and two word buffers, or (flat path) the samples of a
+// tile of `recs` blocks.
+PCX_HD uint32_t decw_front_bytes(uint32_t variant, uint32_t d, uint32_t w, uint32_t L, uint32_t recs)
+{
+    const uint64_t slot = round_up((uint64_t)(L + 2 * kPad) * (d / 8), 16) + dec_words_bytes(variant, d, w, L);
+    const uint64_t flat = dec_flat(variant, d, w, L) ? round_up((uint64_t)recs * L * (d / 8), 16) : 0;
+    return (uint32_t)(slot > flat ? slot : flat);
+}
+
+// Shared memory of one warp of the warp decoder: the front part above, the
+// records of a tile of up to `recs` blocks.
 PCX_HD uint32_t decw_warp_bytes_for(uint32_t variant, uint32_t d, uint32_t w, uint32_t L, uint32_t recs)
 {
-    const uint64_t slot = round_up((uint64_t)(L + 2 * kPad) * (d / 8), 16);
     const uint64_t rec = (uint64_t)recs * (variant == PC_VARIANT_BASIC ? kDecRecBasic : kDecRecAdvanced);
-    return (uint32_t)(slot + dec_words_bytes(variant, d, w, L) + rec);
+    return (uint32_t)(decw_front_bytes(variant, d, w, L, recs) + rec);
 }
 
 // Warps per CTA that fit a 200 KB budget (1 to 4; 0: does not fit, which no

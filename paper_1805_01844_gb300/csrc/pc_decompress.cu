@@ -1145,6 +1145,100 @@ __device__ __forceinline__ DecBlock dec_setup(const uint8_t *in, uint64_t gb, ui
     return dec_setup_entry<WB, VAR, ORB>(vmin, Bm1, n_b, L, ot, ws, limit_ns);
 }
 
+// One basic word by one lane, its block's constants per lane: digits
+// (least significant first) d_i of s, i < p, the first nd of them stored at
+// shared address a (+ vmin), the rest checked to be 0 (padding).  Returns
+// true if the word is not the image of valid digits.
+template <typename T, uint32_t WB>
+__device__ __forceinline__ bool decode_word_lane(uint64_t s, uint32_t p, uint32_t nd, uint32_t hstar, uint64_t B,
+                                                 uint32_t vmin, Magic32 mg, uint64_t Dh, uint64_t MD, uint32_t a)
+{
+    constexpr uint32_t E = sizeof(T);
+    const uint32_t B32 = (uint32_t)B;
+    bool bad = false;
+    uint32_t i = 0;
+    // h digits of x; returns the last quotient (the piece's top digit)
+    auto piece = [&](uint32_t x, uint32_t h) -> uint32_t {
+        for (uint32_t t = 0; t + 1 < h; ++t, ++i) {
+            const uint32_t q = magic_div(x, mg);
+            const uint32_t dg = x - q * B32;
+            if (i < nd) st_shared<T>(a + i * E, dg + vmin);
+            else bad |= dg != 0;
+            x = q;
+        }
+        if (i < nd) st_shared<T>(a + i * E, x + vmin);
+        else bad |= x != 0;
+        ++i;
+        return x;
+    };
+    uint32_t rem = p;
+    uint64_t hv = s;
+    if (WB == 64 && p > hstar) {
+        uint32_t lo;
+        if (Dh <= 0x80000000ull) hv = divmod_inv64_r32(hv, (uint32_t)Dh, MD, lo);
+        else {
+            uint64_t l64;
+            hv = divmod_inv64(hv, Dh, MD, l64);
+            lo = (uint32_t)l64;
+        }
+        piece(lo, hstar);
+        rem = p - hstar;
+        if (rem > hstar) {  // p = 2 h* + 1: a middle piece of h* digits
+            if (Dh <= 0x80000000ull) hv = divmod_inv64_r32(hv, (uint32_t)Dh, MD, lo);
+            else {
+                uint64_t l64;
+                hv = divmod_inv64(hv, Dh, MD, l64);
+                lo = (uint32_t)l64;
+            }
+            piece(lo, hstar);
+            rem -= hstar;
+        }
+    }
+    if (WB == 64) bad |= (hv >> 32) != 0;
+    const uint32_t top = piece((uint32_t)hv, rem);
+    bad |= sizeof(T) == 2 ? top >= B32 : top >= B;
+    return bad;
+}
+
+// The words [0, Wt) of a warp tile (global, from g), a lane per word in
+// rounds of 32: each lane finds its block (the last record whose word offset
+// is <= its word; offsets only grow), decodes its word with that block's
+// constants and stores the digits at the block's samples in the tile's
+// shared buffer ut (block b at b L); blocks without words are filled with
+// their minimum.  The next round's word is loaded before the current one is
+// decoded.  Returns true for an invalid word (this lane's).
+template <typename T, uint32_t WB>
+__device__ bool decode_flat_tile(const typename WordT<T, WB>::type *g, uint32_t Wt, const uint8_t *recs,
+                                 uint32_t kRec, uint32_t nblk, uint32_t L, T *ut)
+{
+    using Word = typename WordT<T, WB>::type;
+    const uint32_t lane = threadIdx.x & 31u;
+    auto rec = [&](uint32_t b) -> const DecBlock & { return *reinterpret_cast<const DecBlock *>(recs + b * kRec); };
+    const uint32_t ua = (uint32_t)__cvta_generic_to_shared(ut);
+    bool bad = false;
+    uint32_t b = 0;
+    Word s = lane < Wt ? g[lane] : Word(0);
+    for (uint32_t g0 = 0; g0 < Wt; g0 += 32) {
+        const uint32_t j = g0 + lane;
+        const Word next = j + 32 < Wt ? g[j + 32] : Word(0);
+        if (j < Wt) {
+            while (b + 1 < nblk && rec(b + 1).woff <= j) ++b;
+            const DecBlock &k = rec(b);
+            const uint32_t jw = j - k.woff, first = jw * k.p;
+            const uint32_t nd = min(k.p, k.n_b - first);
+            bad |= decode_word_lane<T, WB>((uint64_t)s, k.p, nd, k.hstar, k.B, k.vmin, k.mg, k.Dh, k.MD,
+                                           ua + (b * L + first) * (uint32_t)sizeof(T));
+        }
+        s = next;
+    }
+    for (uint32_t c = 0; c < nblk; ++c) {
+        const DecBlock &k = rec(c);
+        if (k.W == 0)
+            for (uint32_t i = lane; i < k.n_b; i += 32) ut[c * L + i] = (T)k.vmin;
+    }
+    return bad;
+}
+
 // Warp-granular decoding (basic, and advanced with the series table on 16-bit
 // data): no shared barrier at all.  A warp owns a tile of consecutive blocks
 // (up to dec_tile_cap, fewer for a short stream); lane b sets up block b
@@ -1174,8 +1268,9 @@ k_decode_w(const uint8_t *__restrict__ in, uint32_t L, T *__restrict__ out, uint
     Word *wbuf = reinterpret_cast<Word *>(smem + warp * warp_bytes + slot_bytes);
     // then the tile's block records
     constexpr uint32_t kRec = VAR == PC_VARIANT_BASIC ? kDecRecBasic : kDecRecAdvanced;
-    uint8_t *recs = smem + warp * warp_bytes + slot_bytes + dec_words_bytes(VAR, D, WB, L);
+    uint8_t *recs = smem + warp * warp_bytes + decw_front_bytes(VAR, D, WB, L, dec_tile_cap(VAR, D, WB, L));
     auto rec = [&](uint32_t b) -> const DecBlock & { return *reinterpret_cast<const DecBlock *>(recs + b * kRec); };
+    const bool flat = dec_flat(VAR, D, WB, L);  // the flat path reuses the slot and buffers for the tile's samples
 
     if (*reinterpret_cast<volatile uint32_t *>(&ws->status) != PC_OK) return;
     const uint64_t *h64 = reinterpret_cast<const uint64_t *>(in);
@@ -1202,6 +1297,19 @@ k_decode_w(const uint8_t *__restrict__ in, uint32_t L, T *__restrict__ out, uint
             nz = __ballot_sync(0xFFFFFFFFu, lane < nblk && mine.W > 0);
             if (lane < nblk) store_rec<VAR>(recs, mine, lane);
             __syncwarp();
+        }
+        if constexpr (!CHUNKED && VAR == PC_VARIANT_BASIC) {
+            if (flat) {  // short blocks: a lane per word across the tile
+                const uint32_t Wt = __shfl_sync(0xFFFFFFFFu, nz ? rec(nblk - 1).woff + rec(nblk - 1).W : 0u, 0);
+                bad |= decode_flat_tile<T, WB>(payload + offsets[wt], Wt, recs, kRec, nblk, L, u);
+                __syncwarp();
+                uint32_t nt = 0;  // the tile's samples
+                for (uint32_t b = 0; b < nblk; ++b) nt += rec(b).n_b;
+                copy_block_out<T>(out + blk0 * L, u, nt, L);
+                __syncwarp();
+                if (wt == n_wt - 1 && lane == 0) *n_out = n;
+                continue;
+            }
         }
         if constexpr (!CHUNKED) {
             const uint64_t base = offsets[wt];
