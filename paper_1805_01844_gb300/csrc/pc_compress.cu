@@ -5,9 +5,58 @@
 
 namespace pcx {
 
+#ifndef PCX_SHORT_TILES
+#define PCX_SHORT_TILES 1
+#endif
+
+// Long streams of short 16-bit basic blocks (L <= 128, L / 8 a power of two):
+// look-back tiles of 128 whole blocks (compress_tile_short).
+template <typename T, uint32_t WB>
+static cudaError_t launch_compress_short(const LaunchArgs &a, bool &taken)
+{
+    taken = false;
+    if (!PCX_SHORT_TILES || a.L > 128 || a.L % 8 != 0 || ((a.L / 8) & (a.L / 8 - 1)) != 0)
+        return cudaSuccess;
+    const uint64_t n_tiles = ceil_div(a.n_blocks, (uint64_t)kShortTileBlocks);
+    if (n_tiles < kSmallTiles) return cudaSuccess;
+    taken = true;
+    auto kern = k_compress_short<T, WB>;
+    const uint32_t smem = short_smem(sizeof(T) * 8, a.L);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0, dev = 0, sms = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kShortThreads, smem)) != cudaSuccess)
+        return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    uint64_t grid = (uint64_t)per_sm * sms;
+    if (n_tiles < grid) grid = n_tiles;
+    StreamArgs sa;
+    sa.in = a.in;
+    sa.n = a.n;
+    sa.L = a.L;
+    sa.out = static_cast<uint8_t *>(a.out);
+    sa.out_bytes = a.out_count;
+    sa.status = a.status;
+    sa.n_blocks = a.n_blocks;
+    sa.n_tiles = n_tiles;
+    sa.tb = kShortTileBlocks;
+    sa.ot = OrbitTable{a.orb_flags, a.orb_hdr, static_cast<ulonglong2 *>(a.orb_slots), &a.ws->orbit_cursor};
+    kern<<<(unsigned)grid, kShortThreads, smem, a.stream>>>(sa, a.ws, a.limit_ns);
+    return cudaGetLastError();
+}
+
 template <typename T, uint32_t WB, uint32_t VAR, bool ORB, uint32_t NT>
 static cudaError_t launch_compress_t(const LaunchArgs &a)
 {
+    if constexpr (VAR == PC_VARIANT_BASIC && sizeof(T) == 2) {
+        bool taken = false;
+        const cudaError_t e = launch_compress_short<T, WB>(a, taken);
+        if (taken || e != cudaSuccess) return e;
+    }
     const TileCfg cfg1 = tile_cfg(kKernelCompress, VAR, sizeof(T) * 8, WB, a.L, ORB, NT);
     // basic streams long enough for look-back tiles of several full stage
     // tiles on every SM: one look-back per multi_k stage tiles

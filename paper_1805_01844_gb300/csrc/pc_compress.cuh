@@ -847,6 +847,201 @@ __device__ void write_empty_stream(const StreamArgs &sa)
 // registers, which round up past a third of the register file, only two fit
 // and compression ran 24 % slower), while 32-bit advanced tiles that walk
 // their series use up to 100 KB and fit two.
+// ---- short basic blocks (L <= 128) ---------------------------------------
+// A look-back tile of up to kShortTileBlocks short blocks, staged whole (no
+// restaging): each warp stages its blocks as in compress_tile; after one CTA
+// barrier, groups of L / VE lanes take a block's min/max together (one
+// 16-byte shared load per lane, a reduction over the group) and set its
+// padding; a thread per block counts its words; a CTA scan and one look-back
+// per tile; table entries by a thread per block and words packed a lane per
+// word across the tile (pack_basic_flat).  The stream's ragged last block
+// takes block_minmax.
+constexpr uint32_t kShortTileBlocks = 128;
+constexpr uint32_t kShortThreads = 256;
+
+struct ShortVars {
+    uint64_t B[kShortTileBlocks];
+    PackK pk[kShortTileBlocks];
+    uint32_t vmin[kShortTileBlocks];
+    uint32_t W[kShortTileBlocks];
+    uint32_t woff[kShortTileBlocks];
+    uint32_t p[kShortTileBlocks];
+    uint32_t wtot[kShortThreads / 32];
+    uint64_t excl;
+    uint32_t agg;
+    uint32_t ok;
+};
+
+PCX_HD uint32_t short_stage_bytes(uint32_t d, uint32_t L)
+{
+    return (uint32_t)round_up((uint64_t)(L + kPad) * (d / 8), 16);
+}
+
+PCX_HD uint32_t short_smem(uint32_t d, uint32_t L)
+{
+    return (uint32_t)round_up((uint64_t)kShortTileBlocks * short_stage_bytes(d, L) + sizeof(ShortVars), 16);
+}
+
+template <typename T, uint32_t WB>
+__device__ void compress_tile_short(const StreamArgs &sa, uint64_t tile, uint8_t *smem, WsHeader *ws,
+                                    uint64_t limit_ns, uint32_t &phase)
+{
+    using Word = typename WordOf<T, WB>::type;
+    constexpr uint32_t D = sizeof(T) * 8, NT = kShortThreads, NW = NT / 32;
+    constexpr uint32_t VE = 16 / sizeof(T);
+    const uint32_t L = sa.L;
+    const uint32_t SB = short_stage_bytes(D, L);
+    ShortVars &sv = *reinterpret_cast<ShortVars *>(smem + (uint64_t)kShortTileBlocks * SB);
+    const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+    const T *in = static_cast<const T *>(sa.in);
+    const uint64_t n = sa.n, n_blocks = sa.n_blocks, n_tiles = sa.n_tiles;
+    const uint64_t payload_off = PC_HEADER_BYTES + table_bytes(n_blocks, D);
+    const uint64_t blk0 = tile * sa.tb;
+    const uint32_t nblk = (uint32_t)umin64(sa.tb, n_blocks - blk0);
+    const uint64_t cnt = umin64(n - blk0 * L, (uint64_t)nblk * L);
+    auto slot = [&](uint32_t b) -> T * { return reinterpret_cast<T *>(smem + (uint64_t)b * SB); };
+
+    // 1. each warp stages its blocks (warp, warp + NW, ...): lane i issues the
+    // bulk copy of the warp's i-th block once lane 0 has set the expected bytes
+    {
+        uint32_t bytes = 0;
+        for (uint32_t b = warp + lane * NW; b < nblk; b += 32 * NW)
+            bytes += ((uint32_t)umin64(L, cnt - (uint64_t)b * L) / VE) * 16u;
+        bytes = __reduce_add_sync(0xFFFFFFFFu, bytes);
+        fence_proxy_async_smem();
+        if (lane == 0) mbar_arrive_expect_tx(&g_stage_bar[warp], bytes);
+        __syncwarp();
+        for (uint32_t b = warp + lane * NW; b < nblk; b += 32 * NW) {
+            const uint32_t nb16 = ((uint32_t)umin64(L, cnt - (uint64_t)b * L) / VE) * 16u;
+            if (nb16) bulk_copy_g2s(slot(b), in + (blk0 + b) * L, nb16, &g_stage_bar[warp]);
+        }
+    }
+    const bool ragged = cnt % L != 0;  // the stream's last block is short (only that one can be)
+    if (cnt % VE != 0 && (nblk - 1) % NW == warp) {
+        const uint32_t b = nblk - 1;
+        const uint32_t n_b = (uint32_t)(cnt - (uint64_t)b * L);
+        for (uint32_t e = n_b / VE * VE + lane; e < n_b; e += 32) slot(b)[e] = in[(blk0 + b) * L + e];
+    }
+    stage_wait(warp, phase, ws, limit_ns);
+    ++phase;
+    __syncthreads();  // every block staged: any group may take any block
+
+    // 2. min / max: G lanes per whole block, a 16-byte vector each
+    {
+        const uint32_t G = L / VE, gi = threadIdx.x & (G - 1);
+        const uint32_t gmask = G == 32 ? 0xFFFFFFFFu : (((1u << G) - 1u) << (lane & ~(G - 1)));
+        const uint32_t nfull = ragged ? nblk - 1 : nblk;
+        for (uint32_t b = threadIdx.x / G; b < nfull; b += NT / G) {
+            const uint4 x = reinterpret_cast<const uint4 *>(slot(b))[gi];
+            uint32_t mn, mx;
+            if constexpr (sizeof(T) == 2) {
+                const uint32_t pmn = min_u16x2(min_u16x2(x.x, x.y), min_u16x2(x.z, x.w));
+                const uint32_t pmx = max_u16x2(max_u16x2(x.x, x.y), max_u16x2(x.z, x.w));
+                mn = min(pmn & 0xFFFFu, pmn >> 16);
+                mx = max(pmx & 0xFFFFu, pmx >> 16);
+            } else {
+                mn = min(min(x.x, x.y), min(x.z, x.w));
+                mx = max(max(x.x, x.y), max(x.z, x.w));
+            }
+            mn = __reduce_min_sync(gmask, mn);
+            mx = __reduce_max_sync(gmask, mx);
+            for (uint32_t i = gi; i < kPad; i += G) slot(b)[L + i] = (T)mn;
+            if (gi == 0) {
+                sv.vmin[b] = mn;
+                sv.B[b] = (uint64_t)mx - mn + 1;
+            }
+        }
+        if (ragged && warp == NW - 1) {
+            const uint32_t b = nblk - 1;
+            block_minmax<T>(slot(b), (uint32_t)(cnt - (uint64_t)b * L), &sv.vmin[b], &sv.B[b]);
+        }
+    }
+    __syncthreads();
+
+    // 3-4. word counts (a thread per block), CTA scan, look-back
+    uint32_t W = 0;
+    if (threadIdx.x < nblk) {
+        const uint32_t b = threadIdx.x;
+        const uint64_t B = sv.B[b];
+        if (B > 1) {
+            const uint32_t n_b = (uint32_t)umin64(L, cnt - (uint64_t)b * L);
+            const uint32_t p = basic_p(B, WB);
+            sv.p[b] = p;
+            W = (n_b + p - 1) / p;
+            sv.pk[b] = basic_pack_k(B, p, sv.vmin[b], WB);
+        }
+        sv.W[b] = W;
+    }
+    const uint32_t incl = warp_incl_scan_u32(W);
+    if (lane == 31) sv.wtot[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const uint32_t t = lane < NW ? sv.wtot[lane] : 0u;
+        const uint32_t ti = warp_incl_scan_u32(t);
+        const uint32_t agg = __shfl_sync(0xFFFFFFFFu, ti, 31);
+        uint64_t excl = 0;
+        bool ok = false;
+        if (stage_dead()) {  // the staged samples are not whole: successors stop on this tile's error
+            if (lane == 0) st_release(&sa.status[tile], kFlagError);
+        } else {
+            lookback_publish(sa.status, tile, agg);
+            ok = lookback_complete(sa.status, tile, agg, ws, limit_ns, &excl);
+        }
+        __syncwarp();
+        if (lane < NW) sv.wtot[lane] = ti - t;
+        if (lane == 0) {
+            sv.agg = agg;
+            sv.excl = excl;
+            sv.ok = ok ? 1u : 0u;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < nblk) sv.woff[threadIdx.x] = sv.wtot[warp] + incl - W;
+    __syncthreads();
+
+    // 5. table entries, packed words, and the stream's closing bytes
+    if (sv.ok) {
+        for (uint32_t b = threadIdx.x; b < nblk; b += NT) {
+            const uint64_t gb = blk0 + b;
+            const uint64_t Bm1 = sv.B[b] - 1;
+            if constexpr (D == 16) {
+                reinterpret_cast<uint32_t *>(sa.out + PC_HEADER_BYTES)[gb] = sv.vmin[b] | ((uint32_t)Bm1 << 16);
+            } else {
+                reinterpret_cast<uint64_t *>(sa.out + PC_HEADER_BYTES)[gb] = (uint64_t)sv.vmin[b] | (Bm1 << 32);
+            }
+        }
+        Word *payload = reinterpret_cast<Word *>(sa.out + payload_off);
+        pack_basic_flat<T, WB, NT>(smem, SB, sv.woff, sv.p, sv.B, sv.pk, nblk, sv.agg, payload + sv.excl);
+        if (tile == n_tiles - 1) {
+            const uint64_t payload_words = sv.excl + sv.agg;
+            const uint64_t tend = PC_HEADER_BYTES + n_blocks * 2u * (D / 8);
+            for (uint64_t o = tend + threadIdx.x; o < payload_off; o += NT) sa.out[o] = 0;
+            if (threadIdx.x == 0) {
+                write_header<D, WB, PC_VARIANT_BASIC>(sa.out, L, n, n_blocks, payload_words);
+                *sa.out_bytes = payload_off + payload_words * (WB / 8);
+            }
+        }
+    }
+    __syncthreads();  // the stage and the tile arrays are free again
+}
+
+template <typename T, uint32_t WB>
+__global__ void __launch_bounds__(kShortThreads, 4) k_compress_short(StreamArgs sa, WsHeader *ws, uint64_t limit_ns)
+{
+    extern __shared__ __align__(16) uint8_t smem[];
+    __shared__ uint32_t s_tile;
+    stage_bars_init();
+    uint32_t phase = 0;
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = g_stage_dead ? 0xFFFFFFFFu : atomicAdd(&ws->ticket, 1u);
+        __syncthreads();
+        const uint64_t tile = s_tile;
+        __syncthreads();
+        if (tile >= sa.n_tiles) break;
+        compress_tile_short<T, WB>(sa, tile, smem, ws, limit_ns, phase);
+    }
+}
+
 #ifndef PCX_COMPRESS_MIN_CTAS_BASIC
 #define PCX_COMPRESS_MIN_CTAS_BASIC 3
 #endif
