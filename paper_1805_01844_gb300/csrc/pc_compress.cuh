@@ -847,7 +847,7 @@ __device__ void write_empty_stream(const StreamArgs &sa)
 // registers, which round up past a third of the register file, only two fit
 // and compression ran 24 % slower), while 32-bit advanced tiles that walk
 // their series use up to 100 KB and fit two.
-// ---- short basic blocks (L <= 128) ---------------------------------------
+// ---- short basic blocks (L <= 256) ---------------------------------------
 // A look-back tile of up to kShortTileBlocks short blocks, staged whole (no
 // restaging): each warp stages its blocks as in compress_tile; after one CTA
 // barrier, groups of L / VE lanes take a block's min/max together (one
@@ -877,9 +877,13 @@ PCX_HD uint32_t short_stage_bytes(uint32_t d, uint32_t L)
     return (uint32_t)round_up((uint64_t)(L + kPad) * (d / 8), 16);
 }
 
+// Blocks per look-back tile: 128, or 64 for blocks of 256 samples (so that
+// four CTAs of 256 threads share an SM's shared memory).
+PCX_HD uint32_t short_tile_blocks(uint32_t L) { return L <= 128 ? kShortTileBlocks : kShortTileBlocks / 2; }
+
 PCX_HD uint32_t short_smem(uint32_t d, uint32_t L)
 {
-    return (uint32_t)round_up((uint64_t)kShortTileBlocks * short_stage_bytes(d, L) + sizeof(ShortVars), 16);
+    return (uint32_t)round_up((uint64_t)short_tile_blocks(L) * short_stage_bytes(d, L) + sizeof(ShortVars), 16);
 }
 
 template <typename T, uint32_t WB>
@@ -891,7 +895,7 @@ __device__ void compress_tile_short(const StreamArgs &sa, uint64_t tile, uint8_t
     constexpr uint32_t VE = 16 / sizeof(T);
     const uint32_t L = sa.L;
     const uint32_t SB = short_stage_bytes(D, L);
-    ShortVars &sv = *reinterpret_cast<ShortVars *>(smem + (uint64_t)kShortTileBlocks * SB);
+    ShortVars &sv = *reinterpret_cast<ShortVars *>(smem + (uint64_t)sa.tb * SB);
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
     const T *in = static_cast<const T *>(sa.in);
     const uint64_t n = sa.n, n_blocks = sa.n_blocks, n_tiles = sa.n_tiles;

@@ -1,5 +1,5 @@
-"""Long streams of short 16-bit basic blocks (L = 8 ... 128) are compressed
-with look-back tiles of 128 whole blocks (group min/max, a thread per block
+"""Long streams of short 16-bit basic blocks (L = 8 ... 256) are compressed
+with look-back tiles of 128 (L = 256: 64) whole blocks (group min/max, a thread per block
 for the word counts, words packed a lane per word across the tile).  Every
 byte of such streams equals the oracle's — constant blocks (no words), wide
 blocks, a ragged last block — and the stream decodes back."""
@@ -13,16 +13,16 @@ import oracle  # noqa: E402
 import paper_1805_01844_gb300 as pc  # noqa: E402
 from paper_1805_01844_gb300 import native  # noqa: E402
 
-SHORT_TILE_BLOCKS = 128
 SMALL_TILES = 2432  # tiles a stream needs before it takes these tiles (152 SMs x 16)
 
 
-@pytest.mark.parametrize("L,w", [(8, 64), (32, 32), (64, 64), (128, 32), (128, 64)])
+@pytest.mark.parametrize("L,w", [(8, 64), (32, 32), (64, 64), (128, 32), (128, 64), (256, 64)])
 def test_short_block_tiles_match_oracle(L, w):
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     dev = torch.device("cuda:0")
-    n_blocks = SHORT_TILE_BLOCKS * SMALL_TILES + 77
+    tile_blocks = 128 if L <= 128 else 64  # blocks per look-back tile
+    n_blocks = tile_blocks * SMALL_TILES + 77
     n = (n_blocks - 1) * L + max(1, L // 2 - 3)  # ragged last block
     rng = np.random.default_rng(L + w)
     x = np.clip(rng.normal(1200, 9, n), 0, 65535).astype(np.uint16)
