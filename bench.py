@@ -606,7 +606,33 @@ def white_noise_2e30(dev, peak, steps=20):
            "decompress_roofline_frac": (raw + size) / (md / 1e3) / GB / peak}
     out["compress_pct_hbm"] = 100 * out["compress_gbs"] / peak
     out["decompress_pct_hbm"] = 100 * out["decompress_gbs"] / peak
-    del x, sbuf, ybuf, codec
+    del sbuf, ybuf, codec
+    # the same samples in short blocks (the block lengths of Fig. 7's best
+    # ratios and of the learned chooser's short options), basic, w = 64
+    short = []
+    for L in (32, 64, 128, 256):
+        codec = pc.Codec(pc.BASIC, 16, 64, L, max_samples=n, device=dev)
+        sbuf = torch.empty(codec.bound(n), dtype=torch.uint8, device=dev)
+        ybuf = torch.empty(n, dtype=torch.int16, device=dev)
+        tc, td = [], []
+        for k in range(8):
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            e[0].record()
+            _, nb = codec.compress(x, out=sbuf)
+            e[1].record()
+            codec.decompress(sbuf, sbuf.numel(), n, out=ybuf)
+            e[2].record()
+            torch.cuda.synchronize()
+            if k >= 3:
+                tc.append(e[0].elapsed_time(e[1]))
+                td.append(e[1].elapsed_time(e[2]))
+        assert codec.device_status() == 0 and torch.equal(ybuf, x), L
+        mc, md = sorted(tc)[len(tc) // 2], sorted(td)[len(td) // 2]
+        short.append({"block_len": L, "ratio": raw / int(nb.item()), "compress_gbs": raw / (mc / 1e3) / GB,
+                      "decompress_gbs": raw / (md / 1e3) / GB})
+        del sbuf, ybuf, codec
+    out["short_blocks_w64"] = short
+    del x
     torch.cuda.empty_cache()
     return out
 
