@@ -25,7 +25,7 @@ struct BatchItemDev {
     uint64_t n_blocks;
     uint64_t n_tiles;  // real tiles (0 for an empty item, which still owns one ticket)
     uint32_t L;
-    uint32_t key;      // dtype 32 << 2 | word 64 << 1 | advanced
+    uint32_t key;      // short tiles << 3 | dtype 32 << 2 | word 64 << 1 | advanced
     uint32_t tb;       // blocks per tile
     uint32_t pad_;
 };
@@ -105,7 +105,7 @@ k_compress_batch(const BatchItemDev *__restrict__ items, const uint64_t *__restr
         sa.ot = (it.key & 2u) ? ot64 : ot32;
         const uint64_t tile = t - prefix[i];
         if (it.n_tiles == 0) {
-            switch (it.key) {
+            switch (it.key & 7u) {
             case 0: empty_item<16, 32, 0>(sa); break;
             case 1: empty_item<16, 32, 1>(sa); break;
             case 2: empty_item<16, 64, 0>(sa); break;
@@ -116,6 +116,13 @@ k_compress_batch(const BatchItemDev *__restrict__ items, const uint64_t *__restr
             default: empty_item<32, 64, 1>(sa); break;
             }
             continue;
+        }
+        if constexpr (NT == kShortThreads) {
+            if (it.key & 8u) {  // short 16-bit basic blocks: look-back tiles of whole short blocks
+                if (it.key & 2u) compress_tile_short<uint16_t, 64>(sa, tile, smem, ws, limit_ns, phase);
+                else compress_tile_short<uint16_t, 32>(sa, tile, smem, ws, limit_ns, phase);
+                continue;
+            }
         }
         switch (it.key) {
         case 0: compress_tile<uint16_t, 32, 0, false, NT>(sa, tile, smem, ws, limit_ns, phase); break;
@@ -352,11 +359,23 @@ namespace {
 
 bool a16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
+// Items of short 16-bit basic blocks take the short-block tiles in 256-thread
+// launches.
+bool item_short(const pc_params &p, uint32_t nt)
+{
+    return nt == kShortThreads && short_tiles_ok(p.variant, p.dtype_bits, p.word_bits, p.block_len);
+}
+
+uint32_t item_tb(const pc_params &p, uint32_t nt)
+{
+    if (item_short(p, nt)) return short_tile_blocks(p.block_len);
+    return tile_cfg(kKernelCompress, p.variant, p.dtype_bits, p.word_bits, p.block_len, true, nt).tb;
+}
+
 uint64_t item_tiles(const pc_batch_item &it, uint32_t nt)
 {
     const pc_params &p = it.params;
-    const TileCfg cfg = tile_cfg(kKernelCompress, p.variant, p.dtype_bits, p.word_bits, p.block_len, true, nt);
-    return ceil_div(ceil_div(it.n_samples, p.block_len), cfg.tb);
+    return ceil_div(ceil_div(it.n_samples, p.block_len), item_tb(p, nt));
 }
 
 // Per call: header words and look-back words cleared, the tables kept or
@@ -502,7 +521,8 @@ pc_status pc_batch_describe(const pc_batch_item *items, uint32_t n_items, pc_bat
         const uint64_t t = item_tiles(it, nt);
         total += t ? t : 1;
         const TileCfg cfg = tile_cfg(kKernelCompress, p.variant, p.dtype_bits, p.word_bits, p.block_len, true, nt);
-        if (cfg.smem > smem) smem = cfg.smem;
+        const uint32_t need_smem = item_short(p, nt) ? short_smem(p.dtype_bits, p.block_len) : cfg.smem;
+        if (need_smem > smem) smem = need_smem;
     }
     if (total >> 31) return PC_ERR_UNSUPPORTED;  // tickets are 32-bit
     info->n_items = n_items;
@@ -534,9 +554,10 @@ pc_status pc_batch_plan(const pc_batch_item *items, uint32_t n_items, const pc_b
         d.out_bytes = it.d_out_bytes;
         d.n_blocks = ceil_div(it.n_samples, p.block_len);
         d.n_tiles = item_tiles(it, info->cta_threads);
-        d.tb = tile_cfg(kKernelCompress, p.variant, p.dtype_bits, p.word_bits, p.block_len, true, info->cta_threads).tb;
+        d.tb = item_tb(p, info->cta_threads);
         d.L = p.block_len;
-        d.key = (p.dtype_bits == 32 ? 4u : 0u) | (p.word_bits == 64 ? 2u : 0u) | (p.variant ? 1u : 0u);
+        d.key = (item_short(p, info->cta_threads) ? 8u : 0u) | (p.dtype_bits == 32 ? 4u : 0u) |
+                (p.word_bits == 64 ? 2u : 0u) | (p.variant ? 1u : 0u);
         dv[i] = d;
         prefix[i] = run;
         run += d.n_tiles ? d.n_tiles : 1;

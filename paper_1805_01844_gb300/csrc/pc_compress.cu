@@ -5,12 +5,6 @@
 
 namespace pcx {
 
-#ifndef PCX_SHORT_TILES
-#define PCX_SHORT_TILES 1
-#endif
-#ifndef PCX_SHORT_MAXL
-#define PCX_SHORT_MAXL 256
-#endif
 
 // Long streams of short 16-bit basic blocks (L <= PCX_SHORT_MAXL, L / 8 a
 // power of two): look-back tiles of 128 (L = 256: 64) whole blocks
@@ -19,11 +13,7 @@ template <typename T, uint32_t WB>
 static cudaError_t launch_compress_short(const LaunchArgs &a, bool &taken)
 {
     taken = false;
-    // (L = 256 with 32-bit words, ~43 words per block, measured 18 % slower
-    // than the multi-stage tiles; with 64-bit words 1-14 % faster)
-    if (!PCX_SHORT_TILES || a.L > PCX_SHORT_MAXL || a.L % 8 != 0 || ((a.L / 8) & (a.L / 8 - 1)) != 0 ||
-        (a.L > 128 && WB == 32))
-        return cudaSuccess;
+    if (!short_tiles_ok(PC_VARIANT_BASIC, sizeof(T) * 8, WB, a.L)) return cudaSuccess;
     const uint32_t tb = short_tile_blocks(a.L);
     const uint64_t n_tiles = ceil_div(a.n_blocks, (uint64_t)tb);
     if (n_tiles < kSmallTiles) return cudaSuccess;

@@ -877,6 +877,22 @@ PCX_HD uint32_t short_stage_bytes(uint32_t d, uint32_t L)
     return (uint32_t)round_up((uint64_t)(L + kPad) * (d / 8), 16);
 }
 
+#ifndef PCX_SHORT_TILES
+#define PCX_SHORT_TILES 1
+#endif
+#ifndef PCX_SHORT_MAXL
+#define PCX_SHORT_MAXL 256
+#endif
+// Streams (or batch items) of short 16-bit basic blocks that take these
+// tiles: L / 8 a power of two, L <= 128, or L = 256 with 64-bit words (with
+// 32-bit words, ~43 words per block, L = 256 measured 18 % slower than the
+// multi-stage tiles; with 64-bit words 1-14 % faster).
+PCX_HD bool short_tiles_ok(uint32_t variant, uint32_t d, uint32_t w, uint32_t L)
+{
+    return PCX_SHORT_TILES && variant == PC_VARIANT_BASIC && d == 16 && L <= PCX_SHORT_MAXL && L % 8 == 0 &&
+           ((L / 8) & (L / 8 - 1)) == 0 && (L <= 128 || w == 64);
+}
+
 // Blocks per look-back tile: 128, or 64 for blocks of 256 samples (so that
 // four CTAs of 256 threads share an SM's shared memory).
 PCX_HD uint32_t short_tile_blocks(uint32_t L) { return L <= 128 ? kShortTileBlocks : kShortTileBlocks / 2; }

@@ -108,3 +108,25 @@ def test_time_aware_autotune_stays_within_the_size_rule():
     assert (p.block_len, p.word_bits) in sizes
     q = autotune(to_dev(x), sample=1 << 16, time_slack=1e9, time_sample=1 << 17)
     assert sizes[(q.block_len, q.word_bits)] == min(sizes.values())
+
+
+def test_short_block_items_match_oracle():
+    """16-bit basic items of short blocks take look-back tiles of whole
+    short blocks in 256-thread launches: every item equals the oracle's
+    stream, from one sample to several tiles, ragged last blocks included."""
+    rng = np.random.default_rng(9)
+    hosts, tensors, params = [], [], []
+    for i, (L, w) in enumerate([(8, 64), (32, 32), (64, 64), (128, 32), (128, 64), (256, 64), (256, 32), (16, 64)]):
+        for n in (1, L * 128 - 3, L * 300 + 5):
+            x = np.clip(rng.normal(500, 20, n), 0, 65535).astype(np.uint16)
+            if n > 10:
+                x[rng.integers(0, n, max(1, n // 500))] = 65535
+                x[: min(n, 3 * L)] = 9
+            hosts.append(x)
+            tensors.append(to_dev(x))
+            params.append(native.params(0, 16, w, L))
+    b = Batch(tensors, params, cta_threads=256)
+    b.compress()
+    assert b.device_status() == 0
+    for x, p, s in zip(hosts, params, b.streams()):
+        assert s == oracle.compress(x, 0, p.word_bits, p.block_len), p
