@@ -118,9 +118,13 @@ k_compress_batch(const BatchItemDev *__restrict__ items, const uint64_t *__restr
             continue;
         }
         if constexpr (NT == kShortThreads) {
-            if (it.key & 8u) {  // short 16-bit basic blocks: look-back tiles of whole short blocks
-                if (it.key & 2u) compress_tile_short<uint16_t, 64>(sa, tile, smem, ws, limit_ns, phase);
-                else compress_tile_short<uint16_t, 32>(sa, tile, smem, ws, limit_ns, phase);
+            if (it.key & 8u) {  // short basic blocks: look-back tiles of whole short blocks
+                switch (it.key & 6u) {
+                case 0: compress_tile_short<uint16_t, 32>(sa, tile, smem, ws, limit_ns, phase); break;
+                case 2: compress_tile_short<uint16_t, 64>(sa, tile, smem, ws, limit_ns, phase); break;
+                case 4: compress_tile_short<uint32_t, 32>(sa, tile, smem, ws, limit_ns, phase); break;
+                default: compress_tile_short<uint32_t, 64>(sa, tile, smem, ws, limit_ns, phase); break;
+                }
                 continue;
             }
         }
@@ -359,7 +363,7 @@ namespace {
 
 bool a16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
-// Items of short 16-bit basic blocks take the short-block tiles in 256-thread
+// Items of short basic blocks take the short-block tiles in 256-thread
 // launches.
 bool item_short(const pc_params &p, uint32_t nt)
 {
@@ -368,7 +372,7 @@ bool item_short(const pc_params &p, uint32_t nt)
 
 uint32_t item_tb(const pc_params &p, uint32_t nt)
 {
-    if (item_short(p, nt)) return short_tile_blocks(p.block_len);
+    if (item_short(p, nt)) return short_tile_blocks(p.dtype_bits, p.block_len);
     return tile_cfg(kKernelCompress, p.variant, p.dtype_bits, p.word_bits, p.block_len, true, nt).tb;
 }
 

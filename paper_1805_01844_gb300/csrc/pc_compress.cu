@@ -6,15 +6,14 @@
 namespace pcx {
 
 
-// Long streams of short 16-bit basic blocks (L <= PCX_SHORT_MAXL, L / 8 a
-// power of two): look-back tiles of 128 (L = 256: 64) whole blocks
-// (compress_tile_short).
+// Long streams of short basic blocks (short_tiles_ok): look-back tiles of up
+// to 128 whole blocks (compress_tile_short).
 template <typename T, uint32_t WB>
 static cudaError_t launch_compress_short(const LaunchArgs &a, bool &taken)
 {
     taken = false;
     if (!short_tiles_ok(PC_VARIANT_BASIC, sizeof(T) * 8, WB, a.L)) return cudaSuccess;
-    const uint32_t tb = short_tile_blocks(a.L);
+    const uint32_t tb = short_tile_blocks(sizeof(T) * 8, a.L);
     const uint64_t n_tiles = ceil_div(a.n_blocks, (uint64_t)tb);
     if (n_tiles < kSmallTiles) return cudaSuccess;
     taken = true;
@@ -50,7 +49,7 @@ static cudaError_t launch_compress_short(const LaunchArgs &a, bool &taken)
 template <typename T, uint32_t WB, uint32_t VAR, bool ORB, uint32_t NT>
 static cudaError_t launch_compress_t(const LaunchArgs &a)
 {
-    if constexpr (VAR == PC_VARIANT_BASIC && sizeof(T) == 2) {
+    if constexpr (VAR == PC_VARIANT_BASIC) {
         bool taken = false;
         const cudaError_t e = launch_compress_short<T, WB>(a, taken);
         if (taken || e != cudaSuccess) return e;

@@ -883,23 +883,29 @@ PCX_HD uint32_t short_stage_bytes(uint32_t d, uint32_t L)
 #ifndef PCX_SHORT_MAXL
 #define PCX_SHORT_MAXL 256
 #endif
-// Streams (or batch items) of short 16-bit basic blocks that take these
-// tiles: L / 8 a power of two, L <= 128, or L = 256 with 64-bit words (with
+// Streams (or batch items) of short basic blocks that take these tiles: a
+// block is a power of two of 16-byte vectors, at most 32 (one per lane of a
+// group), and L <= 128, or L = 256 with 64-bit words for 16-bit data (with
 // 32-bit words, ~43 words per block, L = 256 measured 18 % slower than the
 // multi-stage tiles; with 64-bit words 1-14 % faster).
 PCX_HD bool short_tiles_ok(uint32_t variant, uint32_t d, uint32_t w, uint32_t L)
 {
-    return PCX_SHORT_TILES && variant == PC_VARIANT_BASIC && d == 16 && L <= PCX_SHORT_MAXL && L % 8 == 0 &&
-           ((L / 8) & (L / 8 - 1)) == 0 && (L <= 128 || w == 64);
+    const uint32_t ve = 16 / (d / 8), g = L / ve;
+    return PCX_SHORT_TILES && variant == PC_VARIANT_BASIC && L <= PCX_SHORT_MAXL && L % ve == 0 && g <= 32 &&
+           (g & (g - 1)) == 0 && (L <= 128 || w == 64);
 }
 
-// Blocks per look-back tile: 128, or 64 for blocks of 256 samples (so that
-// four CTAs of 256 threads share an SM's shared memory).
-PCX_HD uint32_t short_tile_blocks(uint32_t L) { return L <= 128 ? kShortTileBlocks : kShortTileBlocks / 2; }
+// Blocks per look-back tile: 128, or fewer so that a tile's samples stay
+// within 32 KB (four CTAs of 256 threads share an SM's shared memory).
+PCX_HD uint32_t short_tile_blocks(uint32_t d, uint32_t L)
+{
+    const uint32_t tb = 32768u / (L * (d / 8));
+    return tb < kShortTileBlocks ? tb : kShortTileBlocks;
+}
 
 PCX_HD uint32_t short_smem(uint32_t d, uint32_t L)
 {
-    return (uint32_t)round_up((uint64_t)short_tile_blocks(L) * short_stage_bytes(d, L) + sizeof(ShortVars), 16);
+    return (uint32_t)round_up((uint64_t)short_tile_blocks(d, L) * short_stage_bytes(d, L) + sizeof(ShortVars), 16);
 }
 
 template <typename T, uint32_t WB>

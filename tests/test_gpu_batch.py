@@ -111,8 +111,8 @@ def test_time_aware_autotune_stays_within_the_size_rule():
 
 
 def test_short_block_items_match_oracle():
-    """16-bit basic items of short blocks take look-back tiles of whole
-    short blocks in 256-thread launches: every item equals the oracle's
+    """Basic items of short blocks (16- and 32-bit) take look-back tiles of
+    whole short blocks in 256-thread launches: every item equals the oracle's
     stream, from one sample to several tiles, ragged last blocks included."""
     rng = np.random.default_rng(9)
     hosts, tensors, params = [], [], []
@@ -125,6 +125,12 @@ def test_short_block_items_match_oracle():
             hosts.append(x)
             tensors.append(to_dev(x))
             params.append(native.params(0, 16, w, L))
+    for L, w in [(4, 64), (32, 32), (128, 64)]:  # 32-bit samples
+        x = np.clip(rng.normal(2e6, 300, L * 200 + 3), 0, 2 ** 32 - 1).astype(np.uint32)
+        x[5] = 2 ** 32 - 1
+        hosts.append(x)
+        tensors.append(to_dev(x))
+        params.append(native.params(0, 32, w, L))
     b = Batch(tensors, params, cta_threads=256)
     b.compress()
     assert b.device_status() == 0
