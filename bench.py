@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-paper-sweeps", action="store_true")
     ap.add_argument("--serve-events", type=int, default=20000)
+    ap.add_argument("--serve-v2", action="store_true",
+                    help="also serve with the chooser and one version-2 stream per event")
     return ap.parse_args()
 
 
@@ -438,7 +440,7 @@ def main():
 
     serving = None
     if not args.no_serve and rank == 0 and world == 1:
-        serving = serve_metrics(dev, args.serve_events, trained)
+        serving = serve_metrics(dev, args.serve_events, trained, v2=args.serve_v2)
 
     if world > 1:
         dist.barrier()
@@ -897,7 +899,7 @@ def learned_vs_plain(dev, train_samples=2 << 30, test_bytes=1 << 30):
             c)
 
 
-def serve_metrics(dev, n_events, trained=None):
+def serve_metrics(dev, n_events, trained=None, v2=False):
     """The serving loop at 20k events/s (Poisson) from four camera
     geometries, continuous batching under an 8 GB budget, chooser off and on."""
     import numpy as np
@@ -910,8 +912,10 @@ def serve_metrics(dev, n_events, trained=None):
             for k, gi in enumerate([k % 4 for k in range(64)])]
     ev = [pool[int(rng.integers(0, len(pool)))] for _ in range(n_events)]
     out = {}
-    for name, ch in (("plain", None), ("learned", trained or Chooser(dev, seed=0))):
-        srv = serve.Server(dev, budget=8 << 30, n_streams=3, chooser=ch)
+    ch_l = trained or Chooser(dev, seed=0)
+    runs = [("plain", None, False), ("learned", ch_l, False)] + ([("learned_v2", ch_l, True)] if v2 else [])
+    for name, ch, use_v2 in runs:
+        srv = serve.Server(dev, budget=8 << 30, n_streams=3, chooser=ch, v2=use_v2)
         srv.run(ev[: min(500, n_events)], rate=20000.0, seed=1)  # warm-up
         m = srv.run(ev, rate=20000.0, seed=2)
         m.pop("kept", None)
@@ -919,8 +923,9 @@ def serve_metrics(dev, n_events, trained=None):
                                        "slots_per_stream")}
     out["note"] = ("plain = one stream per event (advanced, L 1024, w 64); learned = the chooser trained in the "
                    "'learned' section, one stream per 4096-sample segment, each with a 64-byte header (~1.7 % at "
-                   "this ratio), on pedestal + noise events where no option gains more than that; events cycle a "
-                   "pool of 64")
+                   "this ratio); learned_v2 (--serve-v2) = the same segments joined into one version-2 stream per "
+                   "event (a code byte and a 4-byte size per segment; one pc_assemble_v2 call per event); pedestal "
+                   "+ noise events; events cycle a pool of 64")
     return out
 
 

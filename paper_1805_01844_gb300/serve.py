@@ -16,8 +16,10 @@ With the learned chooser on, each event is cut into segments of 4096 samples
 whose parameters the MLP picks; features, choices and the per-segment
 compression of all admitted events run on the device without a host round
 trip (pc_segments_*), each segment's stream in its own slot of the event's
-output area.  Otherwise each event is one batch item with the plain
-parameters.
+output area; with v2, each event's segments are then joined into one
+version-2 stream (a code byte and a size per segment instead of a 64-byte
+header; pc_assemble_v2, one call per event).  Otherwise each event is one
+batch item with the plain parameters.
 """
 import time
 from collections import deque
@@ -63,27 +65,36 @@ class StreamPool:
         self.totals = totals  # device int64 [2]: events, compressed bytes
 
     def nbytes_held(self):
-        return self.inp.numel() * 2 + self.out.numel() + self.nbytes.numel() * 8
+        v2 = getattr(self, "v2out", None)
+        return (self.inp.numel() * 2 + self.out.numel() + self.nbytes.numel() * 8 +
+                (v2.numel() + self.v2n.numel() * 8 if v2 is not None else 0))
 
 
 class Server:
     def __init__(self, device="cuda", budget=8 << 30, n_streams=3, variant=native.ADVANCED,
-                 block_len=1024, word_bits=64, chooser=None, slot_cap=256):
+                 block_len=1024, word_bits=64, chooser=None, slot_cap=256, v2=False):
         self.device = torch.device(device)
         self.variant = variant
         self.chooser = chooser
+        self.v2 = bool(v2 and chooser is not None)
         self.params = native.params(variant, 16, word_bits, block_len)
         outb = [event_out_bytes(g[0] * g[1], self.params, chooser is not None) for g in GEOMETRIES]
-        per_event = sum(g[0] * g[1] * 2 + o + 8 * -(-g[0] * g[1] // native.SEGMENT_SAMPLES)
-                        for g, o in zip(GEOMETRIES, outb))
+        v2b = [(native.bound_v2(variant, 16, native.SEGMENT_SAMPLES, g[0] * g[1]) + 15) // 16 * 16 if self.v2 else 0
+               for g in GEOMETRIES]
+        per_event = sum(g[0] * g[1] * 2 + o + v + 8 * -(-g[0] * g[1] // native.SEGMENT_SAMPLES) + 8
+                        for g, o, v in zip(GEOMETRIES, outb, v2b))
         ws_reserve = n_streams * (48 << 20)  # launch workspaces (series tables, look-back words, plans)
         slots = int(max(1, min(slot_cap, (budget - ws_reserve) // per_event)))
         # per-stream running totals (events, compressed bytes) stay on the device
         self.totals = torch.zeros((len(GEOMETRIES), 2), dtype=torch.int64, device=self.device)
         self.pools = [StreamPool(g, slots, o, self.device, self.totals[i])
                       for i, (g, o) in enumerate(zip(GEOMETRIES, outb))]
+        for pool, v in zip(self.pools, v2b):  # the events' version-2 streams and their sizes
+            pool.v2out = torch.empty((slots, v), dtype=torch.uint8, device=self.device) if v else None
+            pool.v2n = torch.zeros(slots, dtype=torch.int64, device=self.device) if v else None
         self.cuda_streams = [torch.cuda.Stream(self.device) for _ in range(n_streams)]
         self.workspaces = [None] * n_streams
+        self.v2_workspaces = [None] * n_streams
         self.budget = budget
         assert sum(p.nbytes_held() for p in self.pools) + ws_reserve <= budget
 
@@ -166,9 +177,23 @@ class Server:
             seg = Segments([p.inp[slot] for p, (_, _, slot) in zip(pools, admitted)], self.variant,
                            outs=[p.out[slot] for p, (_, _, slot) in zip(pools, admitted)],
                            nbytes=[p.nbytes[slot] for p, (_, _, slot) in zip(pools, admitted)],
-                           totals=[p.totals for p in pools], workspace=self.workspaces[si], stream=stream)
+                           totals=None if self.v2 else [p.totals for p in pools], workspace=self.workspaces[si],
+                           stream=stream)
             self.workspaces[si] = seg.ws
             seg.compress(self.chooser.predict(seg.features()))
+            if self.v2:
+                seg.v2_slots = []
+                for k, (p, (_, _, slot)) in enumerate(zip(pools, admitted)):
+                    seg.assemble_v2(k, out=p.v2out[slot], out_bytes=p.v2n[slot:slot + 1],
+                                    workspace=self.v2_workspaces[si])
+                    self.v2_workspaces[si] = seg._v2_ws
+                    seg.v2_slots.append((p, slot))
+                idx = torch.tensor([gi for _, gi, _ in admitted], dtype=torch.int64).pin_memory()
+                idx = idx.to(self.device, non_blocking=True)
+                sizes = torch.cat([p.v2n[slot:slot + 1] for p, slot in seg.v2_slots])
+                self.totals[:, 1].index_add_(0, idx, sizes)
+                self.totals[:, 0].index_add_(0, idx, torch.ones_like(sizes))
+                seg.idx = idx  # kept alive until the launch completes
             return seg
         tensors = [self.pools[gi].inp[slot] for _, gi, slot in admitted]
         outs = [self.pools[gi].out[slot] for _, gi, slot in admitted]
@@ -187,18 +212,24 @@ class Server:
 def _streams_of(b, k):
     """Host bytes of the streams of member k of a finished launch."""
     if isinstance(b, Segments):
+        if getattr(b, "v2_slots", None):
+            p, slot = b.v2_slots[k]
+            return [p.v2out[slot][:int(p.v2n[slot].item())].cpu().numpy().tobytes()]
         return b.streams(k)
     n = int(b.nbytes[k].item())
     return [b.outs[k][:n].cpu().numpy().tobytes()]
 
 
-def compress_alone(x, variant=native.ADVANCED, block_len=1024, word_bits=64, chooser=None):
+def compress_alone(x, variant=native.ADVANCED, block_len=1024, word_bits=64, chooser=None, v2=False):
     """The same event compressed on its own: its stream, or with the chooser
-    the streams of its segments."""
+    the streams of its segments (v2: their version-2 stream)."""
     x = x.contiguous()
     if chooser is not None:
         seg = Segments([x], variant)
         seg.compress(chooser.predict(seg.features()))
+        if v2:
+            buf, nb = seg.assemble_v2(0)
+            return [buf[:int(nb.item())].cpu().numpy().tobytes()]
         return seg.streams(0)
     p = native.params(variant, 16, word_bits, block_len)
     b = Batch([x], [p])

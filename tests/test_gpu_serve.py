@@ -25,13 +25,13 @@ def events(n, seed):
     return out
 
 
-@pytest.mark.parametrize("use_chooser", [False, True])
-def test_results_identical_alone_and_in_the_mix(use_chooser):
+@pytest.mark.parametrize("use_chooser,v2", [(False, False), (True, False), (True, True)])
+def test_results_identical_alone_and_in_the_mix(use_chooser, v2):
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     dev = torch.device("cuda:0")
     ch = Chooser(dev, seed=1) if use_chooser else None
-    srv = serve.Server(dev, budget=1 << 30, n_streams=3, chooser=ch, slot_cap=16)
+    srv = serve.Server(dev, budget=1 << 30, n_streams=3, chooser=ch, slot_cap=16, v2=v2)
     ev = events(600, seed=3 + use_chooser)
     keep = list(range(0, 600, 37))
     m = srv.run(ev, rate=20000.0, seed=1, keep=keep)
@@ -41,22 +41,24 @@ def test_results_identical_alone_and_in_the_mix(use_chooser):
     for e in keep:
         gi, x = ev[e]
         xd = torch.from_numpy(x.view(np.int16).copy()).to(dev)
-        alone = serve.compress_alone(xd, chooser=ch)
+        alone = serve.compress_alone(xd, chooser=ch, v2=v2)
         assert m["kept"][e] == alone, e
-        # every piece is a stream of its segment (or of the whole event)
-        y = np.concatenate([oracle.decompress(s) for s in alone])
+        # every piece is a stream of its segment (or of the whole event; v2:
+        # the event's version-2 stream)
+        dec = oracle.decompress_v2 if v2 else oracle.decompress
+        y = np.concatenate([dec(s) for s in alone])
         assert np.array_equal(y, x)
 
 
-@pytest.mark.parametrize("use_chooser", [False, True])
-def test_device_totals_match_streams(use_chooser):
+@pytest.mark.parametrize("use_chooser,v2", [(False, False), (True, False), (True, True)])
+def test_device_totals_match_streams(use_chooser, v2):
     """The per-camera totals kept in device memory add up every event's
     streams exactly once."""
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     dev = torch.device("cuda:0")
     ch = Chooser(dev, seed=2) if use_chooser else None
-    srv = serve.Server(dev, budget=1 << 30, n_streams=2, chooser=ch, slot_cap=8)
+    srv = serve.Server(dev, budget=1 << 30, n_streams=2, chooser=ch, slot_cap=8, v2=v2)
     ev = events(120, seed=7)
     m = srv.run(ev, rate=50000.0, seed=3, keep=range(120))
     assert m["stream_bytes"] == sum(len(s) for e in range(120) for s in m["kept"][e])
